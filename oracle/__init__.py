@@ -1,0 +1,173 @@
+"""CPU oracle for the fused columnar scan (paper §2-§3).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+benchmark's ``cpu_baseline`` / reference leg are the only callers.  The
+product library never imports this package and this package never imports
+the product library; the two share only the seeded generators in ``synth``.
+
+The arithmetic lives in plain C (``gbscan_oracle.c``), built with gcc into
+``oracle/_build/liboracle.so``.  This module only marshals numpy arrays.
+Every function is pinned in ``tests/test_oracle.py`` against facts that do
+not come from the oracle itself (bit-level layout definition, reductions to
+numpy reshapes at b = 8/16/32, histogram brute force, closed forms).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gbscan_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+OK = 0
+EINVAL = 1
+
+_u32p = np.ctypeslib.ndpointer(dtype=np.uint32, flags="C_CONTIGUOUS")
+_i64 = ctypes.c_int64
+_u64 = ctypes.c_uint64
+_u32 = ctypes.c_uint32
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle with gcc (portable flags only; it also runs on Arm)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(
+            ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-pthread", "-o", tmp, _SRC]
+        )
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            lib.oracle_n_blocks.restype = _u64
+            lib.oracle_n_blocks.argtypes = [_u64]
+            lib.oracle_packed_words.restype = _u64
+            lib.oracle_packed_words.argtypes = [_u64, _u32]
+            lib.oracle_pack.restype = ctypes.c_int
+            lib.oracle_pack.argtypes = [_u32p, _u64, _u32, _u32, _u32p]
+            lib.oracle_unpack.restype = ctypes.c_int
+            lib.oracle_unpack.argtypes = [_u32p, _u64, _u32, _u32, _u32p]
+            lib.oracle_scan_values.restype = None
+            lib.oracle_scan_values.argtypes = [
+                _u32p, _u64, _i64, _i64, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]
+            lib.oracle_scan_packed.restype = ctypes.c_int
+            lib.oracle_scan_packed.argtypes = [
+                _u32p, _u64, _u32, _u32, _i64, _i64, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]
+            lib.oracle_zonemap.restype = ctypes.c_int
+            lib.oracle_zonemap.argtypes = [_u32p, _u64, _u32, _u32, _u32p, _u32p]
+            lib.oracle_scan_zoneskip.restype = ctypes.c_int
+            lib.oracle_scan_zoneskip.argtypes = [
+                _u32p, _u32p, _u32p, _u64, _u32, _u32, _i64, _i64,
+                ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_u64)]
+            lib.oracle_scan_packed_threads.restype = ctypes.c_int
+            lib.oracle_scan_packed_threads.argtypes = [
+                _u32p, _u64, _u32, _u32, _i64, _i64, ctypes.c_int,
+                ctypes.POINTER(_i64), ctypes.POINTER(_i64)]
+            _lib = lib
+    return _lib
+
+
+def _u32arr(a) -> np.ndarray:
+    a = np.ascontiguousarray(a)
+    if a.dtype != np.uint32:
+        raise TypeError(f"expected uint32 array, got {a.dtype}")
+    return a
+
+
+def n_blocks(n: int) -> int:
+    return int(_load().oracle_n_blocks(n))
+
+
+def packed_words(n: int, b: int) -> int:
+    return int(_load().oracle_packed_words(n, b))
+
+
+def pack(values, b: int, base: int = 0) -> np.ndarray:
+    """Lane-interleaved FOR encoding of ``values`` (uint32) at ``b`` bits."""
+    v = _u32arr(values)
+    n = v.size
+    out = np.zeros(max(packed_words(n, b), 1), dtype=np.uint32)
+    rc = _load().oracle_pack(v if n else np.zeros(1, np.uint32), n, b, base, out)
+    if rc != OK:
+        raise ValueError(f"oracle_pack rejected the input (b={b}, base={base})")
+    return out[: packed_words(n, b)]
+
+
+def unpack(words, n: int, b: int, base: int = 0) -> np.ndarray:
+    w = _u32arr(words)
+    out = np.zeros(max(n, 1), dtype=np.uint32)
+    rc = _load().oracle_unpack(w if w.size else np.zeros(1, np.uint32), n, b, base, out)
+    if rc != OK:
+        raise ValueError("oracle_unpack rejected the input")
+    return out[:n]
+
+
+def scan_values(values, lo: int, hi: int) -> tuple[int, int]:
+    """Brute force COUNT and SUM of lo <= v < hi over raw values."""
+    v = _u32arr(values)
+    c, s = _i64(), _i64()
+    _load().oracle_scan_values(v if v.size else np.zeros(1, np.uint32), v.size, lo, hi,
+                               ctypes.byref(c), ctypes.byref(s))
+    return c.value, s.value
+
+
+def scan_packed(words, n: int, b: int, base: int, lo: int, hi: int) -> tuple[int, int]:
+    """Fused decode -> filter -> aggregate over a packed column."""
+    w = _u32arr(words)
+    c, s = _i64(), _i64()
+    rc = _load().oracle_scan_packed(w if w.size else np.zeros(1, np.uint32), n, b, base, lo, hi,
+                                    ctypes.byref(c), ctypes.byref(s))
+    if rc != OK:
+        raise ValueError("oracle_scan_packed rejected the input")
+    return c.value, s.value
+
+
+def scan_packed_threads(words, n: int, b: int, base: int, lo: int, hi: int,
+                        threads: int) -> tuple[int, int]:
+    w = _u32arr(words)
+    c, s = _i64(), _i64()
+    rc = _load().oracle_scan_packed_threads(w if w.size else np.zeros(1, np.uint32), n, b, base,
+                                            lo, hi, threads, ctypes.byref(c), ctypes.byref(s))
+    if rc != OK:
+        raise ValueError("oracle_scan_packed_threads rejected the input")
+    return c.value, s.value
+
+
+def zonemap(words, n: int, b: int, base: int = 0) -> tuple[np.ndarray, np.ndarray]:
+    """Per-block (min, max) of decoded values."""
+    w = _u32arr(words)
+    nb = n_blocks(n)
+    zmin = np.zeros(max(nb, 1), dtype=np.uint32)
+    zmax = np.zeros(max(nb, 1), dtype=np.uint32)
+    rc = _load().oracle_zonemap(w if w.size else np.zeros(1, np.uint32), n, b, base, zmin, zmax)
+    if rc != OK:
+        raise ValueError("oracle_zonemap rejected the input")
+    return zmin[:nb], zmax[:nb]
+
+
+def scan_zoneskip(words, zmin, zmax, n: int, b: int, base: int, lo: int, hi: int):
+    """Zone-map skipping scan; returns (count, sum, blocks_scanned)."""
+    w = _u32arr(words)
+    zmn, zmx = _u32arr(zmin), _u32arr(zmax)
+    c, s, t = _i64(), _i64(), _u64()
+    one = np.zeros(1, np.uint32)
+    rc = _load().oracle_scan_zoneskip(w if w.size else one, zmn if zmn.size else one,
+                                      zmx if zmx.size else one, n, b, base, lo, hi,
+                                      ctypes.byref(c), ctypes.byref(s), ctypes.byref(t))
+    if rc != OK:
+        raise ValueError("oracle_scan_zoneskip rejected the input")
+    return c.value, s.value, t.value

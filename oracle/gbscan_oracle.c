@@ -1,0 +1,261 @@
+/*
+ * Plain, slow, single-threaded CPU oracle for the fused columnar scan.
+ *
+ * TEST INFRASTRUCTURE ONLY. Nothing in the product path may call, link or
+ * load this file: only the tests, the smoke check and the benchmark's CPU
+ * baseline leg use it. It shares no code, header or constant with the CUDA
+ * library; both sides only receive inputs from the seeded generators.
+ *
+ * What it computes (paper §2 "Problem and Model", §3 "Method"): a column of
+ * N unsigned 32-bit values v_i, each stored in b bits (1 <= b <= 32), is
+ * decoded, filtered by a predicate and aggregated in one pass.  The paper's
+ * predicates are equality counts; the scan here takes the half-open range
+ * lo <= v < hi (equality c is the range [c, c+1)) and returns
+ *     COUNT = #{ i : lo <= v_i < hi }
+ *     SUM   = sum of v_i over those i, exact in int64.
+ *
+ * Readings of what the paper leaves open (each one is a choice, listed with
+ * its reason in the design notes):
+ *   - Frame of reference: the stored code is u_i = v_i - base, 0 <= u_i < 2^b,
+ *     and base + 2^b - 1 must fit in 32 bits (so b = 32 forces base = 0).
+ *   - Transposed layout (§3, "FastLanes-style", 1024-value blocks over 32
+ *     lanes): value j of block k goes to lane j mod 32 at row floor(j/32).
+ *     Each lane owns a stream of 32*b bits; row r occupies stream bits
+ *     [r*b, r*b + b), least significant bit first, and stream bit p lives in
+ *     bit (p mod 32) of the lane's word floor(p/32).  Lane word w of block k
+ *     is stored at 32-bit offset 32*b*k + 32*w + lane.  No row reordering.
+ *   - The last block is padded with zero codes; padding is never counted.
+ *   - Zone maps (§3, "per-block zone maps (min/max skipping)"): one
+ *     (min, max) pair of decoded values per 1024-value block, over valid
+ *     positions only.  A block is skipped iff max < lo or min >= hi, which
+ *     cannot change COUNT or SUM.
+ *
+ * Parity pins for every function live in tests/test_oracle.py.
+ */
+#include <stdint.h>
+#include <stddef.h>
+#include <string.h>
+#include <pthread.h>
+
+#define ORACLE_OK 0
+#define ORACLE_EINVAL 1
+
+#define BLOCK_VALUES 1024u
+#define LANES 32u
+
+uint64_t oracle_n_blocks(uint64_t n) { return (n + BLOCK_VALUES - 1) / BLOCK_VALUES; }
+
+/* Number of 32-bit words of the packed column: b words per lane, 32 lanes per block. */
+uint64_t oracle_packed_words(uint64_t n, uint32_t b)
+{
+    return oracle_n_blocks(n) * (uint64_t)LANES * (uint64_t)b;
+}
+
+static int width_ok(uint32_t b, uint32_t base)
+{
+    if (b < 1 || b > 32) return 0;
+    /* the largest code must still decode to a 32-bit value */
+    if ((uint64_t)base + ((1ull << b) - 1ull) > 0xFFFFFFFFull) return 0;
+    return 1;
+}
+
+/* Offset of lane word `w` (0 <= w < b) of block `k`. */
+static uint64_t word_at(uint64_t k, uint32_t b, uint64_t w, uint32_t lane)
+{
+    return k * (uint64_t)LANES * b + (uint64_t)LANES * w + lane;
+}
+
+/* Encode: FOR subtraction, then place each code in its lane stream. */
+int oracle_pack(const uint32_t *values, uint64_t n, uint32_t b, uint32_t base, uint32_t *out)
+{
+    uint64_t i;
+    if (!width_ok(b, base)) return ORACLE_EINVAL;
+    if (n > 0 && (values == NULL || out == NULL)) return ORACLE_EINVAL;
+    for (i = 0; i < n; ++i) {
+        if (values[i] < base) return ORACLE_EINVAL;
+        if ((uint64_t)(values[i] - base) >> b) return ORACLE_EINVAL;
+    }
+    if (n == 0) return ORACLE_OK;
+    memset(out, 0, oracle_packed_words(n, b) * sizeof(uint32_t));
+    for (i = 0; i < n; ++i) {
+        uint64_t u = (uint64_t)(values[i] - base);
+        uint64_t k = i / BLOCK_VALUES;
+        uint64_t j = i % BLOCK_VALUES;
+        uint32_t lane = (uint32_t)(j % LANES);
+        uint64_t row = j / LANES;
+        uint64_t p = row * b;            /* first stream bit of this value */
+        uint64_t w = p / 32;
+        uint32_t off = (uint32_t)(p % 32);
+        out[word_at(k, b, w, lane)] |= (uint32_t)(u << off);
+        if (off + b > 32) /* the value continues in the lane's next word */
+            out[word_at(k, b, w + 1, lane)] |= (uint32_t)(u >> (32 - off));
+    }
+    return ORACLE_OK;
+}
+
+/* Code of value i, read back from its lane stream. */
+static uint32_t code_at(const uint32_t *words, uint64_t i, uint32_t b)
+{
+    uint64_t k = i / BLOCK_VALUES;
+    uint64_t j = i % BLOCK_VALUES;
+    uint32_t lane = (uint32_t)(j % LANES);
+    uint64_t row = j / LANES;
+    uint64_t p = row * b;
+    uint64_t w = p / 32;
+    uint32_t off = (uint32_t)(p % 32);
+    uint64_t window = words[word_at(k, b, w, lane)];
+    if (off + b > 32) window |= (uint64_t)words[word_at(k, b, w + 1, lane)] << 32;
+    return (uint32_t)((window >> off) & ((1ull << b) - 1ull));
+}
+
+/* Decode: code plus base. */
+int oracle_unpack(const uint32_t *words, uint64_t n, uint32_t b, uint32_t base, uint32_t *values)
+{
+    uint64_t i;
+    if (!width_ok(b, base)) return ORACLE_EINVAL;
+    for (i = 0; i < n; ++i) values[i] = code_at(words, i, b) + base;
+    return ORACLE_OK;
+}
+
+/* The plain definition over raw values: brute force, no packing involved. */
+void oracle_scan_values(const uint32_t *values, uint64_t n, int64_t lo, int64_t hi,
+                        int64_t *count, int64_t *sum)
+{
+    int64_t c = 0, s = 0;
+    uint64_t i;
+    for (i = 0; i < n; ++i) {
+        int64_t v = (int64_t)values[i];
+        if (lo <= v && v < hi) {
+            c += 1;
+            s += v;
+        }
+    }
+    *count = c;
+    *sum = s;
+}
+
+/* Fused decode -> filter -> aggregate over values [first, last) of a packed column. */
+static void scan_range(const uint32_t *words, uint64_t first, uint64_t last, uint32_t b,
+                       uint32_t base, int64_t lo, int64_t hi, int64_t *count, int64_t *sum)
+{
+    int64_t c = 0, s = 0;
+    uint64_t i;
+    for (i = first; i < last; ++i) {
+        int64_t v = (int64_t)code_at(words, i, b) + (int64_t)base;
+        if (lo <= v && v < hi) {
+            c += 1;
+            s += v;
+        }
+    }
+    *count = c;
+    *sum = s;
+}
+
+int oracle_scan_packed(const uint32_t *words, uint64_t n, uint32_t b, uint32_t base,
+                       int64_t lo, int64_t hi, int64_t *count, int64_t *sum)
+{
+    if (!width_ok(b, base)) return ORACLE_EINVAL;
+    scan_range(words, 0, n, b, base, lo, hi, count, sum);
+    return ORACLE_OK;
+}
+
+/* Per-block (min, max) of decoded values over the block's valid positions. */
+int oracle_zonemap(const uint32_t *words, uint64_t n, uint32_t b, uint32_t base,
+                   uint32_t *zmin, uint32_t *zmax)
+{
+    uint64_t k, i, nb = oracle_n_blocks(n);
+    if (!width_ok(b, base)) return ORACLE_EINVAL;
+    for (k = 0; k < nb; ++k) {
+        uint64_t first = k * BLOCK_VALUES;
+        uint64_t last = first + BLOCK_VALUES < n ? first + BLOCK_VALUES : n;
+        uint32_t mn = 0xFFFFFFFFu, mx = 0;
+        for (i = first; i < last; ++i) {
+            uint32_t v = code_at(words, i, b) + base;
+            if (v < mn) mn = v;
+            if (v > mx) mx = v;
+        }
+        zmin[k] = mn;
+        zmax[k] = mx;
+    }
+    return ORACLE_OK;
+}
+
+/* Zone-map skipping: scan only the blocks whose [min, max] meets [lo, hi). */
+int oracle_scan_zoneskip(const uint32_t *words, const uint32_t *zmin, const uint32_t *zmax,
+                         uint64_t n, uint32_t b, uint32_t base, int64_t lo, int64_t hi,
+                         int64_t *count, int64_t *sum, uint64_t *blocks_scanned)
+{
+    uint64_t k, nb = oracle_n_blocks(n), touched = 0;
+    int64_t c = 0, s = 0;
+    if (!width_ok(b, base)) return ORACLE_EINVAL;
+    for (k = 0; k < nb; ++k) {
+        uint64_t first = k * BLOCK_VALUES;
+        uint64_t last = first + BLOCK_VALUES < n ? first + BLOCK_VALUES : n;
+        int64_t bc, bs;
+        if ((int64_t)zmax[k] < lo || (int64_t)zmin[k] >= hi) continue;
+        touched += 1;
+        scan_range(words, first, last, b, base, lo, hi, &bc, &bs);
+        c += bc;
+        s += bs;
+    }
+    *count = c;
+    *sum = s;
+    *blocks_scanned = touched;
+    return ORACLE_OK;
+}
+
+/*
+ * The same fused scan split over `threads` disjoint block ranges, one POSIX
+ * thread each, with the per-thread (count, sum) added at the end.  Integer
+ * addition is associative, so the result equals oracle_scan_packed exactly.
+ * Used only to time the oracle on all host cores.
+ */
+struct range_job {
+    const uint32_t *words;
+    uint64_t first, last;
+    uint32_t b, base;
+    int64_t lo, hi, count, sum;
+};
+
+static void *range_worker(void *arg)
+{
+    struct range_job *j = (struct range_job *)arg;
+    scan_range(j->words, j->first, j->last, j->b, j->base, j->lo, j->hi, &j->count, &j->sum);
+    return NULL;
+}
+
+int oracle_scan_packed_threads(const uint32_t *words, uint64_t n, uint32_t b, uint32_t base,
+                               int64_t lo, int64_t hi, int threads, int64_t *count, int64_t *sum)
+{
+    enum { MAX_THREADS = 1024 };
+    static struct range_job jobs[MAX_THREADS];
+    static pthread_t tids[MAX_THREADS];
+    static int running[MAX_THREADS];
+    uint64_t nb = oracle_n_blocks(n), per;
+    int t;
+    int64_t c = 0, s = 0;
+    if (!width_ok(b, base) || threads < 1 || threads > MAX_THREADS) return ORACLE_EINVAL;
+    per = (nb + (uint64_t)threads - 1) / (uint64_t)threads;
+    for (t = 0; t < threads; ++t) {
+        uint64_t fb = (uint64_t)t * per, lb = fb + per;
+        jobs[t].words = words;
+        jobs[t].first = fb * BLOCK_VALUES < n ? fb * BLOCK_VALUES : n;
+        jobs[t].last = lb * BLOCK_VALUES < n ? lb * BLOCK_VALUES : n;
+        jobs[t].b = b;
+        jobs[t].base = base;
+        jobs[t].lo = lo;
+        jobs[t].hi = hi;
+        jobs[t].count = 0;
+        jobs[t].sum = 0;
+        running[t] = pthread_create(&tids[t], NULL, range_worker, &jobs[t]) == 0;
+        if (!running[t]) range_worker(&jobs[t]); /* run inline if a thread cannot start */
+    }
+    for (t = 0; t < threads; ++t) {
+        if (running[t]) pthread_join(tids[t], NULL);
+        c += jobs[t].count;
+        s += jobs[t].sum;
+    }
+    *count = c;
+    *sum = s;
+    return ORACLE_OK;
+}

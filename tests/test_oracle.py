@@ -1,0 +1,267 @@
+"""Pins for the CPU oracle against facts that do not come from the oracle.
+
+Each test names what fixes the expected value:
+  * the layout definition written at bit level with numpy bit arrays (an
+    independent construction from the oracle's shift/mask arithmetic);
+  * reductions of special widths to plain numpy reshapes (b = 8, 16, 32);
+  * histogram brute force (np.bincount) for COUNT/SUM, exhaustive on tiny
+    domains;
+  * closed forms (a permutation of 0..N-1 sums to N(N-1)/2);
+  * invariants (range additivity, frame-of-reference shift, zone-skip
+    exactness, multiset invariance under displacement);
+  * the probability of a zone-map skip on i.i.d. uniform data.
+A plausible mistake in the oracle (swapped lane/row, MSB-first streams, a
+dropped carry word, an inclusive upper bound, base not added back, a tail
+block counted) fails at least one of them.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+SIZES = [0, 1, 31, 32, 33, 1023, 1024, 1025, 4096 + 7]
+
+
+def layout_by_bits(values: np.ndarray, b: int, base: int) -> np.ndarray:
+    """Lane-interleaved image built from bit arrays (no shifts or masks).
+
+    Value j of a 1024-value block sits at lane j % 32, row j // 32; a lane's
+    stream is the concatenation of its rows' b-bit codes, least significant
+    bit first; stream bit p is bit p % 32 of lane word p // 32; word w of lane
+    l of block k is stored at 32*b*k + 32*w + l.
+    """
+    n = values.size
+    nb = (n + 1023) // 1024
+    codes = np.zeros(nb * 1024, dtype=np.uint32)
+    codes[:n] = values - np.uint32(base)
+    bits = np.unpackbits(codes.astype("<u4").view(np.uint8), bitorder="little")
+    bits = bits.reshape(nb * 1024, 32)[:, :b]              # code bits, LSB first
+    bits = bits.reshape(nb, 32, 32, b)                       # (block, row, lane, bit)
+    streams = bits.transpose(0, 2, 1, 3).reshape(nb, 32, 32 * b)   # (block, lane, stream bit)
+    words = np.packbits(streams.reshape(nb, 32, b, 32), axis=-1, bitorder="little")
+    words = words.reshape(nb, 32, b, 4).copy().view("<u4").reshape(nb, 32, b)  # (block, lane, word)
+    return words.transpose(0, 2, 1).reshape(-1).astype(np.uint32)
+
+
+def hist_count_sum(values: np.ndarray, lo: int, hi: int):
+    """COUNT/SUM from a value histogram (small domains only)."""
+    if values.size == 0:
+        return 0, 0
+    h = np.bincount(values.astype(np.int64))
+    lo_c, hi_c = max(lo, 0), min(hi, h.size)
+    if lo_c >= hi_c:
+        return 0, 0
+    v = np.arange(lo_c, hi_c, dtype=np.int64)
+    return int(h[lo_c:hi_c].sum()), int((h[lo_c:hi_c] * v).sum())
+
+
+@pytest.mark.parametrize("b", range(1, 33))
+def test_pack_matches_bit_level_layout(b):
+    base = 0 if b == 32 else 7 * b
+    for n in SIZES:
+        v = synth.uniform_values(synth.seed_for(90, b, n), n, b, base)
+        got = oracle.pack(v, b, base)
+        assert got.size == oracle.packed_words(n, b) == ((n + 1023) // 1024) * 32 * b
+        if n:
+            np.testing.assert_array_equal(got, layout_by_bits(v, b, base))
+
+
+@pytest.mark.parametrize("b", range(1, 33))
+def test_round_trip_all_widths_and_tails(b):
+    max_base = (1 << 32) - (1 << b)          # largest base that keeps codes in 32 bits
+    base = max_base if b % 3 == 0 else min(12345, max_base)
+    for n in SIZES:
+        v = synth.uniform_values(synth.seed_for(91, b, n), n, b, base)
+        np.testing.assert_array_equal(oracle.unpack(oracle.pack(v, b, base), n, b, base), v)
+
+
+def test_b32_is_the_plain_array():
+    # negative control (i) at b = 32: the transposed layout is the identity
+    v = synth.uniform_values(5, 4096, 32)
+    np.testing.assert_array_equal(oracle.pack(v, 32), v)
+    # tail: zero padded to whole blocks
+    w = oracle.pack(v[:1500], 32)
+    np.testing.assert_array_equal(w[:1500], v[:1500])
+    assert not w[1500:].any()
+
+
+def test_b16_and_b8_are_plain_transposes():
+    # b = 16: lane word w holds rows 2w (low half) and 2w+1 (high half)
+    v = synth.uniform_values(6, 3 * 1024, 16)
+    halves = oracle.pack(v, 16).view("<u2").reshape(3, 16, 32, 2)   # block, word, lane, half
+    np.testing.assert_array_equal(halves.transpose(0, 1, 3, 2).reshape(-1), v)
+    # b = 8: lane word w holds rows 4w .. 4w+3, one byte each
+    v = synth.uniform_values(7, 2 * 1024, 8)
+    q = oracle.pack(v, 8).view(np.uint8).reshape(2, 8, 32, 4)       # block, word, lane, byte
+    np.testing.assert_array_equal(q.transpose(0, 1, 3, 2).reshape(-1), v)
+
+
+def test_b3_repeating_pattern_closed_form():
+    # v_j = j mod 8 puts the constant code l mod 8 in every row of lane l;
+    # for lane 1 the 96-bit stream has ones exactly at positions = 0 (mod 3)
+    v = (np.arange(1024) % 8).astype(np.uint32)
+    w = oracle.pack(v, 3).reshape(3, 32)
+    expect = [sum(1 << p for p in range(32) if (32 * i + p) % 3 == 0) for i in range(3)]
+    assert [int(x) for x in w[:, 1]] == expect == [0x49249249, 0x92492492, 0x24924924]
+    assert not w[:, 0].any() and not w[:, 8].any()
+
+
+@pytest.mark.parametrize("b", [1, 2, 3, 4])
+def test_scan_exhaustive_small_domains(b):
+    d = 1 << b
+    for n in [1, 33, 1025, 2100]:
+        v = synth.uniform_values(synth.seed_for(92, b, n), n, b)
+        w = oracle.pack(v, b)
+        for lo in range(-1, d + 2):
+            for hi in range(-1, d + 2):
+                want = hist_count_sum(v, lo, hi)
+                assert oracle.scan_values(v, lo, hi) == want
+                assert oracle.scan_packed(w, n, b, 0, lo, hi) == want
+
+
+@pytest.mark.parametrize("b", [5, 8, 11, 13, 16, 21, 27, 31, 32])
+def test_scan_packed_matches_histogram(b):
+    n = 5000
+    v = synth.uniform_values(synth.seed_for(93, b), n, b)
+    w = oracle.pack(v, b)
+    rng = np.random.default_rng(b)
+    d = 1 << b
+    for _ in range(20):
+        lo, hi = sorted(int(x) for x in rng.integers(0, d + 1, size=2))
+        # histogram over the sorted unique values keeps memory small at large b
+        uniq, cnt = np.unique(v, return_counts=True)
+        m = (uniq >= lo) & (uniq < hi)
+        want = (int(cnt[m].sum()), int((uniq[m].astype(np.int64) * cnt[m]).sum()))
+        assert oracle.scan_packed(w, n, b, 0, lo, hi) == want
+
+
+def test_full_domain_closed_form():
+    n = 3 * 1024 + 77
+    b = math.ceil(math.log2(n))
+    v = np.random.default_rng(1).permutation(n).astype(np.uint32)
+    w = oracle.pack(v, b)
+    assert oracle.scan_packed(w, n, b, 0, 0, 1 << b) == (n, n * (n - 1) // 2)
+    assert oracle.scan_packed(w, n, b, 0, -(1 << 40), 1 << 40) == (n, n * (n - 1) // 2)
+    # equality predicate [c, c+1) hits exactly one value of a permutation
+    for c in (0, 1, n // 2, n - 1):
+        assert oracle.scan_packed(w, n, b, 0, c, c + 1) == (1, c)
+    assert oracle.scan_packed(w, n, b, 0, n, 1 << b) == (0, 0)
+
+
+def test_empty_and_inverted_ranges():
+    v = synth.uniform_values(3, 3000, 10)
+    w = oracle.pack(v, 10)
+    for lo, hi in [(5, 5), (9, 3), (1 << 10, 1 << 11), (-10, 0)]:
+        assert oracle.scan_packed(w, 3000, 10, 0, lo, hi) == (0, 0)
+
+
+def test_range_additivity_and_for_shift():
+    b, base, n = 12, 100_000, 7000
+    v = synth.uniform_values(4, n, b, base)
+    w = oracle.pack(v, b, base)
+    rng = np.random.default_rng(9)
+    for _ in range(30):
+        a, m, c = sorted(int(x) for x in rng.integers(base, base + (1 << b) + 1, size=3))
+        ac = oracle.scan_packed(w, n, b, base, a, c)
+        am = oracle.scan_packed(w, n, b, base, a, m)
+        mc = oracle.scan_packed(w, n, b, base, m, c)
+        assert ac == (am[0] + mc[0], am[1] + mc[1])
+        # frame of reference: the same codes read with base 0 see every value shifted
+        cu, su = oracle.scan_packed(w, n, b, 0, a - base, c - base)
+        assert ac == (cu, su + base * cu)
+
+
+def test_threaded_scan_equals_single_thread():
+    b, n = 9, 50_000
+    v = synth.uniform_values(8, n, b)
+    w = oracle.pack(v, b)
+    for lo, hi in [(0, 512), (13, 300), (511, 512)]:
+        ref = oracle.scan_packed(w, n, b, 0, lo, hi)
+        for t in (1, 3, 8):
+            assert oracle.scan_packed_threads(w, n, b, 0, lo, hi, t) == ref
+
+
+@pytest.mark.parametrize("b", [1, 7, 16, 32])
+def test_zonemap_matches_numpy_block_reductions(b):
+    base = 0 if b == 32 else 3
+    for n in [1, 1024, 5000]:
+        v = synth.clustered_values(synth.seed_for(94, b, n), n, b, 0.01, base)
+        zmin, zmax = oracle.zonemap(oracle.pack(v, b, base), n, b, base)
+        nb = (n + 1023) // 1024
+        pad_lo = np.full(nb * 1024, np.iinfo(np.uint32).max, np.uint32)
+        pad_hi = np.zeros(nb * 1024, np.uint32)
+        pad_lo[:n] = v
+        pad_hi[:n] = v
+        np.testing.assert_array_equal(zmin, pad_lo.reshape(nb, 1024).min(axis=1))
+        np.testing.assert_array_equal(zmax, pad_hi.reshape(nb, 1024).max(axis=1))
+
+
+@pytest.mark.parametrize("p", [0.0, 0.01, 0.1, 1.0])
+def test_zoneskip_is_exact_and_sorted_touches_few_blocks(p):
+    b, n = 16, 64 * 1024 + 100
+    v = synth.clustered_values(synth.seed_for(95, 0, int(p * 100)), n, b, p)
+    w = oracle.pack(v, b)
+    zmin, zmax = oracle.zonemap(w, n, b)
+    for sigma in [1e-4, 1e-3, 1e-2, 0.1, 0.5]:
+        lo, hi = synth.pick_range(synth.seed_for(95, 1, int(sigma * 1e4)), b, sigma)
+        c, s, touched = oracle.scan_zoneskip(w, zmin, zmax, n, b, 0, lo, hi)
+        assert (c, s) == oracle.scan_packed(w, n, b, 0, lo, hi) == oracle.scan_values(v, lo, hi)
+        if p == 0.0:
+            # sorted: the matches are one contiguous run of positions
+            assert touched <= math.ceil(c / 1024) + 1
+
+
+def test_zoneskip_on_uniform_data_follows_the_skip_probability():
+    # i.i.d. uniform codes: a block is skipped iff all 1024 values miss on one
+    # side, probability (lo/D)^1024 + (1 - hi/D)^1024.  The range [D-1, D)
+    # keeps only blocks that hold the maximum code: P(skip) = (1-1/D)^1024.
+    b, n = 16, 2048 * 1024
+    d = 1 << b
+    v = synth.uniform_values(11, n, b)
+    w = oracle.pack(v, b)
+    zmin, zmax = oracle.zonemap(w, n, b)
+    nb = n // 1024
+    _, _, touched = oracle.scan_zoneskip(w, zmin, zmax, n, b, 0, d - 1, d)
+    p_skip = (1 - 1 / d) ** 1024
+    skipped = nb - touched
+    sd = math.sqrt(nb * p_skip * (1 - p_skip))
+    assert abs(skipped - nb * p_skip) < 5 * sd
+    # an interior range of selectivity 0.1 skips nothing
+    lo, hi = d // 2, d // 2 + d // 10
+    _, _, touched = oracle.scan_zoneskip(w, zmin, zmax, n, b, 0, lo, hi)
+    assert touched == nb
+
+
+def test_displacement_keeps_the_multiset():
+    b, n = 16, 30_000
+    ref = np.sort(synth.uniform_values(21, n, b))
+    for p in [0.0, 0.01, 0.1, 1.0]:
+        v = synth.clustered_values(21, n, b, p)
+        np.testing.assert_array_equal(np.sort(v), ref)
+        w = oracle.pack(v, b)
+        assert oracle.scan_packed(w, n, b, 0, 1000, 40000) == oracle.scan_values(ref, 1000, 40000)
+
+
+def test_invalid_inputs_are_rejected():
+    v = np.array([0, 1, 2, 300], dtype=np.uint32)
+    with pytest.raises(ValueError):
+        oracle.pack(v, 8)            # 300 needs 9 bits
+    with pytest.raises(ValueError):
+        oracle.pack(v, 0)
+    with pytest.raises(ValueError):
+        oracle.pack(v, 33)
+    with pytest.raises(ValueError):
+        oracle.pack(v + 5, 9, base=6)  # value below the base
+    with pytest.raises(ValueError):
+        oracle.pack(v, 32, base=1)     # base + 2^32 - 1 overflows 32 bits
+
+
+def test_pick_range_hits_target_selectivity():
+    for b in [4, 8, 16]:
+        for sigma in [1e-3, 0.1, 0.5, 1.0]:
+            lo, hi = synth.pick_range(1, b, sigma)
+            assert 0 <= lo < hi <= (1 << b)
+            assert hi - lo == max(1, round(sigma * (1 << b)))
