@@ -1,0 +1,492 @@
+"""Benchmark of the fused columnar scan on GB300.
+
+Workload (one "step"): the bit-width x selectivity sweep -- for every width
+b = 1..32 a resident column of N = 2^28 uniform values in [0, 2^b), scanned
+at sigma in {1e-3, 1e-2, 0.1, 0.5, 0.9, 1.0} with the branch-free and the
+branchy kernel: 384 fused decode -> filter -> COUNT/SUM scans, 17.7 GB of
+packed columns.  Consecutive launches read different columns (sigma outer,
+b inner), so every scan streams its column from HBM, not L2.
+
+The JSON line reports the whole-job read throughput (algorithmic bytes
+N*b/8 per scan / device time), per-width GB/s and f = GB/s / beta_read with
+beta_read measured live by a read-only probe, the law refit (T_dec, b*),
+the roofline of the scan kernel at b >= 16, the end-to-end figure through the
+C ABI from pinned host buffers, and the oracle's CPU throughput.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "fused scan read GB/s & fraction of HBM BW vs b; values/s; batched-planned speedup"
+N_SWEEP = 1 << 28
+WIDTHS = list(range(1, 33))
+SIGMAS = [1e-3, 1e-2, 0.1, 0.5, 0.9, 1.0]
+STRATS = ["branchfree", "branchy"]
+WORKLOAD = ("bit-width x selectivity sweep: N=2^28 uniform values per width, b=1..32, "
+            "sigma in {1e-3,1e-2,0.1,0.5,0.9,1.0}, branch-free + branchy, COUNT + int64 SUM "
+            "(384 scans per step)")
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        return {}
+
+
+def pred_for(b, sigma):
+    return synth.pick_range(synth.seed_for(2, b, 1 + int(round(sigma * 1e4))), b, sigma)
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is None:
+            self.out = ""
+            return
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = []
+        for line in (getattr(self, "out", "") or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[4:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r[1:]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def source_digest() -> str:
+    h = hashlib.sha256()
+    for f in ["scan_kernels.cuh", "gb_ptx.cuh", "scan_inst.cu"]:
+        h.update(open(os.path.join(ROOT, "paper_2606_22423_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_from_profile(b_lo=16):
+    """dram bytes per launch from the committed ncu summary, if it matches this source."""
+    p = os.path.join(ROOT, "profiles", "scan_full_traffic.json")
+    try:
+        d = json.load(open(p))
+    except (OSError, ValueError):
+        return None
+    if d.get("source_digest") != source_digest():
+        return None
+    return d
+
+
+# ============================================================ CPU / oracle
+def cpu_sample_gbs(columns_host, threads, budget_s=12.0):
+    """Oracle (threaded) on prefixes of the sweep columns at sigma = 0.1."""
+    import oracle
+
+    total_bytes, t_used, scans = 0, 0.0, 0
+    for b, words in columns_host:
+        lo, hi = pred_for(b, 0.1)
+        n = words.size // b * 32  # values covered by these whole blocks
+        t0 = time.perf_counter()
+        oracle.scan_packed_threads(words, n, b, 0, lo, hi, threads)
+        t_used += time.perf_counter() - t0
+        total_bytes += n * b / 8
+        scans += 1
+        if t_used > budget_s:
+            break
+    return total_bytes / t_used / 1e9, scans, t_used
+
+
+def run_reference(args, world, rank):
+    """The oracle as it stands, timed on the host cores, on a sample of the sweep."""
+    if rank != 0:
+        return
+    import oracle
+
+    oracle.build()
+    threads = os.cpu_count() or 1
+    n = 1 << 20                    # sample: a 2^20-value column per width, same distribution
+    cols = []
+    for b in WIDTHS:
+        v = synth.uniform_values(synth.seed_for(2, b), n, b)
+        cols.append((b, oracle.pack(v, b)))
+    preds = {(b, s): pred_for(b, s) for b in WIDTHS for s in SIGMAS}
+
+    def step():
+        nbytes = 0
+        for _ in STRATS:
+            for s in SIGMAS:
+                for b, words in cols:
+                    lo, hi = preds[(b, s)]
+                    oracle.scan_packed_threads(words, n, b, 0, lo, hi, threads)
+                    nbytes += n * b / 8
+        return nbytes
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    nbytes = 0
+    for _ in range(args.steps):
+        nbytes += step()
+    dt = time.perf_counter() - t0
+    gbs = nbytes / dt / 1e9
+    sample = (f"384 scans per step (32 widths x 6 sigmas x 2) over a 2^20-value column per width drawn "
+              f"from the same distribution; oracle.scan_packed_threads on {threads} host threads")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "n_per_width_sampled": n},
+        "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ============================================================ GPU arm
+def run_ours(args, world, rank, local):
+    import torch
+
+    from paper_2606_22423_gb300 import build as libbuild
+    from paper_2606_22423_gb300 import gbscan, lawfit
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (no CPU fallback)")
+    libbuild.build()
+    gbscan.load()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(device=dev)
+    pk = peaks()
+    hbm_peak = pk.get("hbm_gbs")
+    peak_src = "measured" if hbm_peak else "fallback"
+    hbm_peak = hbm_peak or 6800.0
+
+    # ---- beta_read: read-only probe over 4 GiB (best of 10)
+    probe = torch.empty(1 << 30, dtype=torch.int32, device=dev)
+    probe.fill_(7)
+    chk = torch.zeros(1, dtype=torch.int64, device=dev)
+    with torch.cuda.stream(stream):
+        best = 0.0
+        for i in range(13):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            gbscan.scan_probe_read(probe, probe.numel() * 4, chk, stream)
+            e1.record(stream)
+            e1.synchronize()
+            if i >= 3:
+                best = max(best, probe.numel() * 4 / (e0.elapsed_time(e1) * 1e-3) / 1e9)
+    beta_read = best
+    del probe
+    torch.cuda.empty_cache()
+
+    # ---- resident columns (device-side generation + device encoder)
+    cols = {}
+    for b in WIDTHS:
+        v = synth.uniform_values_device(synth.seed_for(2, b), N_SWEEP, b, device=dev)
+        cols[b] = gbscan.Column.from_device(v, N_SWEEP, b, stream=stream)
+        del v
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    preds = {(b, s): pred_for(b, s) for b in WIDTHS for s in SIGMAS}
+    order = [(st, s, b) for st in STRATS for s in SIGMAS for b in WIDTHS]
+    res = torch.zeros((len(order), 4), dtype=torch.int64, device=dev)
+    bytes_of = {b: N_SWEEP * b / 8 for b in WIDTHS}
+    step_bytes = sum(bytes_of[b] for _, _, b in order)
+
+    def step(evs=None):
+        for i, (st, s, b) in enumerate(order):
+            lo, hi = preds[(b, s)]
+            if evs is not None:
+                evs[i][0].record(stream)
+            cols[b].run_async(lo, hi, res[i], st, stream)
+            if evs is not None:
+                evs[i][1].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    for b in WIDTHS:
+        cols[b].status(stream)
+    # exactness across strategies: branch-free and branchy must agree bit for bit
+    r = res.cpu().numpy()
+    half = len(order) // 2
+    assert (r[:half, :3] == r[half:, :3]).all(), "branchy and branch-free disagree"
+
+    all_evs = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                for _ in order] for _ in range(args.steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t0.record(stream)
+        for k in range(args.steps):
+            step(all_evs[k])
+        t1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    ms = t0.elapsed_time(t1)
+    ms_max = max_over_ranks(ms, world)
+    value = step_bytes * args.steps * world / (ms_max * 1e-3) / 1e9
+    clocks = clk.summary()
+    for b in WIDTHS:
+        cols[b].status(stream)
+
+    # ---- per-launch durations
+    dur = {}
+    for i, key in enumerate(order):
+        dur[key] = statistics.mean(all_evs[k][i][0].elapsed_time(all_evs[k][i][1]) for k in range(args.steps))
+    per_b = {}
+    fit_pts = {st: ([], []) for st in STRATS}
+    for st in STRATS:
+        for b in WIDTHS:
+            ts = [dur[(st, s, b)] for s in SIGMAS]
+            gbs = [bytes_of[b] / (t * 1e-3) / 1e9 for t in ts]
+            for g in gbs:
+                fit_pts[st][0].append(b)
+                fit_pts[st][1].append(g / beta_read)
+            per_b.setdefault(str(b), {})[st] = {
+                "gbs_by_sigma": [round(g, 1) for g in gbs],
+                "gbs": round(bytes_of[b] * len(ts) / (sum(ts) * 1e-3) / 1e9, 1),
+                "f": round(bytes_of[b] * len(ts) / (sum(ts) * 1e-3) / 1e9 / beta_read, 4),
+                "gvals_per_s": round(N_SWEEP * len(ts) / (sum(ts) * 1e-3) / 1e9, 1),
+            }
+    law = {}
+    for st in STRATS:
+        bb, ff = (np.array(x) for x in fit_pts[st])
+        t_dec, med = lawfit.fit_tdec(bb, ff, beta_read * 1e9)
+        t_lsq, rms = lawfit.fit_tdec_lsq(bb, ff, beta_read * 1e9)
+        law[st] = {"t_dec_gvals": round(t_dec / 1e9, 1), "b_star": round(lawfit.ridge(t_dec, beta_read * 1e9), 2),
+                   "median_abs_err": round(med, 4), "t_dec_lsq_gvals": round(t_lsq / 1e9, 1), "rms_err": round(rms, 4)}
+    # branch crossover analogue (time per scan vs sigma, averaged over widths b <= 8 where decode binds)
+    small = [b for b in WIDTHS if b <= 8]
+    t_br = [statistics.mean(dur[("branchy", s, b)] for b in small) for s in SIGMAS]
+    t_bf = [statistics.mean(dur[("branchfree", s, b)] for b in small) for s in SIGMAS]
+    branch = lawfit.fit_branch_models(np.array(SIGMAS), np.array(t_br), np.array(t_bf))
+    branch["sigma"] = SIGMAS
+    branch["ms_branchy"] = [round(x, 5) for x in t_br]
+    branch["ms_branchfree"] = [round(x, 5) for x in t_bf]
+
+    # ---- roofline: the branch-free scan kernel at b >= 16 (HBM-bound regime)
+    hb = [(st, s, b) for (st, s, b) in order if st == "branchfree" and b >= 16]
+    ach = sum(bytes_of[b] for _, _, b in hb) / (sum(dur[k] for k in hb) * 1e-3) / 1e9
+    prof = traffic_from_profile()
+    roofline = {"kernel": "k_scan_full<b, branch-free>, b=16..32", "bound": "hbm", "achieved": round(ach, 1),
+                "peak": hbm_peak, "unit": "GB/s", "frac": round(ach / hbm_peak, 4),
+                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs, a read+write copy)",
+                "frac_of_beta_read": round(ach / beta_read, 4),
+                "traffic": prof["dram_bytes_per_launch"] if prof else None,
+                "traffic_algorithmic": prof["algorithmic_bytes_per_launch"] if prof else None}
+
+    # ---- realised selectivities
+    realised = {}
+    for i, (st, s, b) in enumerate(order):
+        if st == "branchfree" and b in (8, 16, 32):
+            realised[f"b{b}_sigma{s}"] = round(r[i, 0] / N_SWEEP, 6)
+
+    # ---- e2e through the C ABI with host buffers: upload each packed column
+    # from pinned memory, then its 12 scans with host results
+    e2e = None
+    if not args.no_e2e:
+        host = {}
+        for b in WIDTHS:
+            words = gbscan.scan_packed_words(N_SWEEP, b)
+            h = torch.empty(words, dtype=torch.int32, pin_memory=True)
+            dev_view = torch.empty(words, dtype=torch.int32, device=dev)
+            cudart_copy(dev_view, cols[b].dev_packed, words * 4)
+            h.copy_(dev_view)
+            del dev_view
+            host[b] = h
+        torch.cuda.synchronize()
+
+        def e2e_step():
+            for b in WIDTHS:
+                cols[b].upload_packed(host[b], stream)
+                for st in STRATS:
+                    for s in SIGMAS:
+                        lo, hi = preds[(b, s)]
+                        cols[b].run(lo, hi, st, stream)
+
+        e2e_step()
+        barrier(world)
+        torch.cuda.synchronize()
+        t_a = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        dt = max_over_ranks(time.perf_counter() - t_a, world)
+        e2e = {"value": step_bytes * args.steps * world / dt / 1e9, "unit": "GB/s",
+               "h2d_bytes_per_step": int(sum(gbscan.scan_packed_words(N_SWEEP, b) * 4 for b in WIDTHS)),
+               "d2h_bytes_per_step": 36 * len(order),
+               "path": "scan_column_upload_packed (pinned host) + scan_run x 12 per width"}
+        del host
+
+    # ---- CPU baseline: the oracle on a bounded sample, all host cores
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import oracle
+
+        oracle.build()
+        threads = os.cpu_count() or 1
+        sample_n = 1 << 24
+        host_cols = []
+        for b in WIDTHS:
+            words = sample_n // 1024 * 32 * b
+            t = torch.empty(words, dtype=torch.int32, device=dev)
+            cudart_copy(t, cols[b].dev_packed, words * 4)
+            host_cols.append((b, t.cpu().numpy().view(np.uint32)))
+        gbs, scans, used = cpu_sample_gbs(host_cols, threads)
+        cpu = {"value": round(gbs, 3), "unit": "GB/s", "cores": threads, "kind": "oracle",
+               "sample": f"{scans} scans at sigma=0.1 over the first 2^24 values of the b=1..{host_cols[scans-1][0]} "
+                         f"columns ({used:.1f} s); oracle.scan_packed_threads"}
+
+    for c in cols.values():
+        c.close()
+
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_per_width": N_SWEEP, "widths": "1..32", "sigmas": SIGMAS,
+                   "strategies": STRATS, "parallelism": f"replicas x{world} (independent sweeps, no collective)",
+                   "l2": "inputs larger than L2: each launch reads a different column than the one before; "
+                         "17.7 GB of columns per step vs 129 MB L2"},
+        "beta_read_gbs": round(beta_read, 1),
+        "roofline": roofline,
+        "law": law,
+        "per_b": per_b,
+        "branch_crossover": branch,
+        "realised_sigma": realised,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "gpu_launches": len(order) * args.steps,
+        "clocks": clocks,
+        "source_digest": source_digest(),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def cudart_copy(dst_tensor, src_ptr: int, nbytes: int):
+    """Device-to-device copy from a raw pointer the library owns into a torch tensor."""
+    import ctypes
+
+    import torch  # noqa: F401
+
+    rt = None
+    for name in ("libcudart.so.13", "libcudart.so", "/usr/local/cuda/lib64/libcudart.so"):
+        try:
+            rt = ctypes.CDLL(name)
+            break
+        except OSError:
+            continue
+    rt.cudaMemcpy.restype = ctypes.c_int
+    rt.cudaMemcpy.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int]
+    rc = rt.cudaMemcpy(dst_tensor.data_ptr(), src_ptr, nbytes, 3)  # cudaMemcpyDeviceToDevice
+    if rc != 0:
+        raise RuntimeError(f"cudaMemcpy failed ({rc})")
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,181 @@
+/*
+ * gbscan: fused columnar scan for GB300 (sm_103a) behind a plain C ABI.
+ *
+ * The operation (paper §2 "Problem and Model"): a column of N unsigned 32-bit
+ * values, each stored in b bits (1 <= b <= 32), is decoded, filtered and
+ * aggregated in one pass.  Reading the column costs N*b/8 bytes, so the scan
+ * can at best run at the memory bandwidth beta; the paper's bandwidth
+ * fraction is f = (N*b/8 / T) / beta and its law (Eq. 2) is
+ * f = min(1, T_dec*b/(8*beta)) with ridge b* = 8*beta/T_dec.
+ *
+ * Encoding (paper §3, the FastLanes-style transposed layout):
+ *   - frame of reference: code u = v - base, 0 <= u < 2^b, and
+ *     base + 2^b - 1 <= 2^32 - 1 (so b = 32 forces base = 0);
+ *   - 1024-value blocks over 32 lanes: value j of block k goes to lane
+ *     j mod 32, row j / 32; a lane's stream holds its 32 rows' b-bit codes
+ *     least-significant bit first; stream bit p is bit p mod 32 of lane word
+ *     p / 32; lane word w of block k is 32-bit word 32*b*k + 32*w + lane.
+ *     A block is b rows of 32 words, i.e. 128*b contiguous bytes;
+ *   - the last block is zero padded; padding never matches.
+ *   The packed column occupies scan_packed_words(n, b) 32-bit words.
+ *
+ * Predicate and aggregate: half-open lo <= v < hi on decoded values (int64
+ * bounds; the paper's equality count on c is [c, c+1)); the result is the
+ * exact COUNT and the exact int64 SUM of the matching values.  N <= 2^31,
+ * so the SUM cannot overflow.
+ *
+ * Conventions for every entry point:
+ *   - the return value is a scan_status; no C++ exception crosses the ABI;
+ *     on failure scan_last_error() returns a message (thread local);
+ *   - "stream" is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream); work is enqueued on it and, unless stated, the call returns
+ *     without waiting;
+ *   - pointers named dev_* are device memory on the current CUDA device,
+ *     host_* are host memory (pinned memory makes copies asynchronous);
+ *   - a scan_column owns the device memory it allocates and frees it in
+ *     scan_column_destroy; a column made by scan_column_create_packed borrows
+ *     the caller's packed buffer, which must outlive the column;
+ *   - calls that use the same column must be ordered on one stream (a column
+ *     carries its own small device workspace); different columns may run on
+ *     different streams concurrently.
+ */
+#ifndef GBSCAN_H
+#define GBSCAN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SCAN_OK = 0,
+    SCAN_EINVAL = 1,   /* bad argument: width, range, size, null or misaligned pointer */
+    SCAN_ENOMEM = 2,   /* a device or pinned host allocation failed */
+    SCAN_ECUDA = 3,    /* a CUDA runtime call failed; see scan_last_error() */
+    SCAN_ETIMEOUT = 4, /* a bounded device-side wait gave up; the result is not valid */
+    SCAN_EBUSY = 5,    /* resource temporarily unavailable (e.g. a full server queue) */
+    SCAN_ENOTSUP = 6   /* the request is valid but this build cannot serve it */
+} scan_status;
+
+typedef enum {
+    SCAN_AUTO = 0,         /* library picks (law / planner); always the same result */
+    SCAN_BRANCHFREE = 1,   /* full scan, predicated (mask) aggregation */
+    SCAN_BRANCHY = 2,      /* full scan, warp-vote early-out per 32-value group */
+    SCAN_ZONE_SKIP_BF = 3, /* zone-map block skipping + persistent queue, branch-free */
+    SCAN_ZONE_SKIP_BR = 4  /* zone-map block skipping + persistent queue, branchy */
+} scan_strategy;
+
+typedef struct {
+    int64_t lo; /* inclusive lower bound on decoded v */
+    int64_t hi; /* exclusive upper bound; lo >= hi selects nothing */
+} scan_pred;
+
+typedef struct {
+    int64_t count;           /* #{ i : lo <= v_i < hi } */
+    int64_t sum;             /* sum of those v_i, exact */
+    uint64_t blocks_scanned; /* 1024-value blocks whose packed bytes were read */
+    uint64_t reserved;
+} scan_result;
+
+typedef struct scan_column scan_column; /* opaque */
+
+/* ------------------------------------------------------------ messages */
+
+/* Message for the last failing call on this thread ("" if none). Never NULL. */
+const char *scan_last_error(void);
+
+/* Name of a status code, e.g. "SCAN_EINVAL". Never NULL. */
+const char *scan_status_string(scan_status s);
+
+/* ------------------------------------------------------ layout (host only) */
+
+/* 32-bit words of a packed column of n values at b bits: ceil(n/1024)*32*b.
+ * Returns 0 for b outside 1..32. */
+uint64_t scan_packed_words(uint64_t n, uint32_t b);
+
+/* Host encoder (paper §3 transposed layout, with frame of reference).
+ * Writes scan_packed_words(n, b) words to host_out (caller owned).  Needs no
+ * GPU.  SCAN_EINVAL if b is outside 1..32, base + 2^b - 1 > 2^32 - 1, n > 2^31,
+ * a pointer is NULL (n > 0), or any value lies outside [base, base + 2^b). */
+scan_status scan_encode_host(const uint32_t *host_values, uint64_t n, uint32_t b, uint32_t base,
+                             uint32_t *host_out);
+
+/* Device encoder: the same layout, computed on the GPU from dev_values into
+ * dev_out (scan_packed_words(n, b) words, 16-byte aligned).  Synchronises
+ * the stream to report out-of-range values as SCAN_EINVAL. */
+scan_status scan_encode_device(const uint32_t *dev_values, uint64_t n, uint32_t b, uint32_t base,
+                               uint32_t *dev_out, void *stream);
+
+/* -------------------------------------------------------------- columns */
+
+/* Encode host values on the host, allocate device memory and upload.
+ * Returns after the upload is complete. */
+scan_status scan_column_create(const uint32_t *host_values, uint64_t n, uint32_t b, uint32_t base,
+                               void *stream, scan_column **out);
+
+/* Allocate a column and encode device-resident values on the GPU. */
+scan_status scan_column_create_device(const uint32_t *dev_values, uint64_t n, uint32_t b,
+                                      uint32_t base, void *stream, scan_column **out);
+
+/* Wrap an already packed device buffer (scan_packed_words(n, b) words,
+ * 16-byte aligned) without copying; the caller keeps ownership. */
+scan_status scan_column_create_packed(const uint32_t *dev_packed, uint64_t n, uint32_t b,
+                                      uint32_t base, void *stream, scan_column **out);
+
+/* Overwrite the column's packed bytes from a host buffer of
+ * scan_packed_words(n, b) words (asynchronous if host_packed is pinned).
+ * Any zone map built before is marked stale and must be rebuilt. */
+scan_status scan_column_upload_packed(scan_column *col, const uint32_t *host_packed, void *stream);
+
+/* Free the column and what it owns.  Synchronises the device first. */
+scan_status scan_column_destroy(scan_column *col);
+
+/* Shape and device pointers of a column (any out pointer may be NULL).
+ * dev_zonemap is NULL until scan_zonemap_build has run; it holds one
+ * (min, max) pair of decoded uint32 values per block, as 2*nblocks words. */
+scan_status scan_column_info(const scan_column *col, uint64_t *n, uint32_t *b, uint32_t *base,
+                             const uint32_t **dev_packed, const uint32_t **dev_zonemap);
+
+/* ------------------------------------------------------------ zone maps */
+
+/* Build the per-block (min, max) zone map (paper §3, "per-block zone maps
+ * (min/max skipping)"; §6 clustering crossover).  Idempotent; one read of the
+ * packed column, 8 bytes written per block. */
+scan_status scan_zonemap_build(scan_column *col, void *stream);
+
+/* ---------------------------------------------------------------- scans */
+
+/* Fused decode -> filter -> aggregate.  Enqueues the kernels on `stream`,
+ * waits for them and writes the result to host memory.  The result is the
+ * same, bit for bit, for every strategy.  Zone-skip strategies need a built
+ * zone map (SCAN_EINVAL otherwise).  SCAN_ETIMEOUT if a bounded device wait
+ * gave up (the result is then not valid). */
+scan_status scan_run(scan_column *col, scan_pred pred, scan_strategy strategy, void *stream,
+                     scan_result *host_out);
+
+/* As scan_run, but writes the 32-byte result to device memory and returns
+ * without waiting.  Check scan_column_status afterwards for device errors. */
+scan_status scan_run_async(scan_column *col, scan_pred pred, scan_strategy strategy, void *stream,
+                           scan_result *dev_out);
+
+/* Wait for the stream and report (then clear) device-side error flags of the
+ * column's kernels: SCAN_OK or SCAN_ETIMEOUT. */
+scan_status scan_column_status(scan_column *col, void *stream);
+
+/* --------------------------------------------------------------- probes */
+
+/* Read-only bandwidth probe (paper §3: beta is the empirical sequential-read
+ * maximum): every byte of dev_buf (16-byte aligned, bytes a multiple of 16)
+ * is read once and folded into a checksum written to *dev_out (8 bytes). */
+scan_status scan_probe_read(const void *dev_buf, uint64_t bytes, void *stream, uint64_t *dev_out);
+
+/* Number of SMs and the persistent grid size the scan kernels use for width b. */
+scan_status scan_launch_shape(uint32_t b, uint32_t *sms, uint32_t *ctas, uint32_t *warps_per_cta,
+                              uint32_t *blocks_per_tile, uint32_t *stages);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBSCAN_H */

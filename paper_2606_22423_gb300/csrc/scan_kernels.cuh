@@ -1,0 +1,659 @@
+// Fused columnar-scan kernels, templated on the bit width B (1..32).
+//
+// Paper §3: 1024-value blocks transposed over 32 lanes so that every lane
+// extracts its values with the same shifts and masks.  On the GPU a block is
+// B rows of 32 words (128*B contiguous bytes); row w holds word w of every
+// lane.  Eight threads cover one block: thread q of the group owns lanes
+// 4q..4q+3 and reads one 16-byte vector per row, so a warp works on four
+// blocks at once and every shared-memory read is conflict-free.
+//
+// Data movement is the GB300 part: each warp runs its own pipeline of
+// kStages shared-memory slots, filled by the bulk TMA engine
+// (cp.async.bulk + mbarrier transaction counts), so ~100 KB per SM stay in
+// flight without holding registers.  The full scan walks tiles in a static
+// persistent order; the zone-skip scan pops candidate blocks from a device
+// queue (one atomic per tile).  Per-thread partials are reduced by warp
+// shuffles, then per CTA, then by the last CTA to finish (no second launch).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "gb_ptx.cuh"
+
+namespace gb {
+
+enum : uint32_t { kErrTimeout = 1u, kErrRange = 2u };
+
+struct ScanParams {
+    const uint32_t* packed;       // lane-interleaved words, 16-byte aligned
+    uint64_t n;                   // number of values
+    uint32_t base;                // frame-of-reference base
+    uint32_t lo;                  // predicate lower bound in code space
+    uint32_t wm1;                 // predicate width minus one (width >= 1)
+    uint32_t pad0;
+    uint64_t zlo, zhi;            // predicate [zlo, zhi) on decoded values, for zone tests
+    const uint2* zonemap;         // (min, max) of decoded values per block
+    uint2* zonemap_out;           // zone-map build output
+    unsigned long long* partials; // 2 words per CTA
+    unsigned int* done;           // grid-finish ticket, reset by the last CTA
+    unsigned int* status;         // error bits (kErr*)
+    unsigned int* cand;           // zone-skip candidate block ids
+    unsigned long long* qctl;     // [0] candidates, [1] queue head, [2] tail kept
+    long long* result;            // count, sum, blocks_scanned, reserved
+};
+
+// Launch shape for width B: warps per CTA, pipeline depth, blocks per tile.
+template <int B>
+struct Shape {
+    static constexpr int kWarps = B <= 16 ? 8 : 4;
+    static constexpr int kStages = 3;
+    static constexpr int kBlockBytes = 128 * B;
+    static constexpr int kBudget = 192 * 1024;
+    static constexpr int kTbRaw = (kBudget / (kWarps * kStages * kBlockBytes)) & ~3;
+    static constexpr int kTB = kTbRaw < 4 ? 4 : (kTbRaw > 128 ? 128 : kTbRaw);
+    static constexpr int kTileBytes = kTB * kBlockBytes;
+    static constexpr int kSlotBytes = kWarps * kStages * kTileBytes;
+    static constexpr int kSmemBytes = kSlotBytes + kWarps * kStages * 8 + kWarps * kStages * 4;
+    static_assert(kSmemBytes <= 227 * 1024, "shared-memory budget");
+    static_assert(kTileBytes % 16 == 0, "bulk copies move multiples of 16 bytes");
+};
+
+// ------------------------------------------------------------- extraction
+__device__ __forceinline__ uint32_t lane_word(const uint4& v, int k)
+{
+    return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
+}
+
+// Code of row r for the thread's lane k (r, k compile-time after unrolling).
+template <int B>
+__device__ __forceinline__ uint32_t code_of(const uint4 (&W)[B], int r, int k)
+{
+    const int bit = r * B;
+    const int w0 = bit >> 5;
+    const int s = bit & 31;
+    const uint32_t lw = lane_word(W[w0], k);
+    if constexpr (B == 32) {
+        return lw;
+    } else {
+        constexpr uint32_t kMask = (1u << B) - 1u;
+        if (s + B <= 32) return (lw >> s) & kMask;
+        const int w1 = (w0 + 1 < B) ? w0 + 1 : w0;
+        return __funnelshift_r(lw, lane_word(W[w1], k), s) & kMask;
+    }
+}
+
+template <int B>
+__device__ __forceinline__ void load_rows(uint4 (&W)[B], const uint4* rows)
+{
+#pragma unroll
+    for (int w = 0; w < B; ++w) W[w] = rows[w * 8];
+}
+
+// -------------------------------------------------------------- aggregate
+// One block, this thread's 4 lanes x 32 rows, every value valid.
+// Accumulators stay 32-bit inside the block:
+//   B <= 21: one word per lane packs (count << (B+5)) + sum;
+//   B <= 27: a 32-bit sum per lane plus a count;
+//   else   : a 64-bit sum.
+template <int B, bool BRANCHY>
+__device__ __forceinline__ void agg_block(const uint4* rows, uint32_t lo, uint32_t wm1,
+                                          uint64_t& cnt, uint64_t& sum)
+{
+    uint4 W[B];
+    load_rows<B>(W, rows);
+    if constexpr (B <= 21) {
+        constexpr int kSB = B + 5;
+        constexpr uint32_t kInc = 1u << kSB;
+        uint32_t a[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+        for (int r = 0; r < 32; ++r) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t u = code_of<B>(W, r, k);
+                const bool m = (u - lo) <= wm1;
+                if constexpr (!BRANCHY) {
+                    if (m) a[k] += u + kInc;
+                } else {
+                    const uint32_t bal = __ballot_sync(kFull, m);
+                    if (bal == kFull) {
+                        a[k] += u + kInc;
+                    } else if (bal != 0u) {
+                        if (m) a[k] += u + kInc;
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            cnt += a[k] >> kSB;
+            sum += a[k] & (kInc - 1u);
+        }
+    } else if constexpr (B <= 27) {
+        uint32_t c = 0u;
+        uint32_t s[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+        for (int r = 0; r < 32; ++r) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t u = code_of<B>(W, r, k);
+                const bool m = (u - lo) <= wm1;
+                if constexpr (!BRANCHY) {
+                    if (m) {
+                        c += 1u;
+                        s[k] += u;
+                    }
+                } else {
+                    const uint32_t bal = __ballot_sync(kFull, m);
+                    if (bal == kFull) {
+                        c += 1u;
+                        s[k] += u;
+                    } else if (bal != 0u) {
+                        if (m) {
+                            c += 1u;
+                            s[k] += u;
+                        }
+                    }
+                }
+            }
+        }
+        cnt += c;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) sum += s[k];
+    } else {
+        uint32_t c = 0u;
+        uint64_t s = 0u;
+#pragma unroll
+        for (int r = 0; r < 32; ++r) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t u = code_of<B>(W, r, k);
+                const bool m = (u - lo) <= wm1;
+                if constexpr (!BRANCHY) {
+                    if (m) {
+                        c += 1u;
+                        s += u;
+                    }
+                } else {
+                    const uint32_t bal = __ballot_sync(kFull, m);
+                    if (bal == kFull) {
+                        c += 1u;
+                        s += u;
+                    } else if (bal != 0u) {
+                        if (m) {
+                            c += 1u;
+                            s += u;
+                        }
+                    }
+                }
+            }
+        }
+        cnt += c;
+        sum += s;
+    }
+}
+
+// Same with a validity mask: value (r, lane 4q+k) counts iff `ok` and its
+// index in the block, 32r + 4q + k, is below `limit`.  Used for the last
+// partial warp step of a tile and for the zero-padded tail block.
+template <int B>
+__device__ __forceinline__ void agg_block_masked(const uint4* rows, uint32_t lo, uint32_t wm1,
+                                                 uint64_t& cnt, uint64_t& sum, bool ok,
+                                                 uint32_t limit, int q)
+{
+    uint4 W[B];
+    load_rows<B>(W, rows);
+    uint32_t c = 0u;
+    uint64_t s = 0u;
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t u = code_of<B>(W, r, k);
+            const uint32_t j = 32u * r + 4u * q + k;
+            if (ok && j < limit && (u - lo) <= wm1) {
+                c += 1u;
+                s += u;
+            }
+        }
+    }
+    cnt += c;
+    sum += s;
+}
+
+// (min, max) of codes of one block over valid positions.
+template <int B>
+__device__ __forceinline__ void minmax_block(const uint4* rows, uint32_t limit, int q,
+                                             uint32_t& mn, uint32_t& mx)
+{
+    uint4 W[B];
+    load_rows<B>(W, rows);
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t u = code_of<B>(W, r, k);
+            const uint32_t j = 32u * r + 4u * q + k;
+            if (j < limit) {
+                mn = min(mn, u);
+                mx = max(mx, u);
+            }
+        }
+    }
+}
+
+// All `nb` blocks of a staged tile (blocks are contiguous in the slot).
+template <int B, bool BRANCHY>
+__device__ __forceinline__ void scan_tile(const unsigned char* tile, uint32_t nb, int lane,
+                                          uint32_t lo, uint32_t wm1, uint64_t& cnt, uint64_t& sum)
+{
+    constexpr uint32_t kBB = 128u * B;
+    const int q = lane & 7;
+    const uint32_t sub = static_cast<uint32_t>(lane >> 3);
+    uint32_t g = 0;
+#pragma unroll 1
+    for (; g + 4u <= nb; g += 4u)
+        agg_block<B, BRANCHY>(reinterpret_cast<const uint4*>(tile + (g + sub) * kBB) + q, lo, wm1,
+                              cnt, sum);
+    if (g < nb) {
+        const bool ok = g + sub < nb;
+        agg_block_masked<B>(reinterpret_cast<const uint4*>(tile + (ok ? g + sub : g) * kBB) + q, lo,
+                            wm1, cnt, sum, ok, 1024u, q);
+    }
+}
+
+// --------------------------------------------------------- grid reduction
+// Sum (count, sum) over the grid: warp shuffles, one word pair per CTA, and
+// the last CTA to arrive folds the pairs, applies the frame of reference
+// (SUM_v = SUM_u + base*COUNT) and resets the ticket for the next launch.
+template <int WARPS>
+__device__ __forceinline__ void grid_finish(const ScanParams& p, uint64_t cnt, uint64_t sum,
+                                            bool queue_mode, uint64_t full_blocks_scanned)
+{
+    __shared__ unsigned long long red[WARPS][2];
+    __shared__ int is_last;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        cnt += __shfl_xor_sync(kFull, cnt, o);
+        sum += __shfl_xor_sync(kFull, sum, o);
+    }
+    if (lane == 0) {
+        red[warp][0] = cnt;
+        red[warp][1] = sum;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long c = 0, s = 0;
+        for (int w = 0; w < WARPS; ++w) {
+            c += red[w][0];
+            s += red[w][1];
+        }
+        p.partials[2 * blockIdx.x] = c;
+        p.partials[2 * blockIdx.x + 1] = s;
+        __threadfence();
+        const unsigned t = atomicAdd(p.done, 1u);
+        is_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    unsigned long long c = 0, s = 0;
+    for (unsigned i = threadIdx.x; i < gridDim.x; i += blockDim.x) {
+        c += __ldcg(&p.partials[2 * i]);
+        s += __ldcg(&p.partials[2 * i + 1]);
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        c += __shfl_xor_sync(kFull, c, o);
+        s += __shfl_xor_sync(kFull, s, o);
+    }
+    __syncthreads();
+    if (lane == 0) {
+        red[warp][0] = c;
+        red[warp][1] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long tc = 0, ts = 0;
+        for (int w = 0; w < WARPS; ++w) {
+            tc += red[w][0];
+            ts += red[w][1];
+        }
+        unsigned long long blocks = full_blocks_scanned;
+        if (queue_mode) {
+            blocks = __ldcg(&p.qctl[0]) + __ldcg(&p.qctl[2]);
+            p.qctl[0] = 0ull;
+            p.qctl[1] = 0ull;
+            p.qctl[2] = 0ull;
+        }
+        p.result[0] = static_cast<long long>(tc);
+        p.result[1] = static_cast<long long>(ts + static_cast<unsigned long long>(p.base) * tc);
+        p.result[2] = static_cast<long long>(blocks);
+        p.result[3] = 0;
+        __threadfence();
+        *p.done = 0u;
+    }
+}
+
+// Tail block (n mod 1024 values, zero padded) read straight from global memory.
+template <int B>
+__device__ __forceinline__ void scan_tail(const ScanParams& p, int lane, uint64_t& cnt,
+                                          uint64_t& sum)
+{
+    const uint64_t tb = p.n >> 10;
+    const uint32_t rem = static_cast<uint32_t>(p.n & 1023u);
+    const int q = lane & 7;
+    const bool ok = (lane >> 3) == 0;
+    const uint4* rows = reinterpret_cast<const uint4*>(p.packed + tb * 32u * B) + q;
+    agg_block_masked<B>(rows, p.lo, p.wm1, cnt, sum, ok, rem, q);
+}
+
+// ------------------------------------------------------------- full scan
+template <int B, bool BRANCHY>
+__global__ void __launch_bounds__(Shape<B>::kWarps * 32, 1) k_scan_full(const ScanParams p)
+{
+    using S = Shape<B>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char* slots = smem + static_cast<size_t>(warp) * S::kStages * S::kTileBytes;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S::kSlotBytes) + warp * S::kStages;
+
+    const uint64_t full_blocks = p.n >> 10;
+    const uint64_t ntiles = (full_blocks + S::kTB - 1) / S::kTB;
+    const uint64_t gw = static_cast<uint64_t>(blockIdx.x) * S::kWarps + warp;
+    const uint64_t GW = static_cast<uint64_t>(gridDim.x) * S::kWarps;
+
+    if (lane == 0) {
+        for (int s = 0; s < S::kStages; ++s) mbar_init(&bars[s], 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+
+    auto issue = [&](uint64_t t, int s) {
+        const uint64_t fb = t * S::kTB;
+        const uint64_t left = full_blocks - fb;
+        const uint32_t nb = left < S::kTB ? static_cast<uint32_t>(left) : S::kTB;
+        const uint32_t bytes = nb * S::kBlockBytes;
+        mbar_arrive_expect_tx(&bars[s], bytes);
+        bulk_g2s(slots + s * S::kTileBytes, p.packed + fb * 32u * B, bytes, &bars[s]);
+    };
+    if (lane == 0) {
+        for (int s = 0; s < S::kStages; ++s) {
+            const uint64_t t = gw + s * GW;
+            if (t < ntiles) issue(t, s);
+        }
+    }
+
+    uint64_t cnt = 0, sum = 0;
+    uint32_t it = 0;
+    bool failed = false;
+#pragma unroll 1
+    for (uint64_t t = gw; t < ntiles; t += GW, ++it) {
+        const int s = static_cast<int>(it % S::kStages);
+        const uint32_t parity = (it / S::kStages) & 1u;
+        const bool ok = mbar_wait(&bars[s], parity, kWaitLimitNs);
+        if (!__all_sync(kFull, ok)) {
+            failed = true;
+            break;
+        }
+        const uint64_t left = full_blocks - t * S::kTB;
+        const uint32_t nb = left < S::kTB ? static_cast<uint32_t>(left) : S::kTB;
+        scan_tile<B, BRANCHY>(slots + s * S::kTileBytes, nb, lane, p.lo, p.wm1, cnt, sum);
+        __syncwarp();
+        const uint64_t tn = t + static_cast<uint64_t>(S::kStages) * GW;
+        if (lane == 0 && tn < ntiles) {
+            fence_proxy_async_smem();
+            issue(tn, s);
+        }
+    }
+    if (failed) {
+        if (lane == 0) atomicOr(p.status, kErrTimeout);
+        // let copies still in flight land before the CTA's shared memory goes away
+        for (uint32_t j = 0; j < static_cast<uint32_t>(S::kStages); ++j) {
+            const uint64_t t = gw + static_cast<uint64_t>(it + j) * GW;
+            if (t >= ntiles) break;
+            const uint32_t jt = it + j;
+            mbar_wait(&bars[jt % S::kStages], (jt / S::kStages) & 1u, kDrainLimitNs);
+        }
+    }
+    if ((p.n & 1023u) && gw == GW - 1) scan_tail<B>(p, lane, cnt, sum);
+    grid_finish<S::kWarps>(p, cnt, sum, false, (p.n + 1023u) >> 10);
+}
+
+// -------------------------------------------------------- zone-map build
+template <int B>
+__global__ void __launch_bounds__(Shape<B>::kWarps * 32, 1) k_zonemap_build(const ScanParams p)
+{
+    using S = Shape<B>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int q = lane & 7;
+    const uint32_t sub = static_cast<uint32_t>(lane >> 3);
+    unsigned char* slots = smem + static_cast<size_t>(warp) * S::kStages * S::kTileBytes;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S::kSlotBytes) + warp * S::kStages;
+
+    const uint64_t full_blocks = p.n >> 10;
+    const uint64_t ntiles = (full_blocks + S::kTB - 1) / S::kTB;
+    const uint64_t gw = static_cast<uint64_t>(blockIdx.x) * S::kWarps + warp;
+    const uint64_t GW = static_cast<uint64_t>(gridDim.x) * S::kWarps;
+
+    if (lane == 0) {
+        for (int s = 0; s < S::kStages; ++s) mbar_init(&bars[s], 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    auto issue = [&](uint64_t t, int s) {
+        const uint64_t fb = t * S::kTB;
+        const uint64_t left = full_blocks - fb;
+        const uint32_t nb = left < S::kTB ? static_cast<uint32_t>(left) : S::kTB;
+        const uint32_t bytes = nb * S::kBlockBytes;
+        mbar_arrive_expect_tx(&bars[s], bytes);
+        bulk_g2s(slots + s * S::kTileBytes, p.packed + fb * 32u * B, bytes, &bars[s]);
+    };
+    if (lane == 0) {
+        for (int s = 0; s < S::kStages; ++s) {
+            const uint64_t t = gw + s * GW;
+            if (t < ntiles) issue(t, s);
+        }
+    }
+    auto emit = [&](uint64_t blk, bool ok, uint32_t mn, uint32_t mx) {
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            mn = min(mn, __shfl_xor_sync(kFull, mn, o));
+            mx = max(mx, __shfl_xor_sync(kFull, mx, o));
+        }
+        if (ok && q == 0) p.zonemap_out[blk] = make_uint2(mn + p.base, mx + p.base);
+    };
+    uint32_t it = 0;
+    bool failed = false;
+#pragma unroll 1
+    for (uint64_t t = gw; t < ntiles; t += GW, ++it) {
+        const int s = static_cast<int>(it % S::kStages);
+        const uint32_t parity = (it / S::kStages) & 1u;
+        const bool okw = mbar_wait(&bars[s], parity, kWaitLimitNs);
+        if (!__all_sync(kFull, okw)) {
+            failed = true;
+            break;
+        }
+        const uint64_t fb = t * S::kTB;
+        const uint64_t left = full_blocks - fb;
+        const uint32_t nb = left < S::kTB ? static_cast<uint32_t>(left) : S::kTB;
+        const unsigned char* tile = slots + s * S::kTileBytes;
+#pragma unroll 1
+        for (uint32_t g = 0; g < nb; g += 4u) {
+            const bool ok = g + sub < nb;
+            uint32_t mn = 0xffffffffu, mx = 0u;
+            minmax_block<B>(
+                reinterpret_cast<const uint4*>(tile + (ok ? g + sub : g) * (128u * B)) + q, 1024u,
+                q, mn, mx);
+            emit(fb + g + sub, ok, mn, mx);
+        }
+        __syncwarp();
+        const uint64_t tn = t + static_cast<uint64_t>(S::kStages) * GW;
+        if (lane == 0 && tn < ntiles) {
+            fence_proxy_async_smem();
+            issue(tn, s);
+        }
+    }
+    if (failed) {
+        if (lane == 0) atomicOr(p.status, kErrTimeout);
+        for (uint32_t j = 0; j < static_cast<uint32_t>(S::kStages); ++j) {
+            const uint64_t t = gw + static_cast<uint64_t>(it + j) * GW;
+            if (t >= ntiles) break;
+            const uint32_t jt = it + j;
+            mbar_wait(&bars[jt % S::kStages], (jt / S::kStages) & 1u, kDrainLimitNs);
+        }
+    }
+    if ((p.n & 1023u) && gw == GW - 1) {
+        const uint32_t rem = static_cast<uint32_t>(p.n & 1023u);
+        const uint4* rows = reinterpret_cast<const uint4*>(p.packed + full_blocks * 32u * B) + q;
+        uint32_t mn = 0xffffffffu, mx = 0u;
+        minmax_block<B>(rows, sub == 0 ? rem : 0u, q, mn, mx);
+        emit(full_blocks, sub == 0, mn, mx);
+    }
+}
+
+// ----------------------------------------------------- zone-map filtering
+constexpr int kFilterThreads = 256;
+constexpr int kFilterPerCta = 2048;
+// k_zone_filter (not templated) is defined once, in the host library unit.
+__global__ void k_zone_filter(const ScanParams p);
+
+// ------------------------------------------------------- zone-skip scan
+// Persistent warps pop up to kTB candidate ids per atomic from the queue,
+// merge consecutive ids into single bulk copies, and scan the staged blocks.
+template <int B, bool BRANCHY>
+__global__ void __launch_bounds__(Shape<B>::kWarps * 32, 1) k_scan_queue(const ScanParams p)
+{
+    using S = Shape<B>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char* slots = smem + static_cast<size_t>(warp) * S::kStages * S::kTileBytes;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S::kSlotBytes) + warp * S::kStages;
+    uint32_t* slot_n = reinterpret_cast<uint32_t*>(smem + S::kSlotBytes + S::kWarps * S::kStages * 8) +
+                       warp * S::kStages;
+
+    const uint64_t ncand = __ldcg(&p.qctl[0]);
+    if (lane == 0) {
+        for (int s = 0; s < S::kStages; ++s) mbar_init(&bars[s], 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+
+    // Pop the next chunk into slot s; returns its block count (0 = queue empty).
+    auto grab = [&](int s) -> uint32_t {
+        unsigned long long start = 0;
+        if (lane == 0) start = atomicAdd(&p.qctl[1], static_cast<unsigned long long>(S::kTB));
+        start = __shfl_sync(kFull, start, 0);
+        const unsigned long long avail = start < ncand ? ncand - start : 0ull;
+        const uint32_t nb = avail < static_cast<unsigned long long>(S::kTB) ? static_cast<uint32_t>(avail)
+                                                                            : static_cast<uint32_t>(S::kTB);
+        if (nb == 0) return 0u;
+        if (lane == 0) mbar_arrive_expect_tx(&bars[s], nb * S::kBlockBytes);
+        __syncwarp();
+        fence_proxy_async_smem();
+        unsigned char* dst = slots + s * S::kTileBytes;
+        for (uint32_t seg = 0; seg < nb; seg += 32u) {
+            const uint32_t i = seg + lane;
+            const bool valid = i < nb;
+            const uint32_t id = valid ? __ldcg(&p.cand[start + i]) : 0u;
+            const uint32_t prev = __shfl_up_sync(kFull, id, 1);
+            const bool head = valid && (lane == 0 || prev + 1u != id);
+            const uint32_t heads = __ballot_sync(kFull, head);
+            const uint32_t vmask = __ballot_sync(kFull, valid);
+            if (head) {
+                const uint32_t later = heads & ~((2u << lane) - 1u);
+                const uint32_t end = later ? static_cast<uint32_t>(__ffs(later) - 1)
+                                           : static_cast<uint32_t>(32 - __clz(vmask));
+                const uint32_t len = end - static_cast<uint32_t>(lane);
+                bulk_g2s(dst + i * S::kBlockBytes, p.packed + static_cast<uint64_t>(id) * 32u * B,
+                         len * S::kBlockBytes, &bars[s]);
+            }
+        }
+        return nb;
+    };
+
+    for (int s = 0; s < S::kStages; ++s) {
+        const uint32_t nb = grab(s);
+        if (lane == 0) slot_n[s] = nb;
+        if (nb == 0) {
+            for (int r = s + 1; r < S::kStages; ++r)
+                if (lane == 0) slot_n[r] = 0u;
+            break;
+        }
+    }
+    __syncwarp();
+
+    uint64_t cnt = 0, sum = 0;
+    uint32_t it = 0;
+    bool failed = false;
+#pragma unroll 1
+    for (;; ++it) {
+        const int s = static_cast<int>(it % S::kStages);
+        const uint32_t nb = slot_n[s];
+        if (nb == 0) break;
+        const bool ok = mbar_wait(&bars[s], (it / S::kStages) & 1u, kWaitLimitNs);
+        if (!__all_sync(kFull, ok)) {
+            failed = true;
+            break;
+        }
+        scan_tile<B, BRANCHY>(slots + s * S::kTileBytes, nb, lane, p.lo, p.wm1, cnt, sum);
+        __syncwarp();
+        const uint32_t nn = grab(s);
+        if (lane == 0) slot_n[s] = nn;
+        __syncwarp();
+    }
+    if (failed) {
+        if (lane == 0) atomicOr(p.status, kErrTimeout);
+        for (uint32_t j = 0; j < static_cast<uint32_t>(S::kStages); ++j) {
+            const uint32_t jt = it + j;
+            if (slot_n[jt % S::kStages] == 0) break;
+            mbar_wait(&bars[jt % S::kStages], (jt / S::kStages) & 1u, kDrainLimitNs);
+        }
+    }
+    // the zero-padded tail block is tested and scanned by CTA 0, warp 0
+    if ((p.n & 1023u) && blockIdx.x == 0 && warp == 0) {
+        const uint2 z = p.zonemap[p.n >> 10];
+        if (static_cast<uint64_t>(z.y) >= p.zlo && static_cast<uint64_t>(z.x) < p.zhi) {
+            scan_tail<B>(p, lane, cnt, sum);
+            if (lane == 0) p.qctl[2] = 1ull;
+        }
+    }
+    grid_finish<S::kWarps>(p, cnt, sum, true, 0);
+}
+
+// ----------------------------------------------------------- dispatching
+enum OpKind : int {
+    kOpFullBF = 0,
+    kOpFullBR = 1,
+    kOpQueueBF = 2,
+    kOpQueueBR = 3,
+    kOpZoneBuild = 4,
+};
+
+struct ShapeInfo {
+    int warps, stages, tile_blocks, smem_bytes;
+};
+
+template <int LO, int HI>
+__host__ inline ShapeInfo shape_range(int b)
+{
+    if constexpr (LO > HI) {
+        return ShapeInfo{0, 0, 0, 0};
+    } else {
+        if (b == LO) return ShapeInfo{Shape<LO>::kWarps, Shape<LO>::kStages, Shape<LO>::kTB,
+                                      Shape<LO>::kSmemBytes};
+        return shape_range<LO + 1, HI>(b);
+    }
+}
+inline ShapeInfo shape_of(int b) { return shape_range<1, 32>(b); }
+
+}  // namespace gb
+
+// One translation unit per width range instantiates the kernels; these are
+// the entry points the host library dispatches to.
+cudaError_t gb_launch_range_1_8(int b, int op, const gb::ScanParams& p, int grid, cudaStream_t st);
+cudaError_t gb_launch_range_9_16(int b, int op, const gb::ScanParams& p, int grid, cudaStream_t st);
+cudaError_t gb_launch_range_17_24(int b, int op, const gb::ScanParams& p, int grid, cudaStream_t st);
+cudaError_t gb_launch_range_25_32(int b, int op, const gb::ScanParams& p, int grid, cudaStream_t st);

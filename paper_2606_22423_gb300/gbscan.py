@@ -1,0 +1,234 @@
+"""ctypes binding of libgbscan.so (the C ABI declared in include/gbscan.h).
+
+Argument marshalling only: every step of the scan runs in the library's
+CUDA kernels.  There is no CPU fallback; if the library is missing or fails
+to load, importing this module raises.  Device buffers are passed as torch
+tensors (their data_ptr()) or raw integers, streams as torch.cuda.Stream or
+raw cudaStream_t integers.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgbscan.so")
+
+SCAN_OK, SCAN_EINVAL, SCAN_ENOMEM, SCAN_ECUDA, SCAN_ETIMEOUT, SCAN_EBUSY, SCAN_ENOTSUP = range(7)
+SCAN_AUTO, SCAN_BRANCHFREE, SCAN_BRANCHY, SCAN_ZONE_SKIP_BF, SCAN_ZONE_SKIP_BR = range(5)
+STRATEGIES = {
+    "auto": SCAN_AUTO,
+    "branchfree": SCAN_BRANCHFREE,
+    "branchy": SCAN_BRANCHY,
+    "zone_bf": SCAN_ZONE_SKIP_BF,
+    "zone_br": SCAN_ZONE_SKIP_BR,
+}
+
+
+class ScanError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_status_name(status)}: {msg}")
+        self.status = status
+
+
+class scan_pred(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_int64), ("hi", ctypes.c_int64)]
+
+
+class scan_result(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int64), ("sum", ctypes.c_int64),
+                ("blocks_scanned", ctypes.c_uint64), ("reserved", ctypes.c_uint64)]
+
+    def pair(self):
+        return int(self.count), int(self.sum)
+
+
+_u32p = ctypes.POINTER(ctypes.c_uint32)
+_vp = ctypes.c_void_p
+_u64 = ctypes.c_uint64
+_u32 = ctypes.c_uint32
+_st = ctypes.c_int
+
+# name -> (restype, argtypes); every function declared in include/gbscan.h
+SIGNATURES = {
+    "scan_last_error": (ctypes.c_char_p, []),
+    "scan_status_string": (ctypes.c_char_p, [_st]),
+    "scan_packed_words": (_u64, [_u64, _u32]),
+    "scan_encode_host": (_st, [_vp, _u64, _u32, _u32, _vp]),
+    "scan_encode_device": (_st, [_vp, _u64, _u32, _u32, _vp, _vp]),
+    "scan_column_create": (_st, [_vp, _u64, _u32, _u32, _vp, ctypes.POINTER(_vp)]),
+    "scan_column_create_device": (_st, [_vp, _u64, _u32, _u32, _vp, ctypes.POINTER(_vp)]),
+    "scan_column_create_packed": (_st, [_vp, _u64, _u32, _u32, _vp, ctypes.POINTER(_vp)]),
+    "scan_column_upload_packed": (_st, [_vp, _vp, _vp]),
+    "scan_column_destroy": (_st, [_vp]),
+    "scan_column_info": (_st, [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u32), ctypes.POINTER(_u32),
+                               ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
+    "scan_zonemap_build": (_st, [_vp, _vp]),
+    "scan_run": (_st, [_vp, scan_pred, _st, _vp, ctypes.POINTER(scan_result)]),
+    "scan_run_async": (_st, [_vp, scan_pred, _st, _vp, _vp]),
+    "scan_column_status": (_st, [_vp, _vp]),
+    "scan_probe_read": (_st, [_vp, _u64, _vp, _vp]),
+    "scan_launch_shape": (_st, [_u32] + [ctypes.POINTER(_u32)] * 5),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the library (build it first with paper_2606_22423_gb300.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise ImportError(f"libgbscan.so not built at {path}; run paper_2606_22423_gb300.build")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _status_name(s: int) -> str:
+    return load().scan_status_string(s).decode()
+
+
+def _check(status: int):
+    if status != SCAN_OK:
+        raise ScanError(status, load().scan_last_error().decode())
+
+
+def _ptr(x) -> int | None:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):          # numpy array
+        return x.ctypes.data
+    raise TypeError(f"cannot take a pointer of {type(x)}")
+
+
+def _stream(s) -> int | None:
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+# ------------------------------------------------------------------ thin API
+def scan_packed_words(n: int, b: int) -> int:
+    return int(load().scan_packed_words(n, b))
+
+
+def scan_encode_host(values, b: int, base: int = 0, out=None):
+    """Encode a uint32 numpy array on the host; returns the packed uint32 array."""
+    import numpy as np
+
+    v = np.ascontiguousarray(values, dtype=np.uint32)
+    words = scan_packed_words(v.size, b)
+    if out is None:
+        out = np.zeros(max(words, 1), dtype=np.uint32)
+    _check(load().scan_encode_host(_ptr(v), v.size, b, base, _ptr(out)))
+    return out[:words]
+
+
+def scan_encode_device(dev_values, n: int, b: int, base: int, dev_out, stream=None):
+    _check(load().scan_encode_device(_ptr(dev_values), n, b, base, _ptr(dev_out), _stream(stream)))
+
+
+def scan_probe_read(dev_buf, nbytes: int, dev_out, stream=None):
+    _check(load().scan_probe_read(_ptr(dev_buf), nbytes, _stream(stream), _ptr(dev_out)))
+
+
+def scan_launch_shape(b: int) -> dict:
+    vals = [ctypes.c_uint32() for _ in range(5)]
+    _check(load().scan_launch_shape(b, *[ctypes.byref(v) for v in vals]))
+    keys = ["sms", "ctas", "warps_per_cta", "blocks_per_tile", "stages"]
+    return {k: int(v.value) for k, v in zip(keys, vals)}
+
+
+class Column:
+    """Owning handle of a scan_column."""
+
+    def __init__(self, handle: int, keepalive=None):
+        self._h = ctypes.c_void_p(handle)
+        self._keep = keepalive
+        n, b, base = _u64(), _u32(), _u32()
+        dp, dz = _vp(), _vp()
+        _check(load().scan_column_info(self._h, ctypes.byref(n), ctypes.byref(b), ctypes.byref(base),
+                                       ctypes.byref(dp), ctypes.byref(dz)))
+        self.n, self.b, self.base = int(n.value), int(b.value), int(base.value)
+        self.dev_packed = dp.value or 0
+
+    # constructors mirror scan_column_create{,_device,_packed}
+    @classmethod
+    def from_host(cls, values, b: int, base: int = 0, stream=None) -> "Column":
+        import numpy as np
+
+        v = np.ascontiguousarray(values, dtype=np.uint32)
+        h = _vp()
+        _check(load().scan_column_create(_ptr(v) if v.size else None, v.size, b, base, _stream(stream),
+                                         ctypes.byref(h)))
+        return cls(h.value)
+
+    @classmethod
+    def from_device(cls, dev_values, n: int, b: int, base: int = 0, stream=None) -> "Column":
+        h = _vp()
+        _check(load().scan_column_create_device(_ptr(dev_values), n, b, base, _stream(stream),
+                                                ctypes.byref(h)))
+        return cls(h.value)
+
+    @classmethod
+    def from_packed(cls, dev_packed, n: int, b: int, base: int = 0, stream=None) -> "Column":
+        h = _vp()
+        _check(load().scan_column_create_packed(_ptr(dev_packed), n, b, base, _stream(stream),
+                                                ctypes.byref(h)))
+        return cls(h.value, keepalive=dev_packed)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def upload_packed(self, host_packed, stream=None):
+        _check(load().scan_column_upload_packed(self._h, _ptr(host_packed), _stream(stream)))
+
+    def zonemap_build(self, stream=None):
+        _check(load().scan_zonemap_build(self._h, _stream(stream)))
+
+    def zonemap_ptr(self) -> int:
+        dz = _vp()
+        _check(load().scan_column_info(self._h, None, None, None, None, ctypes.byref(dz)))
+        return dz.value or 0
+
+    def run(self, lo: int, hi: int, strategy="branchfree", stream=None) -> scan_result:
+        st = STRATEGIES[strategy] if isinstance(strategy, str) else int(strategy)
+        out = scan_result()
+        _check(load().scan_run(self._h, scan_pred(lo, hi), st, _stream(stream), ctypes.byref(out)))
+        return out
+
+    def run_async(self, lo: int, hi: int, dev_out, strategy="branchfree", stream=None):
+        st = STRATEGIES[strategy] if isinstance(strategy, str) else int(strategy)
+        _check(load().scan_run_async(self._h, scan_pred(lo, hi), st, _stream(stream), _ptr(dev_out)))
+
+    def status(self, stream=None):
+        _check(load().scan_column_status(self._h, _stream(stream)))
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            _check(load().scan_column_destroy(self._h))
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,86 @@
+"""The C ABI without a GPU: the library loads, exports every function that
+include/gbscan.h declares, and its host-side logic (layout sizes, the host
+encoder, argument checks) agrees with the oracle."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from paper_2606_22423_gb300 import gbscan
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", h)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^[A-Za-z_][\w \*]*?\b(scan_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    return gbscan.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(lib, name), f"{name} declared but not exported"
+        assert name in gbscan.SIGNATURES, f"{name} has no binding"
+
+
+def test_packed_words(lib):
+    for n in [0, 1, 1023, 1024, 1025, 1 << 31]:
+        for b in [1, 7, 32]:
+            assert gbscan.scan_packed_words(n, b) == oracle.packed_words(n, b)
+    assert gbscan.scan_packed_words(5, 0) == 0 and gbscan.scan_packed_words(5, 33) == 0
+
+
+@pytest.mark.parametrize("b", range(1, 33))
+def test_host_encoder_is_byte_identical_to_the_oracle(lib, b):
+    max_base = (1 << 32) - (1 << b)
+    for n, base in [(1, 0), (1000, min(77, max_base)), (1024, max_base), (3 * 1024 + 5, 0),
+                    (70 * 1024 + 999, min(12345, max_base))]:
+        v = synth.uniform_values(synth.seed_for(80, b, n), n, b, base)
+        got = gbscan.scan_encode_host(v, b, base)
+        np.testing.assert_array_equal(got, oracle.pack(v, b, base))
+
+
+def test_host_encoder_rejects_bad_input(lib):
+    v = np.array([1, 2, 3, 400], dtype=np.uint32)
+    for b, base, why in [(8, 0, "outside"), (0, 0, "width"), (33, 0, "width"), (9, 2, "outside"),
+                         (32, 1, "width")]:
+        with pytest.raises(gbscan.ScanError) as e:
+            gbscan.scan_encode_host(v, b, base)
+        assert e.value.status == gbscan.SCAN_EINVAL
+        assert why in str(e.value)
+
+
+def test_status_strings(lib):
+    assert gbscan._status_name(gbscan.SCAN_ETIMEOUT) == "SCAN_ETIMEOUT"
+    assert gbscan._status_name(99) == "SCAN_UNKNOWN"
+
+
+def test_launch_shapes_fit_shared_memory(lib):
+    for b in range(1, 33):
+        # shape queries need no device for the per-width part
+        st = gbscan.load().scan_launch_shape
+        import ctypes
+
+        vals = [ctypes.c_uint32() for _ in range(5)]
+        assert st(b, None, None, *[ctypes.byref(v) for v in vals[2:]]) == gbscan.SCAN_OK
+        warps, tb, stages = (int(v.value) for v in vals[2:])
+        assert tb % 4 == 0 and tb >= 4
+        assert warps * stages * tb * 128 * b <= 227 * 1024
