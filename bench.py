@@ -245,6 +245,7 @@ def run_ours(args, world, rank, local):
     probe = torch.empty(1 << 30, dtype=torch.int32, device=dev)
     probe.fill_(7)
     chk = torch.zeros(1, dtype=torch.int64, device=dev)
+    torch.cuda.synchronize()
     with torch.cuda.stream(stream):
         best = 0.0
         for i in range(13):
@@ -261,15 +262,17 @@ def run_ours(args, world, rank, local):
 
     # ---- resident columns (device-side generation + device encoder)
     cols = {}
-    for b in WIDTHS:
-        v = synth.uniform_values_device(synth.seed_for(2, b), N_SWEEP, b, device=dev)
-        cols[b] = gbscan.Column.from_device(v, N_SWEEP, b, stream=stream)
-        del v
+    with torch.cuda.stream(stream):       # values are drawn and encoded on one stream
+        for b in WIDTHS:
+            v = synth.uniform_values_device(synth.seed_for(2, b), N_SWEEP, b, device=dev)
+            cols[b] = gbscan.Column.from_device(v, N_SWEEP, b, stream=stream)
+            del v
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
     preds = {(b, s): pred_for(b, s) for b in WIDTHS for s in SIGMAS}
     order = [(st, s, b) for st in STRATS for s in SIGMAS for b in WIDTHS]
     res = torch.zeros((len(order), 4), dtype=torch.int64, device=dev)
+    torch.cuda.synchronize()
     bytes_of = {b: N_SWEEP * b / 8 for b in WIDTHS}
     step_bytes = sum(bytes_of[b] for _, _, b in order)
 
