@@ -164,6 +164,37 @@ scan_status scan_run_async(scan_column *col, scan_pred pred, scan_strategy strat
  * column's kernels: SCAN_OK or SCAN_ETIMEOUT. */
 scan_status scan_column_status(scan_column *col, void *stream);
 
+/* ------------------------------------------------------ no allocation */
+
+/* The paper has no counterpart to this call; it is an integration aid.
+ * The same fused full scan as scan_run_async on a caller-owned packed buffer
+ * (scan_packed_words(n, b) words, 16-byte aligned), for callers that cannot
+ * allocate device memory when they scan: code running inside CUDA graph
+ * capture (cudaMalloc cannot be captured), latency-bound loops that must not
+ * take the allocator's implicit synchronisation, and engines that manage a
+ * fixed memory budget themselves.  It calls no cudaMalloc/cudaFree and no
+ * allocating library routine.  Its grid-reduction scratch is a statically
+ * sized device array of 16 KiB + 64 bytes inside this library (room for 1024
+ * CTAs, one per SM), held by every GPU that loads the library until exit; a
+ * GPU with more SMs than that is refused with SCAN_EINVAL.
+ *   - Outputs: *dev_out gets the 32-byte result, *dev_status gets 0 or error
+ *     bits (nonzero means a bounded device wait gave up and the result is not
+ *     valid); both are caller-owned device memory, written asynchronously.
+ *   - strategy: SCAN_AUTO / SCAN_BRANCHFREE or SCAN_BRANCHY; zone-skip
+ *     strategies need a zone map and are refused with SCAN_EINVAL.
+ *   - The first call on each device looks up the scratch array's address
+ *     (cudaGetSymbolAddress with that device current); make that first call
+ *     before any stream capture begins.
+ *   - Every call on a device shares the one scratch array and clears its
+ *     ticket at the start of the call: calls whose kernels overlap on the GPU
+ *     (different streams, no ordering between them) race and give wrong
+ *     results.  Order them on one stream or with events.
+ * Errors: SCAN_EINVAL for bad width/base, n > 2^31, NULL or misaligned
+ * pointers; SCAN_ECUDA if a launch or memset fails. */
+scan_status scan_run_packed_noalloc(const uint32_t *dev_packed, uint64_t n, uint32_t b,
+                                    uint32_t base, scan_pred pred, scan_strategy strategy,
+                                    void *stream, scan_result *dev_out, uint32_t *dev_status);
+
 /* --------------------------------------------------------------- probes */
 
 /* Read-only bandwidth probe (paper §3: beta is the empirical sequential-read

@@ -89,6 +89,9 @@ cudaError_t launch(int b, int op, const gb::ScanParams& p, int grid, cudaStream_
 
 }  // namespace
 
+// Lets other units of the library set the message scan_last_error() returns.
+void gb_set_last_error(const char* msg) { g_err = msg ? msg : ""; }
+
 namespace gb {
 // ----------------------------------------------------- zone-map filtering
 // Keeps block k iff max_k >= lo and min_k < hi (a block whose [min, max]

@@ -69,6 +69,7 @@ SIGNATURES = {
     "scan_column_status": (_st, [_vp, _vp]),
     "scan_probe_read": (_st, [_vp, _u64, _vp, _vp]),
     "scan_launch_shape": (_st, [_u32] + [ctypes.POINTER(_u32)] * 5),
+    "scan_run_packed_noalloc": (_st, [_vp, _u64, _u32, _u32, scan_pred, _st, _vp, _vp, _vp]),
 }
 
 _lib = None
@@ -141,6 +142,14 @@ def scan_encode_device(dev_values, n: int, b: int, base: int, dev_out, stream=No
 
 def scan_probe_read(dev_buf, nbytes: int, dev_out, stream=None):
     _check(load().scan_probe_read(_ptr(dev_buf), nbytes, _stream(stream), _ptr(dev_out)))
+
+
+def scan_run_packed_noalloc(dev_packed, n: int, b: int, base: int, lo: int, hi: int, dev_out,
+                            dev_status, strategy="branchfree", stream=None):
+    """Full scan without any device allocation (static scratch inside the library)."""
+    st = STRATEGIES[strategy] if isinstance(strategy, str) else int(strategy)
+    _check(load().scan_run_packed_noalloc(_ptr(dev_packed), n, b, base, scan_pred(lo, hi), st,
+                                          _stream(stream), _ptr(dev_out), _ptr(dev_status)))
 
 
 def scan_launch_shape(b: int) -> dict:
