@@ -1,0 +1,263 @@
+// Batched scan: thousands of columns of any width in one persistent launch.
+//
+// The host lays every column's 1024-value blocks out as tiles (the same
+// per-width tile size as the single-column scan, at most 8 KB) and numbers the
+// tiles of all columns consecutively.  Persistent warps pop chunks of
+// consecutive tile numbers from one atomic counter, so a warp usually stays on
+// one column for many tiles; each tile is fetched into the warp's slot ring by
+// bulk TMA copies and decoded by the width-specialised code of the
+// single-column scan, picked by a switch on the column's width.  Columns marked
+// for zone skipping test their blocks' (min, max) before the copy and fetch
+// only the surviving runs.  A warp keeps running (count, sum) totals while the
+// column does not change and adds them to the column's result with three
+// atomics when it does.  The frame of reference is applied per flush
+// (SUM_v = SUM_u + base*COUNT is linear).
+#pragma once
+#include "scan_kernels.cuh"
+
+namespace gb {
+
+enum : uint32_t { kColZone = 1u, kColEmpty = 2u };
+
+struct BatchCol {
+    const uint32_t* packed;  // lane-interleaved words
+    const uint2* zonemap;    // per-block (min, max) of decoded values, or null
+    uint64_t n;              // values
+    uint32_t b, base;
+    uint32_t tile_blocks;    // blocks per tile
+    uint32_t tile_begin;     // first tile number of this column in the launch
+    uint32_t lo, wm1;        // predicate in code space (width >= 1)
+    uint64_t zlo, zhi;       // predicate on decoded values, for zone tests
+    uint32_t flags;          // kColZone, kColEmpty
+    uint32_t out;            // result slot
+};
+
+struct BatchParams {
+    const BatchCol* cols;
+    uint32_t ncols;
+    uint32_t ntiles;
+    uint32_t chunk;                // tiles per atomic pop
+    uint32_t pad;
+    unsigned int* head;            // pop counter, zero before the launch
+    unsigned long long* results;   // per output slot: count, sum, blocks, 0
+    unsigned int* status;
+};
+
+constexpr int kBatchWarps = 8;
+constexpr int kBatchStages = 3;
+constexpr int kBatchSlot = 8 * 1024;
+constexpr int kBatchSmem = kBatchWarps * kBatchStages * (kBatchSlot + 8 + 16);
+
+struct SlotMeta {
+    uint32_t col;   // column index
+    uint32_t nk;    // blocks in the slot
+    uint32_t tail;  // 1 if the last block in the slot is the column's partial tail
+    uint32_t pad;
+};
+
+struct CountSum {
+    uint64_t cnt, sum;
+};
+
+template <int B, bool BRANCHY>
+__device__ __noinline__ CountSum batch_consume_b(const unsigned char* slot, const SlotMeta m,
+                                                 const BatchCol& c, int lane)
+{
+    uint64_t cnt = 0, sum = 0;
+    const Lanes L = make_lanes<B>(c.lo, c.wm1);
+    const uint32_t nfull = m.tail ? m.nk - 1u : m.nk;
+    scan_tile<B, BRANCHY>(slot, nfull, lane, L, c.lo, c.wm1, cnt, sum);
+    if (m.tail) {
+        const int q = lane % Geo<B>::kTpb;
+        agg_block_masked<B>(block_rows<B>(slot + nfull * (128u * B), q), c.lo, c.wm1, cnt, sum,
+                            lane < Geo<B>::kTpb, static_cast<uint32_t>(c.n & 1023u), q);
+    }
+    return CountSum{cnt, sum};
+}
+
+template <bool BRANCHY, int LO, int HI>
+__device__ __forceinline__ CountSum batch_consume_range(int b, const unsigned char* slot,
+                                                        const SlotMeta m, const BatchCol& c, int lane)
+{
+    if constexpr (LO > HI) {
+        return CountSum{0, 0};
+    } else {
+        if (b == LO) return batch_consume_b<LO, BRANCHY>(slot, m, c, lane);
+        return batch_consume_range<BRANCHY, LO + 1, HI>(b, slot, m, c, lane);
+    }
+}
+
+template <bool BRANCHY>
+__global__ void __launch_bounds__(kBatchWarps * 32, 1) k_scan_batch(const BatchParams P)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char* slots = smem + static_cast<size_t>(warp) * kBatchStages * kBatchSlot;
+    uint64_t* bars =
+        reinterpret_cast<uint64_t*>(smem + kBatchWarps * kBatchStages * kBatchSlot) + warp * kBatchStages;
+    SlotMeta* meta = reinterpret_cast<SlotMeta*>(smem + kBatchWarps * kBatchStages * (kBatchSlot + 8)) +
+                     warp * kBatchStages;
+    if (lane == 0) {
+        for (int s = 0; s < kBatchStages; ++s) mbar_init(&bars[s], 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+
+    // producer cursor (warp-uniform)
+    uint32_t t_next = 0, t_end = 0, col = 0;
+    bool exhausted = false;
+    uint32_t phase = 0;  // bit s: parity of slot s's next completion
+
+    // Next tile number, or false when the launch has no more work.
+    auto next_tile = [&](uint32_t& t) -> bool {
+        if (t_next >= t_end) {
+            if (exhausted) return false;
+            unsigned int start = 0;
+            if (lane == 0) start = atomicAdd(P.head, P.chunk);
+            start = __shfl_sync(kFull, start, 0);
+            if (start >= P.ntiles) {
+                exhausted = true;
+                return false;
+            }
+            t_next = start;
+            t_end = min(start + P.chunk, P.ntiles);
+            // locate the column by binary search over tile_begin
+            uint32_t lo = 0, hi = P.ncols - 1;
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi + 1) >> 1;
+                if (__ldg(&P.cols[mid].tile_begin) <= start) lo = mid;
+                else hi = mid - 1;
+            }
+            col = lo;
+        }
+        t = t_next++;
+        while (col + 1 < P.ncols && __ldg(&P.cols[col + 1].tile_begin) <= t) ++col;
+        return true;
+    };
+
+    // Fetch the next tile into slot s; false when there is none.
+    auto produce = [&](int s) -> bool {
+        uint32_t t;
+        if (!next_tile(t)) return false;
+        const BatchCol& c = P.cols[col];
+        const uint32_t bb = 128u * c.b;
+        const uint64_t nblocks = (c.n + 1023u) >> 10;
+        const uint64_t k0 = static_cast<uint64_t>(t - c.tile_begin) * c.tile_blocks;
+        const uint64_t left = nblocks - k0;
+        const uint32_t nb = left < c.tile_blocks ? static_cast<uint32_t>(left) : c.tile_blocks;
+        const bool has_tail = (c.n & 1023u) && (k0 + nb == nblocks);
+        uint64_t keep = (nb >= 64) ? ~0ull : ((1ull << nb) - 1ull);
+        if (c.flags & kColEmpty) {
+            keep = 0;
+        } else if (c.flags & kColZone) {
+            uint64_t km = 0;
+            for (uint32_t base_i = 0; base_i < nb; base_i += 32u) {
+                const uint32_t i = base_i + lane;
+                bool k = false;
+                if (i < nb) {
+                    const uint2 z = __ldg(&c.zonemap[k0 + i]);
+                    k = static_cast<uint64_t>(z.y) >= c.zlo && static_cast<uint64_t>(z.x) < c.zhi;
+                }
+                km |= static_cast<uint64_t>(__ballot_sync(kFull, k)) << base_i;
+            }
+            keep = km;
+        }
+        const uint32_t nk = static_cast<uint32_t>(__popcll(keep));
+        if (lane == 0) {
+            SlotMeta m;
+            m.col = col;
+            m.nk = nk;
+            m.tail = (has_tail && ((keep >> (nb - 1)) & 1ull)) ? 1u : 0u;
+            m.pad = 0;
+            meta[s] = m;
+            if (nk) {
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(&bars[s], nk * bb);
+                unsigned char* dst = slots + s * kBatchSlot;
+                uint64_t rem = keep;
+                uint32_t placed = 0;
+                while (rem) {
+                    const uint32_t first = static_cast<uint32_t>(__ffsll(static_cast<long long>(rem)) - 1);
+                    const uint64_t from = rem >> first;
+                    const uint32_t len = (~from == 0ull) ? (64u - first)
+                                                          : static_cast<uint32_t>(__ffsll(static_cast<long long>(~from)) - 1);
+                    bulk_g2s(dst + placed * bb, c.packed + (k0 + first) * 32u * c.b, len * bb, &bars[s]);
+                    placed += len;
+                    rem &= (len + first >= 64u) ? 0ull : (~0ull << (first + len));
+                }
+            }
+        }
+        __syncwarp();
+        return true;
+    };
+
+    int produced = 0;
+    for (int s = 0; s < kBatchStages; ++s) {
+        if (!produce(s)) break;
+        ++produced;
+    }
+
+    uint64_t cnt = 0, sum = 0, blocks = 0;
+    int cur = -1;
+    auto flush = [&]() {
+        uint64_t c2 = cnt, s2 = sum;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            c2 += __shfl_xor_sync(kFull, c2, o);
+            s2 += __shfl_xor_sync(kFull, s2, o);
+        }
+        if (lane == 0 && cur >= 0) {
+            const BatchCol& c = P.cols[cur];
+            unsigned long long* r = P.results + 4u * c.out;
+            if (c2) atomicAdd(&r[0], static_cast<unsigned long long>(c2));
+            if (c2) atomicAdd(&r[1], static_cast<unsigned long long>(s2 + static_cast<uint64_t>(c.base) * c2));
+            if (blocks) atomicAdd(&r[2], static_cast<unsigned long long>(blocks));
+        }
+        cnt = 0;
+        sum = 0;
+        blocks = 0;
+    };
+
+    bool failed = false;
+    int it = 0;
+#pragma unroll 1
+    for (; it < produced; ++it) {
+        const int s = it % kBatchStages;
+        const SlotMeta m = meta[s];
+        if (static_cast<int>(m.col) != cur) {
+            flush();
+            cur = static_cast<int>(m.col);
+        }
+        if (m.nk) {
+            const bool ok = mbar_wait(&bars[s], (phase >> s) & 1u, kWaitLimitNs);
+            if (!__all_sync(kFull, ok)) {
+                failed = true;
+                break;
+            }
+            phase ^= 1u << s;
+            const BatchCol& c = P.cols[m.col];
+            const CountSum r =
+                batch_consume_range<BRANCHY, 1, 32>(static_cast<int>(c.b), slots + s * kBatchSlot, m, c, lane);
+            cnt += r.cnt;
+            sum += r.sum;
+            blocks += m.nk;
+        }
+        __syncwarp();
+        if (produce(s)) ++produced;
+    }
+    if (failed) {
+        if (lane == 0) atomicOr(P.status, kErrTimeout);
+        // let this warp's copies in flight land before shared memory is released
+        for (int j = it; j < produced && j < it + kBatchStages; ++j) {
+            const int s = j % kBatchStages;
+            if (meta[s].nk) {
+                mbar_wait(&bars[s], (phase >> s) & 1u, kDrainLimitNs);
+                phase ^= 1u << s;
+            }
+        }
+    }
+    flush();
+}
+
+}  // namespace gb
+

@@ -149,6 +149,19 @@ struct scan_column {
     scan_result* host_result = nullptr;  // pinned staging, 48 bytes (result + status)
 };
 
+// Read-only view of a column for the batch planner (not part of the C ABI).
+bool gb_column_view(const scan_column* c, const uint32_t** packed, uint64_t* n, uint32_t* b,
+                    uint32_t* base, const uint2** zonemap)
+{
+    if (!c) return false;
+    *packed = c->packed;
+    *n = c->n;
+    *b = c->b;
+    *base = c->base;
+    *zonemap = c->zonemap_valid ? c->zonemap : nullptr;
+    return true;
+}
+
 // ---------------------------------------------------------------- encoders
 namespace {
 

@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "gb_ptx.cuh"
 
@@ -45,13 +46,31 @@ struct ScanParams {
 
 // Launch shape for width B: warps per CTA, pipeline depth, blocks per tile.
 template <int B>
+struct Shape;
+
+// ------------------------------------------------------------- geometry
+// Threads per block: a thread owns kLpt consecutive lanes and reads them as one
+// vector per row (16 bytes for b <= 16, 8 bytes above, where four blocks per
+// warp step would not fit an 8 KB slot); a warp step covers kLpt blocks.
+template <int B>
+struct Geo {
+    static constexpr int kLpt = B <= 16 ? 4 : 2;
+    static constexpr int kTpb = 32 / kLpt;
+    using Vec = typename std::conditional<kLpt == 4, uint4, uint2>::type;
+};
+
+// Launch shape for width B: 8 warps per CTA, each with kStages slots of up
+// to 8 KB; a tile is the largest multiple of the warp step (kLpt blocks) that
+// fits a slot.
+template <int B>
 struct Shape {
-    static constexpr int kWarps = B <= 16 ? 8 : 4;
+    static constexpr int kWarps = 8;
     static constexpr int kStages = 3;
     static constexpr int kBlockBytes = 128 * B;
-    static constexpr int kBudget = 192 * 1024;
-    static constexpr int kTbRaw = (kBudget / (kWarps * kStages * kBlockBytes)) & ~3;
-    static constexpr int kTB = kTbRaw < 4 ? 4 : (kTbRaw > 128 ? 128 : kTbRaw);
+    static constexpr int kSlotMax = 8 * 1024;
+    static constexpr int kStep = Geo<B>::kLpt;
+    static constexpr int kTbRaw = (kSlotMax / kBlockBytes) / kStep * kStep;
+    static constexpr int kTB = kTbRaw < kStep ? kStep : (kTbRaw > 128 ? 128 : kTbRaw);
     static constexpr int kTileBytes = kTB * kBlockBytes;
     static constexpr int kSlotBytes = kWarps * kStages * kTileBytes;
     static constexpr int kSmemBytes = kSlotBytes + kWarps * kStages * 8 + kWarps * kStages * 4;
@@ -64,10 +83,11 @@ __device__ __forceinline__ uint32_t lane_word(const uint4& v, int k)
 {
     return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
 }
+__device__ __forceinline__ uint32_t lane_word(const uint2& v, int k) { return k == 0 ? v.x : v.y; }
 
 // Code of row r for the thread's lane k (r, k compile-time after unrolling).
 template <int B>
-__device__ __forceinline__ uint32_t code_of(const uint4 (&W)[B], int r, int k)
+__device__ __forceinline__ uint32_t code_of(const typename Geo<B>::Vec (&W)[B], int r, int k)
 {
     const int bit = r * B;
     const int w0 = bit >> 5;
@@ -84,133 +104,210 @@ __device__ __forceinline__ uint32_t code_of(const uint4 (&W)[B], int r, int k)
 }
 
 template <int B>
-__device__ __forceinline__ void load_rows(uint4 (&W)[B], const uint4* rows)
+__device__ __forceinline__ void load_rows(typename Geo<B>::Vec (&W)[B], const typename Geo<B>::Vec* rows)
 {
 #pragma unroll
-    for (int w = 0; w < B; ++w) W[w] = rows[w * 8];
+    for (int w = 0; w < B; ++w) W[w] = rows[w * Geo<B>::kTpb];
 }
 
 // -------------------------------------------------------------- aggregate
-// One block, this thread's 4 lanes x 32 rows, every value valid.
-// Accumulators stay 32-bit inside the block:
-//   B <= 21: one word per lane packs (count << (B+5)) + sum;
-//   B <= 27: a 32-bit sum per lane plus a count;
-//   else   : a 64-bit sum.
-template <int B, bool BRANCHY>
-__device__ __forceinline__ void agg_block(const uint4* rows, uint32_t lo, uint32_t wm1,
-                                          uint64_t& cnt, uint64_t& sum)
+// Per value the decode needs an extraction, two compares and one add.  On
+// this SM the integer ALU pipe retires 16 lanes per cycle and IMAD (FMA-heavy
+// pipe) half that, so the work is split about 3:1: extraction (shift, funnel
+// shift, LOP3 mask) and both compares stay on the ALU, and each value costs
+// exactly one IMAD -- the accumulation (IMAD by an opaque 1, %nctaid.z, which
+// the compiler cannot fold) or, for a field at the top of its word, the
+// extraction itself (IMAD.HI by 2^B with the added constant folded in), in
+// which case the accumulation is an ALU add.
+struct Lanes {
+    uint32_t one;     // 1, opaque to the compiler
+    uint32_t pow2b;   // 2^B (B < 32)
+    uint32_t add;     // constant added to every extracted code (packed count bit)
+    uint32_t mask;    // 2^B - 1
+    uint32_t loi;     // lo' + add
+    uint32_t hii;     // hi' + add (B < 32)
+    uint32_t wm1;     // hi' - lo' - 1
+};
+
+__device__ __forceinline__ uint32_t opaque_one()
 {
-    uint4 W[B];
-    load_rows<B>(W, rows);
-    if constexpr (B <= 21) {
-        constexpr int kSB = B + 5;
-        constexpr uint32_t kInc = 1u << kSB;
-        uint32_t a[4] = {0u, 0u, 0u, 0u};
-#pragma unroll
-        for (int r = 0; r < 32; ++r) {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const uint32_t u = code_of<B>(W, r, k);
-                const bool m = (u - lo) <= wm1;
-                if constexpr (!BRANCHY) {
-                    if (m) a[k] += u + kInc;
-                } else {
-                    const uint32_t bal = __ballot_sync(kFull, m);
-                    if (bal == kFull) {
-                        a[k] += u + kInc;
-                    } else if (bal != 0u) {
-                        if (m) a[k] += u + kInc;
-                    }
-                }
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            cnt += a[k] >> kSB;
-            sum += a[k] & (kInc - 1u);
-        }
-    } else if constexpr (B <= 27) {
-        uint32_t c = 0u;
-        uint32_t s[4] = {0u, 0u, 0u, 0u};
-#pragma unroll
-        for (int r = 0; r < 32; ++r) {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const uint32_t u = code_of<B>(W, r, k);
-                const bool m = (u - lo) <= wm1;
-                if constexpr (!BRANCHY) {
-                    if (m) {
-                        c += 1u;
-                        s[k] += u;
-                    }
-                } else {
-                    const uint32_t bal = __ballot_sync(kFull, m);
-                    if (bal == kFull) {
-                        c += 1u;
-                        s[k] += u;
-                    } else if (bal != 0u) {
-                        if (m) {
-                            c += 1u;
-                            s[k] += u;
-                        }
-                    }
-                }
-            }
-        }
-        cnt += c;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) sum += s[k];
+    uint32_t v;
+    asm("mov.u32 %0, %%nctaid.z;" : "=r"(v));
+    return v;
+}
+
+template <int B>
+__device__ __forceinline__ Lanes make_lanes(uint32_t lo, uint32_t wm1)
+{
+    Lanes L;
+    L.one = opaque_one();
+    L.pow2b = B < 32 ? (L.one << (B & 31)) : 0u;
+    L.add = B <= 21 ? (1u << ((B + 5) & 31)) : 0u;
+    L.mask = B < 32 ? ((1u << (B & 31)) - 1u) : 0xffffffffu;
+    L.loi = lo + L.add;
+    L.hii = lo + wm1 + 1u + L.add;  // only used for B < 32, where it cannot wrap
+    L.wm1 = wm1;
+    return L;
+}
+
+// True when row r's field sits at the top of its word (extracted by IMAD.HI).
+template <int B>
+__device__ __forceinline__ bool top_field(int r)
+{
+    const int s = (r * B) & 31;
+    return B < 32 && s != 0 && s + B == 32;
+}
+
+// Code of row r, lane k, plus L.add (r, k compile-time after unrolling).
+template <int B>
+__device__ __forceinline__ uint32_t field_add(const typename Geo<B>::Vec (&W)[B], int r, int k,
+                                              const Lanes& L)
+{
+    const int bit = r * B;
+    const int w0 = bit >> 5;
+    const int s = bit & 31;
+    const uint32_t lw = lane_word(W[w0], k);
+    if constexpr (B == 32) {
+        return lw;
     } else {
-        uint32_t c = 0u;
-        uint64_t s = 0u;
-#pragma unroll
-        for (int r = 0; r < 32; ++r) {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const uint32_t u = code_of<B>(W, r, k);
-                const bool m = (u - lo) <= wm1;
-                if constexpr (!BRANCHY) {
-                    if (m) {
-                        c += 1u;
-                        s += u;
-                    }
-                } else {
-                    const uint32_t bal = __ballot_sync(kFull, m);
-                    if (bal == kFull) {
-                        c += 1u;
-                        s += u;
-                    } else if (bal != 0u) {
-                        if (m) {
-                            c += 1u;
-                            s += u;
-                        }
-                    }
-                }
-            }
+        uint32_t v;
+        if (top_field<B>(r)) {  // hi32(w * 2^B) + add = (w >> s) + add
+            asm("mad.hi.u32 %0, %1, %2, %3;" : "=r"(v) : "r"(lw), "r"(L.pow2b), "r"(L.add));
+            return v;
         }
-        cnt += c;
-        sum += s;
+        uint32_t x;
+        if (s + B <= 32) {
+            x = lw >> s;
+        } else {
+            const int w1 = (w0 + 1 < B) ? w0 + 1 : w0;
+            x = __funnelshift_r(lw, lane_word(W[w1], k), s);
+        }
+        asm("lop3.b32 %0, %1, %2, %3, 0xEA;" : "=r"(v) : "r"(x), "r"(L.mask), "r"(L.add));  // (x & mask) | add
+        return v;
     }
 }
 
-// Same with a validity mask: value (r, lane 4q+k) counts iff `ok` and its
-// index in the block, 32r + 4q + k, is below `limit`.  Used for the last
-// partial warp step of a tile and for the zero-padded tail block.
+// packed accumulator: a += v + add when lo <= v < hi (compares on the ALU)
+__device__ __forceinline__ void acc0_imad(uint32_t& a, uint32_t ui, const Lanes& L)
+{
+    asm("{\n\t.reg .pred p;\n\t"
+        "setp.ge.u32 p, %1, %2;\n\t"
+        "setp.lt.and.u32 p, %1, %3, p;\n\t"
+        "@p mad.lo.u32 %0, %1, %4, %0;\n\t}"
+        : "+r"(a) : "r"(ui), "r"(L.loi), "r"(L.hii), "r"(L.one));
+}
+__device__ __forceinline__ void acc0_alu(uint32_t& a, uint32_t ui, const Lanes& L)
+{
+    asm("{\n\t.reg .pred p;\n\t"
+        "setp.ge.u32 p, %1, %2;\n\t"
+        "setp.lt.and.u32 p, %1, %3, p;\n\t"
+        "@p add.u32 %0, %0, %1;\n\t}"
+        : "+r"(a) : "r"(ui), "r"(L.loi), "r"(L.hii));
+}
+// 32-bit sum + count
+__device__ __forceinline__ void acc1_imad(uint32_t& c, uint32_t& a, uint32_t ui, const Lanes& L)
+{
+    asm("{\n\t.reg .pred p;\n\t"
+        "setp.ge.u32 p, %2, %3;\n\t"
+        "setp.lt.and.u32 p, %2, %4, p;\n\t"
+        "@p add.u32 %0, %0, 1;\n\t"
+        "@p mad.lo.u32 %1, %2, %5, %1;\n\t}"
+        : "+r"(c), "+r"(a) : "r"(ui), "r"(L.loi), "r"(L.hii), "r"(L.one));
+}
+__device__ __forceinline__ void acc1_alu(uint32_t& c, uint32_t& a, uint32_t ui, const Lanes& L)
+{
+    asm("{\n\t.reg .pred p;\n\t"
+        "setp.ge.u32 p, %2, %3;\n\t"
+        "setp.lt.and.u32 p, %2, %4, p;\n\t"
+        "@p add.u32 %0, %0, 1;\n\t"
+        "@p add.u32 %1, %1, %2;\n\t}"
+        : "+r"(c), "+r"(a) : "r"(ui), "r"(L.loi), "r"(L.hii));
+}
+
+// One block, this thread's 4 lanes x 32 rows, every value valid.
+// Accumulators stay 32-bit inside the block:
+//   B <= 21: one word per lane packs (count << (B+5)) + sum  (mode 0);
+//   B <= 27: a 32-bit sum per lane plus a count              (mode 1);
+//   else   : a 64-bit sum plus a count                       (mode 2).
+// BRANCHY adds a warp vote per 32-value group (one value per thread) and
+// skips the aggregation when no lane of the warp matches.
+template <int B, bool BRANCHY>
+__device__ __forceinline__ void agg_block(const typename Geo<B>::Vec* rows, const Lanes& L,
+                                          uint64_t& cnt, uint64_t& sum)
+{
+    constexpr int kMode = B <= 21 ? 0 : (B <= 27 ? 1 : 2);
+    constexpr int kLpt = Geo<B>::kLpt;
+    typename Geo<B>::Vec W[B];
+    load_rows<B>(W, rows);
+    uint32_t a[kLpt] = {};
+    uint32_t c = 0u;
+    uint64_t s64 = 0u;
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+#pragma unroll
+        for (int k = 0; k < kLpt; ++k) {
+            const uint32_t ui = field_add<B>(W, r, k, L);
+            if constexpr (BRANCHY) {
+                const bool m = (ui - L.loi) <= L.wm1;
+                if (__ballot_sync(kFull, m) != 0u) {
+                    if (m) {
+                        if constexpr (kMode != 0) c += 1u;
+                        if constexpr (kMode == 2) s64 += ui;
+                        else a[k] += ui;
+                    }
+                }
+            } else if constexpr (kMode == 0) {
+                if (top_field<B>(r)) acc0_alu(a[k], ui, L);
+                else acc0_imad(a[k], ui, L);
+            } else if constexpr (kMode == 1) {
+                if (top_field<B>(r)) acc1_alu(c, a[k], ui, L);
+                else acc1_imad(c, a[k], ui, L);
+            } else {
+                // 64-bit sums: plain compare and add
+                if ((ui - L.loi) <= L.wm1) {
+                    c += 1u;
+                    s64 += ui;
+                }
+            }
+        }
+    }
+    if constexpr (kMode == 0) {
+        constexpr int kSB = (B + 5) & 31;
+        constexpr uint32_t kSumMask = (1u << kSB) - 1u;
+#pragma unroll
+        for (int k = 0; k < kLpt; ++k) {
+            cnt += a[k] >> kSB;
+            sum += a[k] & kSumMask;
+        }
+    } else if constexpr (kMode == 1) {
+        cnt += c;
+#pragma unroll
+        for (int k = 0; k < kLpt; ++k) sum += a[k];
+    } else {
+        cnt += c;
+        sum += s64;
+    }
+}
+
+// Same with a validity mask: value (r, lane kLpt*q + k) counts iff `ok` and
+// its index in the block, 32r + kLpt*q + k, is below `limit`.  Used for the
+// last partial warp step of a tile and for the zero-padded tail block.
 template <int B>
-__device__ __forceinline__ void agg_block_masked(const uint4* rows, uint32_t lo, uint32_t wm1,
-                                                 uint64_t& cnt, uint64_t& sum, bool ok,
+__device__ __forceinline__ void agg_block_masked(const typename Geo<B>::Vec* rows, uint32_t lo,
+                                                 uint32_t wm1, uint64_t& cnt, uint64_t& sum, bool ok,
                                                  uint32_t limit, int q)
 {
-    uint4 W[B];
+    constexpr int kLpt = Geo<B>::kLpt;
+    typename Geo<B>::Vec W[B];
     load_rows<B>(W, rows);
     uint32_t c = 0u;
     uint64_t s = 0u;
 #pragma unroll
     for (int r = 0; r < 32; ++r) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < kLpt; ++k) {
             const uint32_t u = code_of<B>(W, r, k);
-            const uint32_t j = 32u * r + 4u * q + k;
+            const uint32_t j = 32u * r + static_cast<uint32_t>(kLpt * q + k);
             if (ok && j < limit && (u - lo) <= wm1) {
                 c += 1u;
                 s += u;
@@ -223,17 +320,18 @@ __device__ __forceinline__ void agg_block_masked(const uint4* rows, uint32_t lo,
 
 // (min, max) of codes of one block over valid positions.
 template <int B>
-__device__ __forceinline__ void minmax_block(const uint4* rows, uint32_t limit, int q,
+__device__ __forceinline__ void minmax_block(const typename Geo<B>::Vec* rows, uint32_t limit, int q,
                                              uint32_t& mn, uint32_t& mx)
 {
-    uint4 W[B];
+    constexpr int kLpt = Geo<B>::kLpt;
+    typename Geo<B>::Vec W[B];
     load_rows<B>(W, rows);
 #pragma unroll
     for (int r = 0; r < 32; ++r) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < kLpt; ++k) {
             const uint32_t u = code_of<B>(W, r, k);
-            const uint32_t j = 32u * r + 4u * q + k;
+            const uint32_t j = 32u * r + static_cast<uint32_t>(kLpt * q + k);
             if (j < limit) {
                 mn = min(mn, u);
                 mx = max(mx, u);
@@ -242,23 +340,30 @@ __device__ __forceinline__ void minmax_block(const uint4* rows, uint32_t limit, 
     }
 }
 
+template <int B>
+__device__ __forceinline__ const typename Geo<B>::Vec* block_rows(const unsigned char* blk, int q)
+{
+    return reinterpret_cast<const typename Geo<B>::Vec*>(blk) + q;
+}
+
 // All `nb` blocks of a staged tile (blocks are contiguous in the slot).
 template <int B, bool BRANCHY>
 __device__ __forceinline__ void scan_tile(const unsigned char* tile, uint32_t nb, int lane,
-                                          uint32_t lo, uint32_t wm1, uint64_t& cnt, uint64_t& sum)
+                                          const Lanes& L, uint32_t lo, uint32_t wm1, uint64_t& cnt,
+                                          uint64_t& sum)
 {
     constexpr uint32_t kBB = 128u * B;
-    const int q = lane & 7;
-    const uint32_t sub = static_cast<uint32_t>(lane >> 3);
+    constexpr uint32_t kStep = Geo<B>::kLpt;          // blocks per warp step
+    const int q = lane % Geo<B>::kTpb;
+    const uint32_t sub = static_cast<uint32_t>(lane / Geo<B>::kTpb);
     uint32_t g = 0;
 #pragma unroll 1
-    for (; g + 4u <= nb; g += 4u)
-        agg_block<B, BRANCHY>(reinterpret_cast<const uint4*>(tile + (g + sub) * kBB) + q, lo, wm1,
-                              cnt, sum);
+    for (; g + kStep <= nb; g += kStep)
+        agg_block<B, BRANCHY>(block_rows<B>(tile + (g + sub) * kBB, q), L, cnt, sum);
     if (g < nb) {
         const bool ok = g + sub < nb;
-        agg_block_masked<B>(reinterpret_cast<const uint4*>(tile + (ok ? g + sub : g) * kBB) + q, lo,
-                            wm1, cnt, sum, ok, 1024u, q);
+        agg_block_masked<B>(block_rows<B>(tile + (ok ? g + sub : g) * kBB, q), lo, wm1, cnt, sum, ok,
+                            1024u, q);
     }
 }
 
@@ -343,9 +448,9 @@ __device__ __forceinline__ void scan_tail(const ScanParams& p, int lane, uint64_
 {
     const uint64_t tb = p.n >> 10;
     const uint32_t rem = static_cast<uint32_t>(p.n & 1023u);
-    const int q = lane & 7;
-    const bool ok = (lane >> 3) == 0;
-    const uint4* rows = reinterpret_cast<const uint4*>(p.packed + tb * 32u * B) + q;
+    const int q = lane % Geo<B>::kTpb;
+    const bool ok = lane < Geo<B>::kTpb;
+    const auto* rows = block_rows<B>(reinterpret_cast<const unsigned char*>(p.packed + tb * 32u * B), q);
     agg_block_masked<B>(rows, p.lo, p.wm1, cnt, sum, ok, rem, q);
 }
 
@@ -385,6 +490,7 @@ __global__ void __launch_bounds__(Shape<B>::kWarps * 32, 1) k_scan_full(const Sc
         }
     }
 
+    const Lanes L = make_lanes<B>(p.lo, p.wm1);
     uint64_t cnt = 0, sum = 0;
     uint32_t it = 0;
     bool failed = false;
@@ -399,7 +505,7 @@ __global__ void __launch_bounds__(Shape<B>::kWarps * 32, 1) k_scan_full(const Sc
         }
         const uint64_t left = full_blocks - t * S::kTB;
         const uint32_t nb = left < S::kTB ? static_cast<uint32_t>(left) : S::kTB;
-        scan_tile<B, BRANCHY>(slots + s * S::kTileBytes, nb, lane, p.lo, p.wm1, cnt, sum);
+        scan_tile<B, BRANCHY>(slots + s * S::kTileBytes, nb, lane, L, p.lo, p.wm1, cnt, sum);
         __syncwarp();
         const uint64_t tn = t + static_cast<uint64_t>(S::kStages) * GW;
         if (lane == 0 && tn < ntiles) {
@@ -428,8 +534,8 @@ __global__ void __launch_bounds__(Shape<B>::kWarps * 32, 1) k_zonemap_build(cons
     using S = Shape<B>;
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int q = lane & 7;
-    const uint32_t sub = static_cast<uint32_t>(lane >> 3);
+    const int q = lane % Geo<B>::kTpb;
+    const uint32_t sub = static_cast<uint32_t>(lane / Geo<B>::kTpb);
     unsigned char* slots = smem + static_cast<size_t>(warp) * S::kStages * S::kTileBytes;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S::kSlotBytes) + warp * S::kStages;
 
@@ -459,7 +565,7 @@ __global__ void __launch_bounds__(Shape<B>::kWarps * 32, 1) k_zonemap_build(cons
     }
     auto emit = [&](uint64_t blk, bool ok, uint32_t mn, uint32_t mx) {
 #pragma unroll
-        for (int o = 1; o < 8; o <<= 1) {
+        for (int o = 1; o < Geo<B>::kTpb; o <<= 1) {
             mn = min(mn, __shfl_xor_sync(kFull, mn, o));
             mx = max(mx, __shfl_xor_sync(kFull, mx, o));
         }
@@ -481,12 +587,10 @@ __global__ void __launch_bounds__(Shape<B>::kWarps * 32, 1) k_zonemap_build(cons
         const uint32_t nb = left < S::kTB ? static_cast<uint32_t>(left) : S::kTB;
         const unsigned char* tile = slots + s * S::kTileBytes;
 #pragma unroll 1
-        for (uint32_t g = 0; g < nb; g += 4u) {
+        for (uint32_t g = 0; g < nb; g += static_cast<uint32_t>(Geo<B>::kLpt)) {
             const bool ok = g + sub < nb;
             uint32_t mn = 0xffffffffu, mx = 0u;
-            minmax_block<B>(
-                reinterpret_cast<const uint4*>(tile + (ok ? g + sub : g) * (128u * B)) + q, 1024u,
-                q, mn, mx);
+            minmax_block<B>(block_rows<B>(tile + (ok ? g + sub : g) * (128u * B), q), 1024u, q, mn, mx);
             emit(fb + g + sub, ok, mn, mx);
         }
         __syncwarp();
@@ -507,7 +611,8 @@ __global__ void __launch_bounds__(Shape<B>::kWarps * 32, 1) k_zonemap_build(cons
     }
     if ((p.n & 1023u) && gw == GW - 1) {
         const uint32_t rem = static_cast<uint32_t>(p.n & 1023u);
-        const uint4* rows = reinterpret_cast<const uint4*>(p.packed + full_blocks * 32u * B) + q;
+        const auto* rows =
+            block_rows<B>(reinterpret_cast<const unsigned char*>(p.packed + full_blocks * 32u * B), q);
         uint32_t mn = 0xffffffffu, mx = 0u;
         minmax_block<B>(rows, sub == 0 ? rem : 0u, q, mn, mx);
         emit(full_blocks, sub == 0, mn, mx);
@@ -585,6 +690,7 @@ __global__ void __launch_bounds__(Shape<B>::kWarps * 32, 1) k_scan_queue(const S
     }
     __syncwarp();
 
+    const Lanes L = make_lanes<B>(p.lo, p.wm1);
     uint64_t cnt = 0, sum = 0;
     uint32_t it = 0;
     bool failed = false;
@@ -598,7 +704,7 @@ __global__ void __launch_bounds__(Shape<B>::kWarps * 32, 1) k_scan_queue(const S
             failed = true;
             break;
         }
-        scan_tile<B, BRANCHY>(slots + s * S::kTileBytes, nb, lane, p.lo, p.wm1, cnt, sum);
+        scan_tile<B, BRANCHY>(slots + s * S::kTileBytes, nb, lane, L, p.lo, p.wm1, cnt, sum);
         __syncwarp();
         const uint32_t nn = grab(s);
         if (lane == 0) slot_n[s] = nn;

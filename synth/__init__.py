@@ -101,3 +101,27 @@ def clustered_values_device(seed: int, n: int, b: int, p: float, base: int = 0, 
     if base:
         u += base
     return _to_u32_bits(u)
+
+
+# ------------------------------------------------------------ many columns
+def batch_spec(seed: int, ncols: int = 4096, total: int = 1 << 31, len_lo: int = 1 << 10,
+               len_hi: int = 1 << 26):
+    """Per-column (n, b, p, sigma) for the batched workload.
+
+    Lengths are log-uniform in [len_lo, len_hi], then every length is scaled
+    by total / sum (floor, at least 1) so the batch holds about `total`
+    values while keeping the log-uniform shape; b is uniform in 1..32; half
+    the columns are uniform (p = None), half sorted with a displaced fraction
+    p drawn from {0, 0.01, 0.1}; sigma is log-uniform in [1e-4, 1].
+    """
+    rng = np.random.default_rng(seed)
+    lens = log_uniform(rng, len_lo, len_hi, size=ncols)
+    lens = np.maximum(1, np.floor(lens * (total / lens.sum()))).astype(np.int64)
+    bs = rng.integers(1, 33, size=ncols)
+    sorted_mask = rng.random(ncols) < 0.5
+    ps = rng.choice([0.0, 0.01, 0.1], size=ncols)
+    sig = log_uniform(rng, 1e-4, 1.0, size=ncols)
+    out = []
+    for i in range(ncols):
+        out.append((int(lens[i]), int(bs[i]), float(ps[i]) if sorted_mask[i] else None, float(sig[i])))
+    return out

@@ -1,0 +1,104 @@
+"""Batched scan parity: one persistent launch over many columns of mixed
+width, length, order and strategy must give, column by column, exactly the
+oracle's COUNT/SUM (and the single-column scan's blocks-read count)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from paper_2606_22423_gb300 import gbscan
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+ALL = ["branchfree", "branchy", "zone_bf", "zone_br"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    torch.cuda.init()
+    return gbscan.load()
+
+
+def _make_columns(ncols, seed, max_len=40_000):
+    rng = np.random.default_rng(seed)
+    cols, vals, meta = [], [], []
+    for i in range(ncols):
+        b = int(rng.integers(1, 33))
+        n = int(rng.integers(0, max_len)) if i % 7 else int(rng.integers(1, 3000))
+        base = 0 if b == 32 else int(rng.integers(0, min(1 << 20, (1 << 32) - (1 << b)) + 1))
+        s = synth.seed_for(60, i, seed)
+        v = (synth.uniform_values(s, n, b, base) if i % 2 else
+             synth.clustered_values(s, n, b, [0.0, 0.01, 0.1][i % 3], base))
+        c = gbscan.Column.from_host(v, b, base)
+        c.zonemap_build()
+        cols.append(c)
+        vals.append(v)
+        meta.append((b, base))
+    return cols, vals, meta
+
+
+def _preds(meta, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i, (b, base) in enumerate(meta):
+        if i % 11 == 3:
+            out.append((base + 5, base + 5))                       # empty
+        elif i % 13 == 4:
+            out.append((base - 1, base + (1 << b) + 1))            # full domain
+        else:
+            sigma = float(synth.log_uniform(rng, 1e-4, 1.0))
+            out.append(synth.pick_range(int(rng.integers(1 << 30)), b, sigma, base))
+    return out
+
+
+@pytest.mark.parametrize("mix", ["branchfree", "mixed"])
+def test_batch_equals_oracle_and_single_column(mix):
+    cols, vals, meta = _make_columns(96, 1)
+    strategies = ["branchfree"] * len(cols) if mix == "branchfree" else [ALL[i % 4] for i in range(len(cols))]
+    bt = gbscan.Batch(cols, strategies)
+    for rep in range(3):                                   # graph replays with new predicates
+        preds = _preds(meta, 10 + rep)
+        got = bt.run(preds)
+        for i, ((lo, hi), v) in enumerate(zip(preds, vals)):
+            assert got[i].pair() == oracle.scan_values(v, lo, hi), (i, meta[i], strategies[i])
+            single = cols[i].run(lo, hi, strategies[i])
+            assert got[i].blocks_scanned == single.blocks_scanned, (i, strategies[i])
+    bt.close()
+    for c in cols:
+        c.close()
+
+
+def test_batch_pop_sizes_and_one_shot():
+    cols, vals, meta = _make_columns(40, 2, max_len=300_000)
+    preds = _preds(meta, 5)
+    want = [oracle.scan_values(v, lo, hi) for v, (lo, hi) in zip(vals, preds)]
+    for pop in [1, 3, 64]:
+        bt = gbscan.Batch(cols, None, tiles_per_pop=pop)
+        assert [r.pair() for r in bt.run(preds)] == want
+        bt.close()
+    assert [r.pair() for r in gbscan.scan_batch_run(cols, preds)] == want
+    for c in cols:
+        c.close()
+
+
+def test_batch_device_results_and_zone_requirement():
+    cols, vals, meta = _make_columns(10, 3)
+    preds = _preds(meta, 6)
+    bt = gbscan.Batch(cols, ["zone_bf"] * 10)
+    out = torch.zeros((10, 4), dtype=torch.int64, device="cuda")
+    bt.run(preds, dev_out=out, host=False)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    for i, (v, (lo, hi)) in enumerate(zip(vals, preds)):
+        assert (int(got[i, 0]), int(got[i, 1])) == oracle.scan_values(v, lo, hi)
+    bt.close()
+    plain = gbscan.Column.from_host(vals[0], meta[0][0], meta[0][1])
+    with pytest.raises(gbscan.ScanError):
+        gbscan.Batch([plain], ["zone_bf"])
+    plain.close()
+    for c in cols:
+        c.close()

@@ -82,5 +82,7 @@ def test_launch_shapes_fit_shared_memory(lib):
         vals = [ctypes.c_uint32() for _ in range(5)]
         assert st(b, None, None, *[ctypes.byref(v) for v in vals[2:]]) == gbscan.SCAN_OK
         warps, tb, stages = (int(v.value) for v in vals[2:])
-        assert tb % 4 == 0 and tb >= 4
+        step = 4 if b <= 16 else 2          # blocks per warp step (lanes per thread)
+        assert tb % step == 0 and tb >= step
+        assert tb * 128 * b <= 8 * 1024      # a tile fits one 8 KB slot
         assert warps * stages * tb * 128 * b <= 227 * 1024
