@@ -424,6 +424,12 @@ def run_ours(args, world, rank, local):
 
     for c in cols.values():
         c.close()
+    torch.cuda.empty_cache()
+    tdec = [law["branchfree"]["t_dec_gvals"], law["branchy"]["t_dec_gvals"],
+            law["branchfree"]["t_dec_gvals"], law["branchy"]["t_dec_gvals"]]
+    batched = None if args.no_batch else run_batched(args, dev, stream, gbscan, beta_read, tdec)
+    torch.cuda.empty_cache()
+    serving = None if args.no_serve else run_serving(args, dev, stream, gbscan)
 
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
@@ -438,6 +444,8 @@ def run_ours(args, world, rank, local):
         "law": law,
         "per_b": per_b,
         "branch_crossover": branch,
+        "batched": batched,
+        "serving": serving,
         "realised_sigma": realised,
         "e2e": e2e,
         "cpu_baseline": cpu,
@@ -447,6 +455,219 @@ def run_ours(args, world, rank, local):
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+BATCH_WORKLOAD = ("batched: 4096 columns, lengths log-uniform in [2^10, 2^26] scaled to 2^31 values in "
+                  "total, b uniform in 1..32, half uniform / half sorted with p in {0, 0.01, 0.1}, sigma "
+                  "log-uniform in [1e-4, 1]")
+
+
+def run_batched(args, dev, stream, gbscan, beta_gbs, t_dec_gvals):
+    """4096-column batch: one planned graph launch vs one plain launch per column.
+
+    Plans compared (results must be identical): fixed branch-free full scan,
+    the bandwidth law per column (fallback), and the trained planner network.
+    """
+    import torch
+
+    from paper_2606_22423_gb300 import planner as plmod
+
+    spec = synth.batch_spec(synth.seed_for(4))
+    cols, preds = [], []
+    with torch.cuda.stream(stream):
+        for i, (n, b, p, sigma) in enumerate(spec):
+            seed = synth.seed_for(4, i)
+            v = (synth.uniform_values_device(seed, n, b, device=dev) if p is None
+                 else synth.clustered_values_device(seed, n, b, p, device=dev))
+            c = gbscan.Column.from_device(v, n, b, stream=stream)
+            c.zonemap_build(stream)
+            cols.append(c)
+            preds.append(synth.pick_range(synth.seed_for(4, i, 1), b, sigma))
+    torch.cuda.synchronize()
+    total_values = sum(x[0] for x in spec)
+    total_bytes = sum(gbscan.scan_packed_words(x[0], x[1]) * 4 for x in spec)
+    ncols = len(cols)
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    def time_calls(fn, reps):
+        ts = []
+        for _ in range(reps):
+            e0, e1 = ev(), ev()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    # per-column plain launches (branch-free full scan), results in device memory
+    res_pc = torch.zeros((ncols, 4), dtype=torch.int64, device=dev)
+
+    def per_column():
+        for i, c in enumerate(cols):
+            c.run_async(preds[i][0], preds[i][1], res_pc[i], "branchfree", stream)
+
+    per_column()
+    torch.cuda.synchronize()
+    ms_loop = time_calls(per_column, 3)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        per_column()
+    with torch.cuda.stream(stream):           # replay on the stream the events time
+        g.replay()
+        torch.cuda.synchronize()
+        ms_graph = time_calls(g.replay, 5)
+    want = res_pc.cpu().numpy()
+
+    out = {}
+    # planner: trained on harness timings of separate training columns, on the GPU
+    t0 = time.perf_counter()
+    tcols, tpreds = plmod.training_columns(seed=11, count=120, stream=stream)
+    X, T = plmod.collect(tcols, tpreds, stream, reps=3)
+    for c in tcols:
+        c.close()
+    net = gbscan.Planner(4, seed=5)
+    hist = plmod.train(net, X, T, steps=1500, lr=3e-3, stream=stream)
+    train_s = time.perf_counter() - t0
+    probe = gbscan.Batch(cols)
+    feats = torch.zeros((ncols, 4), dtype=torch.float32, device=dev)
+    probe.features(preds, feats, stream)
+    torch.cuda.synchronize()
+    law_plan = plmod.choose_law(probe, feats, beta_gbs, t_dec_gvals, stream)
+    probe.close()
+    mlp_plan = plmod.choose(net, feats, stream)
+    net.close()
+    plans = {"branchfree": ["branchfree"] * ncols, "law": law_plan, "planned_mlp": mlp_plan}
+    res_b = torch.zeros((ncols, 4), dtype=torch.int64, device=dev)
+    parr = gbscan.Batch.pred_array(preds)      # marshalled once, outside the timed region
+    for name, strategies in plans.items():
+        bt = gbscan.Batch(cols, strategies)
+        bt.run(parr, stream=stream, dev_out=res_b, host=False)
+        torch.cuda.synchronize()
+        got = res_b.cpu().numpy()
+        exact = bool((got[:, :2] == want[:, :2]).all())
+        ms = time_calls(lambda: bt.run(parr, stream=stream, dev_out=res_b, host=False), 7)
+        mix = {k: strategies.count(k) for k in plmod.STRATEGIES if strategies.count(k)}
+        out[name] = {"ms": round(ms, 4), "exact": exact, "strategy_mix": mix,
+                     "speedup_vs_per_column_graph": round(ms_graph / ms, 2),
+                     "speedup_vs_per_column_loop": round(ms_loop / ms, 2),
+                     "gbs": round(total_bytes / (ms * 1e-3) / 1e9, 1),
+                     "blocks_scanned": int(got[:, 2].sum())}
+        bt.close()
+    for c in cols:
+        c.close()
+    return {"workload": BATCH_WORKLOAD, "ncols": ncols, "values": total_values, "packed_bytes": total_bytes,
+            "ms_per_column_graph": round(ms_graph, 4), "ms_per_column_loop": round(ms_loop, 4),
+            "per_column_launches": ncols, "plans": out,
+            "planner": {"training_columns": 120, "labels": "log ms of each strategy as a one-entry batch",
+                        "steps": 1500, "loss_first": round(hist[0], 4), "loss_last": round(hist[-1], 4),
+                        "train_and_label_s": round(train_s, 1)}}
+
+
+SERVE_WORKLOAD = ("serving: device-resident table of 64 columns x 2^27 values, b = {4,8,12,16,24,32}[c mod 6], "
+                  "even columns sorted, odd shuffled; Poisson arrivals; each query 1-8 distinct columns with "
+                  "range predicates, sigma log-uniform in [1e-4, 1]; COUNT + SUM per column")
+
+
+def run_serving(args, dev, stream, gbscan):
+    """Continuous-batching server vs serial per-query launches (config 5)."""
+    import threading
+
+    import torch
+
+    widths = [4, 8, 12, 16, 24, 32]
+    n = 1 << 27
+    cols = []
+    with torch.cuda.stream(stream):
+        for c in range(64):
+            b = widths[c % 6]
+            seed = synth.seed_for(5, c)
+            v = (synth.clustered_values_device(seed, n, b, 0.0, device=dev) if c % 2 == 0
+                 else synth.uniform_values_device(seed, n, b, device=dev))
+            col = gbscan.Column.from_device(v, n, b, stream=stream)
+            col.zonemap_build(stream)
+            cols.append(col)
+            del v
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    rng = np.random.default_rng(synth.seed_for(5, 0, 9))
+
+    def make_query():
+        k = int(rng.integers(1, 9))
+        ids = [int(x) for x in rng.choice(64, size=k, replace=False)]
+        preds = [synth.pick_range(int(rng.integers(1 << 30)), cols[i].b, float(synth.log_uniform(rng, 1e-4, 1.0)))
+                 for i in ids]
+        return ids, preds
+
+    def alone(q):
+        ids, preds = q
+        return [cols[c].run(lo, hi, "zone_bf", stream).pair() for c, (lo, hi) in zip(ids, preds)]
+
+    # serial per-query launches: one query at a time, one zone-skip scan per column
+    serial = [make_query() for _ in range(300)]
+    alone(serial[0])
+    lat = []
+    t0 = time.perf_counter()
+    for q in serial:
+        a = time.perf_counter()
+        alone(q)
+        lat.append((time.perf_counter() - a) * 1e6)
+    serial_s = time.perf_counter() - t0
+    serial_qps = len(serial) / serial_s
+    out = {"workload": SERVE_WORKLOAD, "serial": {"queries": len(serial), "qps": round(serial_qps, 1),
+                                                  "p50_us": round(float(np.percentile(lat, 50)), 1),
+                                                  "p99_us": round(float(np.percentile(lat, 99)), 1)},
+           "loads": []}
+    checked = 0
+    for factor in [0.25, 0.5, 0.9, 1.5]:
+        rate = factor * serial_qps
+        count = max(200, int(rate * args.serve_seconds))
+        qs = [make_query() for _ in range(count)]
+        gaps = rng.exponential(1.0 / rate, size=count)
+        srv = gbscan.Server(cols, slots=4, device_bytes_per_slot=96 * 512, max_queue=1 << 20)
+        ids = [None] * count
+        lats = [None] * count
+        results = [None] * count
+        ready = threading.Semaphore(0)
+
+        def collect():
+            for i in range(count):
+                ready.acquire()
+                done, res, us = srv.poll(ids[i], len(qs[i][0]), wait=True)
+                lats[i] = us
+                results[i] = [r.pair() for r in res]
+
+        th = threading.Thread(target=collect)
+        th.start()
+        start = time.perf_counter()
+        due = start
+        for i in range(count):
+            due += gaps[i]
+            while time.perf_counter() < due:
+                pass
+            ids[i] = srv.submit(*qs[i])
+            ready.release()
+        th.join()
+        wall = time.perf_counter() - start
+        st = srv.stats()
+        srv.close()
+        # the same queries run alone give the same results, bit for bit
+        sample = list(range(0, count, max(1, count // 25)))
+        exact = all(results[i] == alone(qs[i]) for i in sample)
+        checked += len(sample)
+        out["loads"].append({"load": factor, "offered_qps": round(rate, 1), "queries": count,
+                             "achieved_qps": round(count / wall, 1),
+                             "p50_us": round(float(np.percentile(lats, 50)), 1),
+                             "p99_us": round(float(np.percentile(lats, 99)), 1),
+                             "batches": st["batches"], "queries_per_batch": round(count / max(1, st["batches"]), 2),
+                             "exact_vs_alone": exact})
+    out["exact_checked_queries"] = checked
+    for c in cols:
+        c.close()
+    torch.cuda.empty_cache()
+    return out
 
 
 def cudart_copy(dst_tensor, src_ptr: int, nbytes: int):
@@ -477,6 +698,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=1.5)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

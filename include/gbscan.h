@@ -164,6 +164,134 @@ scan_status scan_run_async(scan_column *col, scan_pred pred, scan_strategy strat
  * column's kernels: SCAN_OK or SCAN_ETIMEOUT. */
 scan_status scan_column_status(scan_column *col, void *stream);
 
+/* -------------------------------------------------------------- batches */
+
+typedef struct scan_batch scan_batch; /* opaque: a planned batch of column scans */
+
+/* Plan a batch over `ncols` columns (spec batched form, configuration
+ * "4096 columns in one persistent CUDA-graph launch"): every column's blocks
+ * are cut into tiles of at most 8 KB and numbered consecutively; one
+ * persistent kernel per predicate flavour (branch-free, branchy) serves all
+ * tiles, warps popping `tiles_per_pop` consecutive tiles per atomic (0 = about
+ * eight pops per warp).  strategies[i] picks column i's kernel and whether it
+ * skips blocks by zone map (NULL = SCAN_BRANCHFREE for all; SCAN_AUTO counts
+ * as branch-free).  Zone-skip columns need a built zone map.  The columns must
+ * outlive the plan.  The first scan_batch_exec records a CUDA graph (copy
+ * descriptors, reset results, kernels, copy results back) that later calls
+ * replay. */
+scan_status scan_batch_create(scan_column *const *cols, uint32_t ncols,
+                              const scan_strategy *strategies, uint32_t tiles_per_pop,
+                              void *stream, scan_batch **out);
+
+/* Run the plan with one predicate per column.  host_out (ncols results, may
+ * be NULL) is filled after the stream is synchronised; dev_out (ncols results
+ * in device memory, may be NULL) is written asynchronously.  Results equal
+ * scan_run's bit for bit.  SCAN_ETIMEOUT if a bounded device wait gave up. */
+scan_status scan_batch_exec(scan_batch *batch, const scan_pred *preds, void *stream,
+                            scan_result *host_out, scan_result *dev_out);
+
+/* Free the plan (synchronises the device first). */
+scan_status scan_batch_destroy(scan_batch *batch);
+
+/* Change the strategy of every column of the plan (re-lays out the tiles;
+ * the next scan_batch_exec records a new graph).  Synchronises the device. */
+scan_status scan_batch_set_strategies(scan_batch *batch, const scan_strategy *strategies);
+
+/* Planner features of every column for these predicates, computed on the GPU
+ * into dev_features (ncols x 4 floats, column order):
+ *   f0 = b/32; f1 = log2(max(N,1))/31;
+ *   f2 = (log10(max(sigma_hat, 1e-5)) + 5)/5, sigma_hat = matches/values over up
+ *        to 32 evenly spaced blocks (an exact sample of the predicate);
+ *   f3 = 1 - mean_k (max_k - min_k + 1)/(colmax - colmin + 1) from the zone map
+ *        (0 without one): ~0 for shuffled, ~1 for sorted columns.
+ * Asynchronous after one stream synchronisation. */
+scan_status scan_batch_features(scan_batch *batch, const scan_pred *preds, void *stream,
+                                float *dev_features);
+
+/* Law-based plan (paper §2 Eq. 2 per strategy), the fallback when no trained
+ * planner is loaded: strategy s costs max(bytes_s/beta, values_s/T_dec[s]),
+ * where a zone skip reads the zone map plus a fraction min(1, sigma_hat +
+ * (1 - c) + 2/blocks) of the blocks.  t_dec_values_per_s[4] (host) are the
+ * fitted T_dec of branch-free, branchy, zone-skip branch-free, zone-skip
+ * branchy; dev_choice (ncols int32, device) gets 0..3 in that order. */
+scan_status scan_batch_law_choose(scan_batch *batch, const float *dev_features,
+                                  float beta_bytes_per_s, const float *t_dec_values_per_s,
+                                  void *stream, int32_t *dev_choice);
+
+/* One-shot batch: plan, run once with host results, free. */
+scan_status scan_batch_run(const scan_column *const *cols, const scan_pred *preds, uint32_t ncols,
+                           const scan_strategy *strategies, void *stream, scan_result *host_out);
+
+/* ------------------------------------------------------ learned planner */
+
+/* The planner (north-star "learned planner"; the paper has none): an FP32
+ * network 4 -> 64 -> 64 -> n_strategies with ReLU hidden layers that predicts
+ * the log time of each strategy from the four features above; the strategy
+ * with the smallest prediction is chosen.  Every strategy returns identical
+ * results, so the planner only changes speed.  Forward, backward (mean
+ * squared error) and Adam run in this library's CUDA kernels; parameters are
+ * one flat float array [W1 (4x64), b1, W2 (64x64), b2, W3 (64xS), b3], each W
+ * row-major (fan_in, fan_out); He-uniform initial weights from splitmix64(seed),
+ * zero biases. */
+typedef struct scan_planner scan_planner;
+
+scan_status scan_planner_create(uint32_t n_strategies, uint64_t seed, scan_planner **out);
+scan_status scan_planner_destroy(scan_planner *planner);
+uint64_t scan_planner_param_count(const scan_planner *planner);
+/* Copy parameters to / from host memory (param_count floats); setting them
+ * resets the Adam state. */
+scan_status scan_planner_get_params(const scan_planner *planner, float *host_params);
+scan_status scan_planner_set_params(scan_planner *planner, const float *host_params);
+/* dev_y[rows x S] = network(dev_x[rows x 4]). */
+scan_status scan_planner_forward(scan_planner *planner, const float *dev_x, uint32_t rows, float *dev_y,
+                                 void *stream);
+/* Gradients of mean((y - t)^2) with respect to every parameter into dev_grads
+ * (param_count floats, may be NULL); *host_loss (may be NULL) gets the loss
+ * after a stream synchronisation. */
+scan_status scan_planner_gradients(scan_planner *planner, const float *dev_x, const float *dev_t,
+                                   uint32_t rows, float *dev_grads, void *stream, float *host_loss);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) at learning rate lr. */
+scan_status scan_planner_train_step(scan_planner *planner, const float *dev_x, const float *dev_t,
+                                    uint32_t rows, float lr, void *stream, float *host_loss);
+/* dev_choice[rows] = argmin over strategies of the predicted log time. */
+scan_status scan_planner_choose(scan_planner *planner, const float *dev_x, uint32_t rows,
+                                int32_t *dev_choice, void *stream);
+/* Binary checkpoint: 16-byte header (magic, version 1, S, count) + floats. */
+scan_status scan_planner_save(const scan_planner *planner, const char *path);
+scan_status scan_planner_load(scan_planner *planner, const char *path);
+
+/* -------------------------------------------------------------- serving */
+
+/* A scan server (spec serving loop; the paper has none): continuous
+ * batching of COUNT/SUM queries against a device-resident table of columns.
+ * A query names n table columns (ids into `cols`), each with its own
+ * predicate.  Admission is by device memory: each of `slots` in-flight
+ * batches owns device_bytes_per_slot bytes of descriptors and results (96
+ * bytes per column scan), and a query waits in the queue until a slot with
+ * room for all its scans frees up; a dispatcher thread packs every waiting
+ * query that fits into one batched launch on that slot's stream, so batches
+ * overlap on the device while new queries keep arriving; a completion thread
+ * retires batches in launch order.  Zone maps are used wherever a column has
+ * one.  Each result equals the query's result run alone, bit for bit.  The
+ * table's columns must outlive the server. */
+typedef struct scan_server scan_server;
+
+scan_status scan_server_create(scan_column *const *cols, uint32_t ncols, uint32_t slots,
+                               uint64_t device_bytes_per_slot, uint32_t max_queue,
+                               scan_server **out);
+/* Enqueue a query; SCAN_EBUSY when max_queue queries already wait. */
+scan_status scan_server_submit(scan_server *server, const uint32_t *col_ids, const scan_pred *preds,
+                               uint32_t n, uint64_t *query_id);
+/* *done = 1 and results copied (n >= the query's column count) once the
+ * query has completed; wait != 0 blocks until then.  A collected query id is
+ * forgotten.  *latency_us (may be NULL) = completion - submission time. */
+scan_status scan_server_poll(scan_server *server, uint64_t query_id, int wait, scan_result *out,
+                             uint32_t n, double *latency_us, int *done);
+scan_status scan_server_stats(scan_server *server, uint64_t *batches, uint64_t *column_scans,
+                              uint64_t *rejected, uint32_t *queued);
+/* Stop the threads, wait for batches in flight, free everything. */
+scan_status scan_server_destroy(scan_server *server);
+
 /* ------------------------------------------------------ no allocation */
 
 /* The paper has no counterpart to this call; it is an integration aid.

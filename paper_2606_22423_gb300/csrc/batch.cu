@@ -1,0 +1,484 @@
+// Host side of the batched scan: a plan lays out the tiles of many columns,
+// keeps a device descriptor table, and records one CUDA graph per plan:
+//   descriptors H2D -> reset results/counters -> branch-free batch kernel
+//   -> branchy batch kernel -> results D2H.
+// Running the plan again with new predicates only rewrites the pinned
+// descriptor table and replays the graph.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "../../include/gbscan.h"
+#include "batch_kernels.cuh"
+
+void gb_set_last_error(const char* msg);
+// column internals shared with capi.cu
+bool gb_column_view(const scan_column* c, const uint32_t** packed, uint64_t* n, uint32_t* b,
+                    uint32_t* base, const uint2** zonemap);
+
+namespace {
+
+scan_status bfail(scan_status s, const char* msg)
+{
+    gb_set_last_error(msg);
+    return s;
+}
+
+scan_status bcuda(cudaError_t e, const char* what)
+{
+    static thread_local char buf[256];
+    snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
+    gb_set_last_error(buf);
+    return e == cudaErrorMemoryAllocation ? SCAN_ENOMEM : SCAN_ECUDA;
+}
+
+#define BT_CUDA(call)                                 \
+    do {                                              \
+        cudaError_t e_ = (call);                      \
+        if (e_ != cudaSuccess) return bcuda(e_, #call); \
+    } while (0)
+
+int batch_grid()
+{
+    static int sms = [] {
+        int dev = 0, n = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        return n > 0 ? n : 1;
+    }();
+    return sms;
+}
+
+uint32_t tile_blocks_for(uint32_t b) { return static_cast<uint32_t>(gb::shape_of(static_cast<int>(b)).tile_blocks); }
+
+}  // namespace
+
+struct scan_batch {
+    uint32_t ncols = 0;
+    std::vector<const scan_column*> cols;
+    std::vector<int> kernel_of;        // 0 branch-free, 1 branchy
+    std::vector<uint32_t> zone;        // 1 if the column skips by zone map
+    std::vector<uint32_t> slot_of;     // index of the column in the descriptor table
+    uint32_t ncol_k[2] = {0, 0};
+    uint32_t ntiles_k[2] = {0, 0};
+    uint32_t chunk_k[2] = {1, 1};
+    uint32_t tiles_per_pop = 0;
+    gb::BatchCol* h_table = nullptr;   // pinned
+    gb::BatchCol* d_table = nullptr;
+    unsigned long long* d_results = nullptr;  // 4 words per column, then 2 pop counters + status
+    scan_result* h_results = nullptr;  // pinned copy of the results
+    cudaStream_t capture_stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+};
+
+cudaError_t gb_launch_batch_branchfree(const gb::BatchParams& p, int grid, cudaStream_t st);
+cudaError_t gb_launch_batch_branchy(const gb::BatchParams& p, int grid, cudaStream_t st);
+
+namespace gb {
+static cudaError_t launch_batch_kernel(bool branchy, const BatchParams& p, int grid, cudaStream_t st)
+{
+    return branchy ? gb_launch_batch_branchy(p, grid, st) : gb_launch_batch_branchfree(p, grid, st);
+}
+}  // namespace gb
+
+namespace {
+
+// Lay out the tiles for the current strategies (branch-free columns first).
+scan_status layout(scan_batch* bt)
+{
+    std::vector<uint32_t> order;
+    for (int k = 0; k < 2; ++k)
+        for (uint32_t i = 0; i < bt->ncols; ++i)
+            if (bt->kernel_of[i] == k) order.push_back(i);
+    const size_t table_bytes = std::max<size_t>(1, bt->ncols) * sizeof(gb::BatchCol);
+    std::memset(bt->h_table, 0, table_bytes);
+    uint32_t tiles[2] = {0, 0};
+    bt->ncol_k[0] = bt->ncol_k[1] = 0;
+    for (uint32_t j = 0; j < order.size(); ++j) {
+        const uint32_t i = order[j];
+        const int k = bt->kernel_of[i];
+        const uint2* zm = nullptr;
+        const uint32_t* pk;
+        uint64_t n;
+        uint32_t b, base;
+        gb_column_view(bt->cols[i], &pk, &n, &b, &base, &zm);
+        gb::BatchCol& d = bt->h_table[j];
+        d.packed = pk;
+        d.zonemap = zm;
+        d.n = n;
+        d.b = b;
+        d.base = base;
+        d.tile_blocks = tile_blocks_for(b);
+        d.tile_begin = tiles[k];
+        d.out = i;
+        const uint64_t nblocks = (n + 1023u) >> 10;
+        const uint64_t t = (nblocks + d.tile_blocks - 1) / d.tile_blocks;
+        if (tiles[k] + t > 0xffffffffull) return bfail(SCAN_EINVAL, "too many tiles in one batch");
+        tiles[k] += static_cast<uint32_t>(t);
+        bt->slot_of[i] = j;
+        bt->ncol_k[k] += 1;
+    }
+    const uint32_t warps = static_cast<uint32_t>(batch_grid()) * gb::kBatchWarps;
+    for (int k = 0; k < 2; ++k) {
+        bt->ntiles_k[k] = tiles[k];
+        // default: about eight pops per warp
+        const uint32_t c = bt->tiles_per_pop ? bt->tiles_per_pop : std::max<uint32_t>(1, tiles[k] / (8 * warps));
+        bt->chunk_k[k] = std::min<uint32_t>(c, 1024);
+    }
+    if (bt->graph) {
+        cudaGraphExecDestroy(bt->graph);
+        bt->graph = nullptr;
+    }
+    return SCAN_OK;
+}
+
+scan_status set_strategy(scan_batch* bt, uint32_t i, scan_strategy st)
+{
+    const uint2* zm = nullptr;
+    const uint32_t* pk;
+    uint64_t n;
+    uint32_t b, base;
+    gb_column_view(bt->cols[i], &pk, &n, &b, &base, &zm);
+    bt->kernel_of[i] = 0;
+    bt->zone[i] = 0;
+    switch (st) {
+    case SCAN_AUTO:
+    case SCAN_BRANCHFREE: break;
+    case SCAN_BRANCHY: bt->kernel_of[i] = 1; break;
+    case SCAN_ZONE_SKIP_BF: bt->zone[i] = 1; break;
+    case SCAN_ZONE_SKIP_BR:
+        bt->zone[i] = 1;
+        bt->kernel_of[i] = 1;
+        break;
+    default: return bfail(SCAN_EINVAL, "unknown strategy");
+    }
+    if (bt->zone[i] && !zm) return bfail(SCAN_EINVAL, "a zone-skip column has no zone map (scan_zonemap_build first)");
+    return SCAN_OK;
+}
+
+// Write the predicate fields of the pinned descriptor table.
+void fill_predicates(scan_batch* bt, const scan_pred* preds)
+{
+    for (uint32_t i = 0; i < bt->ncols; ++i) {
+        gb::BatchCol& d = bt->h_table[bt->slot_of[i]];
+        const int64_t lo_v = static_cast<int64_t>(d.base);
+        const int64_t hi_v = lo_v + (1ll << d.b);
+        const int64_t lo = std::max(preds[i].lo, lo_v);
+        const int64_t hi = std::min(preds[i].hi, hi_v);
+        d.flags = bt->zone[i] ? gb::kColZone : 0u;
+        if (lo >= hi || d.n == 0) {
+            d.flags |= gb::kColEmpty;
+            d.lo = 0;
+            d.wm1 = 0;
+            d.zlo = d.zhi = 0;
+        } else {
+            d.lo = static_cast<uint32_t>(lo - lo_v);
+            d.wm1 = static_cast<uint32_t>(hi - lo - 1);
+            d.zlo = static_cast<uint64_t>(lo);
+            d.zhi = static_cast<uint64_t>(hi);
+        }
+    }
+}
+
+// Planner features, one CTA per column:
+//   f0 = b / 32, f1 = log2(max(N, 1)) / 31,
+//   f2 = (log10(max(sigma_hat, 1e-5)) + 5) / 5, sigma_hat = matches / values over up to
+//        32 evenly spaced blocks (exact integer sample of the true predicate),
+//   f3 = clustering c = 1 - mean_k (max_k - min_k + 1) / (colmax - colmin + 1) from the
+//        zone map (0 without one): about 0 for shuffled data, about 1 for sorted data.
+__global__ void __launch_bounds__(256) k_batch_features(const gb::BatchCol* __restrict__ cols, float* feats)
+{
+    __shared__ unsigned long long red_a[8], red_b[8];
+    __shared__ double red_d[8];
+    const gb::BatchCol c = cols[blockIdx.x];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t nblocks = (c.n + 1023u) >> 10;
+    const uint32_t S = static_cast<uint32_t>(nblocks < 32 ? nblocks : 32);
+    const uint64_t mask = (c.b == 32) ? 0xffffffffull : ((1ull << c.b) - 1ull);
+    unsigned long long match = 0, seen = 0;
+    for (uint32_t idx = threadIdx.x; idx < S * 1024u; idx += blockDim.x) {
+        const uint32_t j = idx >> 10, pos = idx & 1023u;
+        const uint64_t k = static_cast<uint64_t>(j) * nblocks / S;
+        if ((k << 10) + pos >= c.n) continue;
+        ++seen;
+        if (c.flags & gb::kColEmpty) continue;
+        const uint32_t l = pos & 31u, row = pos >> 5;
+        const uint32_t bit = row * c.b, w = bit >> 5, sh = bit & 31u;
+        const uint32_t* blk = c.packed + k * 32u * c.b;
+        uint64_t win = __ldg(&blk[32u * w + l]);
+        if (sh + c.b > 32u) win |= static_cast<uint64_t>(__ldg(&blk[32u * (w + 1u) + l])) << 32;
+        const uint32_t u = static_cast<uint32_t>((win >> sh) & mask);
+        if (u - c.lo <= c.wm1) ++match;
+    }
+    for (int o = 16; o; o >>= 1) {
+        match += __shfl_xor_sync(0xffffffffu, match, o);
+        seen += __shfl_xor_sync(0xffffffffu, seen, o);
+    }
+    if (lane == 0) {
+        red_a[warp] = match;
+        red_b[warp] = seen;
+    }
+    __syncthreads();
+    unsigned long long tm = 0, ts = 0;
+    for (int w = 0; w < 8; ++w) {
+        tm += red_a[w];
+        ts += red_b[w];
+    }
+    __syncthreads();
+    // clustering from the zone map: column range, then the mean relative block range
+    double mean_rel = 1.0;
+    if (c.zonemap && nblocks) {
+        unsigned long long mn = ~0ull, mx = 0;
+        for (uint64_t k = threadIdx.x; k < nblocks; k += blockDim.x) {
+            const uint2 z = __ldg(&c.zonemap[k]);
+            mn = min(mn, static_cast<unsigned long long>(z.x));
+            mx = max(mx, static_cast<unsigned long long>(z.y));
+        }
+        for (int o = 16; o; o >>= 1) {
+            mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+            mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        }
+        if (lane == 0) {
+            red_a[warp] = mn;
+            red_b[warp] = mx;
+        }
+        __syncthreads();
+        unsigned long long cmn = ~0ull, cmx = 0;
+        for (int w = 0; w < 8; ++w) {
+            cmn = min(cmn, red_a[w]);
+            cmx = max(cmx, red_b[w]);
+        }
+        const double span = static_cast<double>(cmx - cmn + 1ull);
+        double acc = 0.0;
+        for (uint64_t k = threadIdx.x; k < nblocks; k += blockDim.x) {
+            const uint2 z = __ldg(&c.zonemap[k]);
+            acc += static_cast<double>(static_cast<unsigned long long>(z.y) - z.x + 1ull) / span;
+        }
+        for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) red_d[warp] = acc;
+        __syncthreads();
+        double tot = 0.0;
+        for (int w = 0; w < 8; ++w) tot += red_d[w];
+        mean_rel = tot / static_cast<double>(nblocks);
+    }
+    if (threadIdx.x == 0) {
+        const double sigma = ts ? static_cast<double>(tm) / static_cast<double>(ts) : 0.0;
+        float* f = feats + 4ull * c.out;
+        f[0] = static_cast<float>(c.b) / 32.f;
+        f[1] = static_cast<float>(log2(c.n > 0 ? static_cast<double>(c.n) : 1.0) / 31.0);
+        f[2] = static_cast<float>((log10(sigma > 1e-5 ? sigma : 1e-5) + 5.0) / 5.0);
+        f[3] = static_cast<float>(c.zonemap ? 1.0 - mean_rel : 0.0);
+    }
+}
+
+// Law fallback (Eq. 2 per strategy): the predicted time of strategy s is
+//   max(bytes_s / beta, values_s / T_dec[s]); a zone skip reads the zone map
+//   plus a fraction phi = min(1, sigma_hat + (1 - c) + 2 / blocks) of the blocks.
+//   Strategies: 0 branch-free, 1 branchy, 2 zone-skip branch-free, 3 zone-skip branchy.
+__global__ void k_law_choose(const float* __restrict__ feats, const gb::BatchCol* __restrict__ cols,
+                             uint32_t ncols, float beta, float t0, float t1, float t2, float t3,
+                             int32_t* __restrict__ out)
+{
+    const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= ncols) return;
+    const gb::BatchCol c = cols[j];
+    const float* f = feats + 4ull * c.out;
+    const double n = static_cast<double>(c.n), nb = static_cast<double>((c.n + 1023u) >> 10);
+    const double bytes = nb * 128.0 * c.b;
+    const double sigma = pow(10.0, 5.0 * f[2] - 5.0);
+    double phi = sigma + (1.0 - f[3]) + (nb > 0 ? 2.0 / nb : 1.0);
+    phi = phi > 1.0 ? 1.0 : phi;
+    const double tdec[4] = {t0, t1, t2, t3};
+    const bool has_zone = c.zonemap != nullptr;
+    int best = 0;
+    double bt = 1e300;
+    for (int s = 0; s < 4; ++s) {
+        const bool zone = s >= 2;
+        if (zone && !has_zone) continue;
+        const double rd = zone ? phi * bytes + 8.0 * nb : bytes;
+        const double vals = zone ? phi * n : n;
+        const double t = fmax(rd / beta, vals / tdec[s]);
+        if (t < bt) {
+            bt = t;
+            best = s;
+        }
+    }
+    out[c.out] = best;
+}
+
+}  // namespace
+
+extern "C" {
+
+scan_status scan_batch_create(scan_column* const* cols, uint32_t ncols, const scan_strategy* strategies,
+                              uint32_t tiles_per_pop, void* stream, scan_batch** out)
+{
+    (void)stream;
+    gb_set_last_error("");
+    if (!out || (ncols && !cols)) return bfail(SCAN_EINVAL, "null pointer");
+    *out = nullptr;
+    for (uint32_t i = 0; i < ncols; ++i)
+        if (!cols[i]) return bfail(SCAN_EINVAL, "a column pointer is NULL");
+    auto* bt = new (std::nothrow) scan_batch();
+    if (!bt) return bfail(SCAN_ENOMEM, "host allocation failed");
+    bt->ncols = ncols;
+    bt->tiles_per_pop = tiles_per_pop;
+    bt->cols.assign(cols, cols + ncols);
+    bt->kernel_of.assign(ncols, 0);
+    bt->zone.assign(ncols, 0);
+    bt->slot_of.assign(ncols, 0);
+    for (uint32_t i = 0; i < ncols; ++i) {
+        const scan_status s = set_strategy(bt, i, strategies ? strategies[i] : SCAN_BRANCHFREE);
+        if (s != SCAN_OK) {
+            delete bt;
+            return s;
+        }
+    }
+    const size_t table_bytes = std::max<size_t>(1, ncols) * sizeof(gb::BatchCol);
+    const size_t res_bytes = (4ull * std::max<uint32_t>(1, ncols) + 4) * sizeof(unsigned long long);
+    cudaError_t e = cudaMallocHost(reinterpret_cast<void**>(&bt->h_table), table_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&bt->d_table), table_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&bt->d_results), res_bytes);
+    if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&bt->h_results), res_bytes);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&bt->capture_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        scan_batch_destroy(bt);
+        return bcuda(e, "batch allocation");
+    }
+    const scan_status s = layout(bt);
+    if (s != SCAN_OK) {
+        scan_batch_destroy(bt);
+        return s;
+    }
+    *out = bt;
+    return SCAN_OK;
+}
+
+scan_status scan_batch_destroy(scan_batch* bt)
+{
+    if (!bt) return SCAN_OK;
+    cudaDeviceSynchronize();
+    if (bt->graph) cudaGraphExecDestroy(bt->graph);
+    if (bt->capture_stream) cudaStreamDestroy(bt->capture_stream);
+    if (bt->h_table) cudaFreeHost(bt->h_table);
+    if (bt->h_results) cudaFreeHost(bt->h_results);
+    if (bt->d_table) cudaFree(bt->d_table);
+    if (bt->d_results) cudaFree(bt->d_results);
+    delete bt;
+    return SCAN_OK;
+}
+
+scan_status scan_batch_set_strategies(scan_batch* bt, const scan_strategy* strategies)
+{
+    gb_set_last_error("");
+    if (!bt || (bt->ncols && !strategies)) return bfail(SCAN_EINVAL, "null pointer");
+    cudaDeviceSynchronize();  // a replay in flight may still read the table
+    for (uint32_t i = 0; i < bt->ncols; ++i) {
+        const scan_status s = set_strategy(bt, i, strategies[i]);
+        if (s != SCAN_OK) return s;
+    }
+    return layout(bt);
+}
+
+scan_status scan_batch_features(scan_batch* bt, const scan_pred* preds, void* stream, float* dev_features)
+{
+    gb_set_last_error("");
+    if (!bt || !dev_features || (bt->ncols && !preds)) return bfail(SCAN_EINVAL, "null pointer");
+    if (!bt->ncols) return SCAN_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    BT_CUDA(cudaStreamSynchronize(st));
+    fill_predicates(bt, preds);
+    BT_CUDA(cudaMemcpyAsync(bt->d_table, bt->h_table, bt->ncols * sizeof(gb::BatchCol), cudaMemcpyHostToDevice, st));
+    k_batch_features<<<bt->ncols, 256, 0, st>>>(bt->d_table, dev_features);
+    BT_CUDA(cudaGetLastError());
+    return SCAN_OK;
+}
+
+scan_status scan_batch_law_choose(scan_batch* bt, const float* dev_features, float beta_bytes_per_s,
+                                  const float* t_dec_values_per_s, void* stream, int32_t* dev_choice)
+{
+    gb_set_last_error("");
+    if (!bt || !dev_features || !dev_choice || !t_dec_values_per_s) return bfail(SCAN_EINVAL, "null pointer");
+    if (!bt->ncols) return SCAN_OK;
+    if (!(beta_bytes_per_s > 0.f)) return bfail(SCAN_EINVAL, "beta must be positive");
+    for (int s = 0; s < 4; ++s)
+        if (!(t_dec_values_per_s[s] > 0.f)) return bfail(SCAN_EINVAL, "every T_dec must be positive");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    k_law_choose<<<(bt->ncols + 255) / 256, 256, 0, st>>>(dev_features, bt->d_table, bt->ncols, beta_bytes_per_s,
+                                                          t_dec_values_per_s[0], t_dec_values_per_s[1],
+                                                          t_dec_values_per_s[2], t_dec_values_per_s[3], dev_choice);
+    BT_CUDA(cudaGetLastError());
+    return SCAN_OK;
+}
+
+scan_status scan_batch_exec(scan_batch* bt, const scan_pred* preds, void* stream, scan_result* host_out,
+                            scan_result* dev_out)
+{
+    gb_set_last_error("");
+    if (!bt || (bt->ncols && !preds)) return bfail(SCAN_EINVAL, "null pointer");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // the previous replay may still read the pinned table: wait for it
+    BT_CUDA(cudaStreamSynchronize(st));
+    fill_predicates(bt, preds);
+    const size_t table_bytes = std::max<size_t>(1, bt->ncols) * sizeof(gb::BatchCol);
+    const size_t res_words = 4ull * std::max<uint32_t>(1, bt->ncols) + 4;
+    unsigned long long* ctl = bt->d_results + 4ull * std::max<uint32_t>(1, bt->ncols);
+    if (!bt->graph) {
+        cudaStream_t cs = bt->capture_stream;
+        BT_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        cudaMemcpyAsync(bt->d_table, bt->h_table, table_bytes, cudaMemcpyHostToDevice, cs);
+        cudaMemsetAsync(bt->d_results, 0, res_words * sizeof(unsigned long long), cs);
+        const gb::BatchCol* tbl[2] = {bt->d_table, bt->d_table + bt->ncol_k[0]};
+        for (int k = 0; k < 2; ++k) {
+            if (!bt->ntiles_k[k]) continue;
+            gb::BatchParams p{};
+            p.cols = tbl[k];
+            p.ncols = bt->ncol_k[k];
+            p.ntiles = bt->ntiles_k[k];
+            p.chunk = bt->chunk_k[k];
+            p.head = reinterpret_cast<unsigned int*>(ctl) + k;
+            p.results = bt->d_results;
+            p.status = reinterpret_cast<unsigned int*>(ctl) + 2;
+            gb::launch_batch_kernel(k == 1, p, batch_grid(), cs);
+        }
+        cudaMemcpyAsync(bt->h_results, bt->d_results, res_words * sizeof(unsigned long long),
+                        cudaMemcpyDeviceToHost, cs);
+        cudaGraph_t g = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(cs, &g);
+        if (ec != cudaSuccess || !g) return bcuda(ec != cudaSuccess ? ec : cudaErrorUnknown, "graph capture");
+        const cudaError_t ei = cudaGraphInstantiate(&bt->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (ei != cudaSuccess) return bcuda(ei, "cudaGraphInstantiate");
+    }
+    BT_CUDA(cudaGraphLaunch(bt->graph, st));
+    if (dev_out)
+        BT_CUDA(cudaMemcpyAsync(dev_out, bt->d_results, 4ull * bt->ncols * sizeof(unsigned long long),
+                                cudaMemcpyDeviceToDevice, st));
+    if (host_out) {
+        BT_CUDA(cudaStreamSynchronize(st));
+        const unsigned int status = reinterpret_cast<const unsigned int*>(
+            reinterpret_cast<const unsigned long long*>(bt->h_results) + 4ull * std::max<uint32_t>(1, bt->ncols))[2];
+        if (status) return bfail(SCAN_ETIMEOUT, "a device-side wait timed out in the batch kernel");
+        std::memcpy(host_out, bt->h_results, sizeof(scan_result) * bt->ncols);
+    }
+    return SCAN_OK;
+}
+
+scan_status scan_batch_run(const scan_column* const* cols, const scan_pred* preds, uint32_t ncols,
+                           const scan_strategy* strategies, void* stream, scan_result* host_out)
+{
+    scan_batch* bt = nullptr;
+    scan_status s = scan_batch_create(const_cast<scan_column* const*>(cols), ncols, strategies, 0, stream, &bt);
+    if (s != SCAN_OK) return s;
+    s = scan_batch_exec(bt, preds, stream, host_out, nullptr);
+    if (s == SCAN_OK) cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    scan_batch_destroy(bt);
+    return s;
+}
+
+}  // extern "C"

@@ -70,6 +70,31 @@ SIGNATURES = {
     "scan_probe_read": (_st, [_vp, _u64, _vp, _vp]),
     "scan_launch_shape": (_st, [_u32] + [ctypes.POINTER(_u32)] * 5),
     "scan_run_packed_noalloc": (_st, [_vp, _u64, _u32, _u32, scan_pred, _st, _vp, _vp, _vp]),
+    "scan_batch_create": (_st, [_vp, _u32, _vp, _u32, _vp, ctypes.POINTER(_vp)]),
+    "scan_batch_exec": (_st, [_vp, _vp, _vp, _vp, _vp]),
+    "scan_batch_destroy": (_st, [_vp]),
+    "scan_batch_run": (_st, [_vp, _vp, _u32, _vp, _vp, _vp]),
+    "scan_batch_set_strategies": (_st, [_vp, _vp]),
+    "scan_batch_features": (_st, [_vp, _vp, _vp, _vp]),
+    "scan_batch_law_choose": (_st, [_vp, _vp, ctypes.c_float, _vp, _vp, _vp]),
+    "scan_planner_create": (_st, [_u32, _u64, ctypes.POINTER(_vp)]),
+    "scan_planner_destroy": (_st, [_vp]),
+    "scan_planner_param_count": (_u64, [_vp]),
+    "scan_planner_get_params": (_st, [_vp, _vp]),
+    "scan_planner_set_params": (_st, [_vp, _vp]),
+    "scan_planner_forward": (_st, [_vp, _vp, _u32, _vp, _vp]),
+    "scan_planner_gradients": (_st, [_vp, _vp, _vp, _u32, _vp, _vp, _vp]),
+    "scan_planner_train_step": (_st, [_vp, _vp, _vp, _u32, ctypes.c_float, _vp, _vp]),
+    "scan_planner_choose": (_st, [_vp, _vp, _u32, _vp, _vp]),
+    "scan_planner_save": (_st, [_vp, ctypes.c_char_p]),
+    "scan_planner_load": (_st, [_vp, ctypes.c_char_p]),
+    "scan_server_create": (_st, [_vp, _u32, _u32, _u64, _u32, ctypes.POINTER(_vp)]),
+    "scan_server_submit": (_st, [_vp, _vp, _vp, _u32, ctypes.POINTER(_u64)]),
+    "scan_server_poll": (_st, [_vp, _u64, ctypes.c_int, _vp, _u32, ctypes.POINTER(ctypes.c_double),
+                               ctypes.POINTER(ctypes.c_int)]),
+    "scan_server_stats": (_st, [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64), ctypes.POINTER(_u64),
+                                ctypes.POINTER(_u32)]),
+    "scan_server_destroy": (_st, [_vp]),
 }
 
 _lib = None
@@ -241,3 +266,188 @@ class Column:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def _strategy_array(strategies, n):
+    if strategies is None:
+        return None
+    arr = (ctypes.c_int * n)(*[STRATEGIES[x] if isinstance(x, str) else int(x) for x in strategies])
+    return arr
+
+
+class Batch:
+    """A planned batch over many columns (scan_batch_create / _exec / _destroy)."""
+
+    def __init__(self, columns, strategies=None, tiles_per_pop: int = 0, stream=None):
+        self.columns = list(columns)
+        n = len(self.columns)
+        self._cols = (_vp * max(n, 1))(*[c.handle.value for c in self.columns])
+        self._strats = _strategy_array(strategies, n)
+        h = _vp()
+        _check(load().scan_batch_create(self._cols, n, self._strats, tiles_per_pop, _stream(stream),
+                                        ctypes.byref(h)))
+        self._h = h
+
+    def set_strategies(self, strategies):
+        n = len(self.columns)
+        self._strats = _strategy_array(strategies, n)
+        _check(load().scan_batch_set_strategies(self._h, self._strats))
+
+    def features(self, preds, dev_features, stream=None):
+        """Planner features (ncols x 4 float32, device) for these predicates."""
+        n = len(self.columns)
+        pr = (scan_pred * max(n, 1))(*[scan_pred(int(lo), int(hi)) for lo, hi in preds])
+        _check(load().scan_batch_features(self._h, pr, _stream(stream), _ptr(dev_features)))
+
+    def law_choose(self, dev_features, beta_bytes_per_s, t_dec_values_per_s, dev_choice, stream=None):
+        """Strategy per column (int32, device) from the bandwidth law with fitted T_dec."""
+        td = (ctypes.c_float * 4)(*[float(x) for x in t_dec_values_per_s])
+        _check(load().scan_batch_law_choose(self._h, _ptr(dev_features), float(beta_bytes_per_s), td,
+                                            _stream(stream), _ptr(dev_choice)))
+
+    @staticmethod
+    def pred_array(preds):
+        """Marshal predicates once (reusable across runs)."""
+        return (scan_pred * max(len(preds), 1))(*[scan_pred(int(lo), int(hi)) for lo, hi in preds])
+
+    def run(self, preds, stream=None, dev_out=None, host=True):
+        n = len(self.columns)
+        pr = preds if isinstance(preds, ctypes.Array) else self.pred_array(preds)
+        out = (scan_result * max(n, 1))() if host else None
+        _check(load().scan_batch_exec(self._h, pr, _stream(stream), out if host else None, _ptr(dev_out)))
+        return [out[i] for i in range(n)] if host else None
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            _check(load().scan_batch_destroy(self._h))
+            self._h = _vp(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def scan_batch_run(columns, preds, strategies=None, stream=None):
+    """One-shot batch with host results."""
+    n = len(columns)
+    cols = (_vp * max(n, 1))(*[c.handle.value for c in columns])
+    pr = (scan_pred * max(n, 1))(*[scan_pred(int(lo), int(hi)) for lo, hi in preds])
+    out = (scan_result * max(n, 1))()
+    _check(load().scan_batch_run(cols, pr, n, _strategy_array(strategies, n), _stream(stream), out))
+    return [out[i] for i in range(n)]
+
+
+STRATEGY_ORDER = ["branchfree", "branchy", "zone_bf", "zone_br"]   # planner output index -> strategy
+
+
+class Planner:
+    """The planner network on the GPU (scan_planner_*): 4 -> 64 -> 64 -> S."""
+
+    def __init__(self, n_strategies: int = 4, seed: int = 1):
+        h = _vp()
+        _check(load().scan_planner_create(n_strategies, seed, ctypes.byref(h)))
+        self._h = h
+        self.S = n_strategies
+        self.nparams = int(load().scan_planner_param_count(self._h))
+
+    def get_params(self):
+        import numpy as np
+
+        out = np.zeros(self.nparams, dtype=np.float32)
+        _check(load().scan_planner_get_params(self._h, _ptr(out)))
+        return out
+
+    def set_params(self, params):
+        import numpy as np
+
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        assert p.size == self.nparams
+        _check(load().scan_planner_set_params(self._h, _ptr(p)))
+
+    def forward(self, dev_x, rows, dev_y, stream=None):
+        _check(load().scan_planner_forward(self._h, _ptr(dev_x), rows, _ptr(dev_y), _stream(stream)))
+
+    def gradients(self, dev_x, dev_t, rows, dev_grads, stream=None):
+        loss = ctypes.c_float()
+        _check(load().scan_planner_gradients(self._h, _ptr(dev_x), _ptr(dev_t), rows, _ptr(dev_grads),
+                                             _stream(stream), ctypes.byref(loss)))
+        return float(loss.value)
+
+    def train_step(self, dev_x, dev_t, rows, lr, stream=None, want_loss=False):
+        loss = ctypes.c_float()
+        _check(load().scan_planner_train_step(self._h, _ptr(dev_x), _ptr(dev_t), rows, float(lr),
+                                              _stream(stream), ctypes.byref(loss) if want_loss else None))
+        return float(loss.value) if want_loss else None
+
+    def choose(self, dev_x, rows, dev_choice, stream=None):
+        _check(load().scan_planner_choose(self._h, _ptr(dev_x), rows, _ptr(dev_choice), _stream(stream)))
+
+    def save(self, path):
+        _check(load().scan_planner_save(self._h, path.encode()))
+
+    def load_file(self, path):
+        _check(load().scan_planner_load(self._h, path.encode()))
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            _check(load().scan_planner_destroy(self._h))
+            self._h = _vp(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching scan server over a device-resident table (scan_server_*)."""
+
+    def __init__(self, columns, slots=3, device_bytes_per_slot=1 << 20, max_queue=4096):
+        self.columns = list(columns)
+        n = len(self.columns)
+        self._cols = (_vp * n)(*[c.handle.value for c in self.columns])
+        h = _vp()
+        _check(load().scan_server_create(self._cols, n, slots, device_bytes_per_slot, max_queue,
+                                         ctypes.byref(h)))
+        self._h = h
+
+    def submit(self, col_ids, preds):
+        n = len(col_ids)
+        ids = (ctypes.c_uint32 * n)(*col_ids)
+        pr = (scan_pred * n)(*[scan_pred(int(lo), int(hi)) for lo, hi in preds])
+        q = _u64()
+        _check(load().scan_server_submit(self._h, ids, pr, n, ctypes.byref(q)))
+        return int(q.value)
+
+    def poll(self, query_id, n, wait=False):
+        """(done, results, latency_us); results is a list of scan_result when done."""
+        out = (scan_result * max(n, 1))()
+        lat = ctypes.c_double()
+        done = ctypes.c_int()
+        _check(load().scan_server_poll(self._h, query_id, 1 if wait else 0, out, n, ctypes.byref(lat),
+                                       ctypes.byref(done)))
+        if not done.value:
+            return False, None, None
+        return True, [out[i] for i in range(n)], float(lat.value)
+
+    def stats(self):
+        b, e, r = _u64(), _u64(), _u64()
+        q = _u32()
+        _check(load().scan_server_stats(self._h, ctypes.byref(b), ctypes.byref(e), ctypes.byref(r),
+                                        ctypes.byref(q)))
+        return {"batches": int(b.value), "column_scans": int(e.value), "rejected": int(r.value),
+                "queued": int(q.value)}
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            _check(load().scan_server_destroy(self._h))
+            self._h = _vp(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,178 @@
+"""The planner's CUDA kernels against the fp64 reference, its features against
+values the oracle computes, and what the trained network gains."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import mlp_ref
+from paper_2606_22423_gb300 import gbscan
+from tests._cudart import d2h_u32
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    torch.cuda.init()
+    return gbscan.load()
+
+
+def _data(seed, rows=96):
+    rng = np.random.default_rng(seed)
+    X = rng.uniform(0, 1, size=(rows, 4)).astype(np.float32)
+    T = rng.normal(size=(rows, 4)).astype(np.float32)
+    return X, T
+
+
+def test_forward_matches_fp64_reference():
+    pl = gbscan.Planner(4, seed=7)
+    params = mlp_ref.unflatten(pl.get_params().astype(np.float64))
+    X, _ = _data(0)
+    y = torch.zeros((X.shape[0], 4), dtype=torch.float32, device="cuda")
+    pl.forward(torch.from_numpy(X).cuda(), X.shape[0], y)
+    torch.cuda.synchronize()
+    want, _ = mlp_ref.forward(params, X.astype(np.float64))
+    np.testing.assert_allclose(y.cpu().numpy(), want, rtol=1e-4, atol=1e-4 * np.abs(want).max())
+    pl.close()
+
+
+def test_gradients_match_fp64_reference():
+    pl = gbscan.Planner(4, seed=8)
+    params = mlp_ref.unflatten(pl.get_params().astype(np.float64))
+    X, T = _data(1)
+    g = torch.zeros(pl.nparams, dtype=torch.float32, device="cuda")
+    loss = pl.gradients(torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda(), X.shape[0], g)
+    Y, cache = mlp_ref.forward(params, X.astype(np.float64))
+    want = mlp_ref.flatten(mlp_ref.backward(params, cache, Y, T.astype(np.float64)))
+    got = g.cpu().numpy()
+    assert loss == pytest.approx(mlp_ref.loss(Y, T), rel=1e-4)
+    scale = np.abs(want).max()
+    np.testing.assert_allclose(got, want, rtol=1e-3, atol=1e-3 * scale)
+    pl.close()
+
+
+def test_adam_steps_match_fp64_reference():
+    pl = gbscan.Planner(4, seed=9)
+    params = mlp_ref.unflatten(pl.get_params().astype(np.float64))
+    m, v = mlp_ref.adam_state(params)
+    X, T = _data(2)
+    dx, dt = torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda()
+    for t in range(1, 4):
+        pl.train_step(dx, dt, X.shape[0], 1e-2)
+        Y, cache = mlp_ref.forward(params, X.astype(np.float64))
+        params, m, v = mlp_ref.adam_step(params, mlp_ref.backward(params, cache, Y, T.astype(np.float64)),
+                                         m, v, t, lr=1e-2)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(pl.get_params(), mlp_ref.flatten(params), rtol=2e-3, atol=2e-4)
+    pl.close()
+
+
+def test_training_reduces_loss_and_choose_is_argmin(tmp_path):
+    teacher = mlp_ref.init(31)
+    rng = np.random.default_rng(3)
+    X = rng.uniform(0, 1, size=(512, 4)).astype(np.float32)
+    T = mlp_ref.forward(teacher, X.astype(np.float64))[0].astype(np.float32)
+    pl = gbscan.Planner(4, seed=10)
+    dx, dt = torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda()
+    first = pl.train_step(dx, dt, 512, 3e-3, want_loss=True)
+    for _ in range(600):
+        pl.train_step(dx, dt, 512, 3e-3)
+    last = pl.train_step(dx, dt, 512, 3e-3, want_loss=True)
+    assert last < 0.1 * first
+    y = torch.zeros((512, 4), dtype=torch.float32, device="cuda")
+    ch = torch.zeros(512, dtype=torch.int32, device="cuda")
+    pl.forward(dx, 512, y)
+    pl.choose(dx, 512, ch)
+    torch.cuda.synchronize()
+    assert (ch.cpu().numpy() == y.cpu().numpy().argmin(axis=1)).all()
+    path = str(tmp_path / "planner.bin")
+    pl.save(path)
+    other = gbscan.Planner(4, seed=99)
+    other.load_file(path)
+    np.testing.assert_array_equal(other.get_params(), pl.get_params())
+    pl.close()
+    other.close()
+
+
+def test_features_match_oracle_computation():
+    cols, preds, expect = [], [], []
+    for i, (n, b, p, sigma) in enumerate([(50_000, 7, None, 0.1), (300_000, 16, 0.0, 0.01),
+                                          (33_000, 32, 1.0, 0.5), (5000, 3, 0.01, 1e-3), (1500, 12, None, 1.0)]):
+        v = (synth.uniform_values(i, n, b) if p is None else synth.clustered_values(i, n, b, p))
+        c = gbscan.Column.from_host(v, b)
+        c.zonemap_build()
+        lo, hi = synth.pick_range(100 + i, b, sigma)
+        cols.append(c)
+        preds.append((lo, hi))
+        words = oracle.pack(v, b)
+        nb = (n + 1023) // 1024
+        S = min(32, nb)
+        picks = [j * nb // S for j in range(S)]
+        sample = np.concatenate([oracle.unpack(words[k * 32 * b:(k + 1) * 32 * b],
+                                               min(1024, n - 1024 * k), b) for k in picks])
+        cnt, _ = oracle.scan_values(sample, lo, hi)
+        sig = cnt / sample.size
+        zmin, zmax = oracle.zonemap(words, n, b)
+        span = float(int(zmax.max()) - int(zmin.min()) + 1)
+        c_score = 1.0 - float(np.mean((zmax.astype(np.float64) - zmin + 1) / span))
+        expect.append([b / 32, math.log2(n) / 31, (math.log10(max(sig, 1e-5)) + 5) / 5, c_score])
+    from paper_2606_22423_gb300 import planner as plmod
+
+    got = plmod.features(cols, preds).cpu().numpy()
+    np.testing.assert_allclose(got, np.array(expect, dtype=np.float64), rtol=1e-5, atol=1e-6)
+    assert got[1, 3] > 0.9 and got[2, 3] < 0.1      # sorted vs shuffled
+    for c in cols:
+        c.close()
+
+
+def test_trained_planner_beats_the_fixed_full_scan_on_clustered_low_selectivity_columns():
+    from paper_2606_22423_gb300 import planner as plmod
+
+    s = torch.cuda.Stream()
+    tcols, tpreds = plmod.training_columns(seed=1, count=80, n_lo=1 << 20, n_hi=1 << 25, stream=s)
+    X, T = plmod.collect(tcols, tpreds, s, reps=2)
+    pl = gbscan.Planner(4, seed=3)
+    plmod.train(pl, X, T, steps=800, lr=3e-3)
+    # held-out batch: sorted columns, selective predicates -> zone skipping should win
+    cols, preds = [], []
+    with torch.cuda.stream(s):
+        for i in range(64):
+            b, n = 8 + (i % 20), 1 << 22
+            c = gbscan.Column.from_device(synth.clustered_values_device(500 + i, n, b, 0.0), n, b, stream=s)
+            c.zonemap_build(s)
+            cols.append(c)
+            preds.append(synth.pick_range(900 + i, b, 1e-3))
+    torch.cuda.synchronize()
+    Xe = plmod.features(cols, preds)
+    planned = plmod.choose(pl, Xe)
+    times, results = {}, {}
+    for name, strategies in [("fixed_full", ["branchfree"] * 64), ("planned", planned)]:
+        bt = gbscan.Batch(cols, strategies)
+        results[name] = [r.pair() for r in bt.run(preds)]
+        out = torch.zeros((64, 4), dtype=torch.int64, device="cuda")
+        ts = []
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            bt.run(preds, dev_out=out, host=False)
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        times[name] = sorted(ts)[2]
+        bt.close()
+    assert results["planned"] == results["fixed_full"]          # the plan never changes a result
+    for i in (0, 21, 42, 63):                                     # and those results are the oracle's
+        words = d2h_u32(cols[i].dev_packed, gbscan.scan_packed_words(cols[i].n, cols[i].b))
+        assert results["planned"][i] == oracle.scan_packed(words, cols[i].n, cols[i].b, 0, *preds[i])
+    assert sum(x.startswith("zone") for x in planned) >= 48
+    assert times["planned"] < 0.8 * times["fixed_full"], times
+    for c in cols + tcols:
+        c.close()
+    pl.close()

@@ -1,0 +1,104 @@
+"""Serving: queries that arrive while others run are batched together and
+overlap on the device, yet every query's result equals the query run alone."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from paper_2606_22423_gb300 import gbscan
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    torch.cuda.init()
+    return gbscan.load()
+
+
+@pytest.fixture(scope="module")
+def table():
+    cols, vals = [], []
+    widths = [4, 8, 12, 16, 24, 32]
+    for i in range(12):
+        b, n = widths[i % 6], (1 << 18) + 77 * i
+        v = synth.clustered_values(700 + i, n, b, 0.0) if i % 2 == 0 else synth.uniform_values(700 + i, n, b)
+        c = gbscan.Column.from_host(v, b)
+        c.zonemap_build()
+        cols.append(c)
+        vals.append(v)
+    yield cols, vals
+    for c in cols:
+        c.close()
+
+
+def _queries(cols, count, seed):
+    rng = np.random.default_rng(seed)
+    qs = []
+    for _ in range(count):
+        k = int(rng.integers(1, 9))
+        ids = [int(x) for x in rng.choice(len(cols), size=k, replace=True)]
+        preds = [synth.pick_range(int(rng.integers(1 << 30)), cols[c].b,
+                                  float(synth.log_uniform(rng, 1e-4, 1.0))) for c in ids]
+        qs.append((ids, preds))
+    return qs
+
+
+def test_results_in_the_mix_equal_results_alone(table):
+    cols, vals = table
+    qs = _queries(cols, 300, 1)
+    alone = [[cols[c].run(lo, hi).pair() for c, (lo, hi) in zip(ids, preds)] for ids, preds in qs]
+    for ids, preds in qs[:10]:                       # alone is itself the oracle's answer
+        for c, (lo, hi) in zip(ids, preds):
+            assert cols[c].run(lo, hi).pair() == oracle.scan_values(vals[c], lo, hi)
+    srv = gbscan.Server(cols, slots=3, device_bytes_per_slot=96 * 64)
+    got = [None] * len(qs)
+
+    def submitter(lo_i, hi_i, delay):
+        for i in range(lo_i, hi_i):
+            qid = srv.submit(*qs[i])
+            got[i] = qid
+            time.sleep(delay)
+
+    # two producers with different pacing so queries arrive while batches run
+    t1 = threading.Thread(target=submitter, args=(0, 150, 0.0))
+    t2 = threading.Thread(target=submitter, args=(150, 300, 0.0002))
+    t1.start(); t2.start(); t1.join(); t2.join()
+    lat = []
+    for i, (ids, _) in enumerate(qs):
+        done, res, us = srv.poll(got[i], len(ids), wait=True)
+        assert done
+        assert [r.pair() for r in res] == alone[i], i
+        lat.append(us)
+    st = srv.stats()
+    assert st["column_scans"] == sum(len(ids) for ids, _ in qs)
+    assert st["batches"] < len(qs)                   # queries were batched together
+    assert min(lat) > 0
+    srv.close()
+
+
+def test_admission_queue_limit_and_small_slots(table):
+    cols, _ = table
+    srv = gbscan.Server(cols, slots=1, device_bytes_per_slot=96 * 8, max_queue=4)
+    qs = _queries(cols, 64, 2)
+    ids, busy = [], 0
+    for q in qs:
+        try:
+            ids.append((srv.submit(*q), q))
+        except gbscan.ScanError as e:
+            assert e.status == gbscan.SCAN_EBUSY
+            busy += 1
+    for qid, (cids, preds) in ids:
+        done, res, _ = srv.poll(qid, len(cids), wait=True)
+        assert done and [r.pair() for r in res] == [cols[c].run(lo, hi).pair() for c, (lo, hi) in zip(cids, preds)]
+    assert srv.stats()["rejected"] == busy
+    with pytest.raises(gbscan.ScanError):            # more scans than one slot holds
+        srv.submit(list(range(9)), [(0, 5)] * 9)
+    srv.close()
