@@ -266,7 +266,7 @@ scan_status scan_planner_load(scan_planner *planner, const char *path);
  * batching of COUNT/SUM queries against a device-resident table of columns.
  * A query names n table columns (ids into `cols`), each with its own
  * predicate.  Admission is by device memory: each of `slots` in-flight
- * batches owns device_bytes_per_slot bytes of descriptors and results (96
+ * batches owns device_bytes_per_slot bytes of descriptors and results (112
  * bytes per column scan), and a query waits in the queue until a slot with
  * room for all its scans frees up; a dispatcher thread packs every waiting
  * query that fits into one batched launch on that slot's stream, so batches
@@ -282,6 +282,10 @@ scan_status scan_server_create(scan_column *const *cols, uint32_t ncols, uint32_
 /* Enqueue a query; SCAN_EBUSY when max_queue queries already wait. */
 scan_status scan_server_submit(scan_server *server, const uint32_t *col_ids, const scan_pred *preds,
                                uint32_t n, uint64_t *query_id);
+/* Enqueue nqueries queries at once (all or none): query k uses entries
+ * offsets[k] .. offsets[k+1]-1 of col_ids/preds; ids go to query_ids[k]. */
+scan_status scan_server_submit_many(scan_server *server, uint32_t nqueries, const uint32_t *offsets,
+                                    const uint32_t *col_ids, const scan_pred *preds, uint64_t *query_ids);
 /* *done = 1 and results copied (n >= the query's column count) once the
  * query has completed; wait != 0 blocks until then.  A collected query id is
  * forgotten.  *latency_us (may be NULL) = completion - submission time. */
@@ -329,6 +333,13 @@ scan_status scan_run_packed_noalloc(const uint32_t *dev_packed, uint64_t n, uint
  * maximum): every byte of dev_buf (16-byte aligned, bytes a multiple of 16)
  * is read once and folded into a checksum written to *dev_out (8 bytes). */
 scan_status scan_probe_read(const void *dev_buf, uint64_t bytes, void *stream, uint64_t *dev_out);
+
+/* Failure-path check: one warp waits, with the same bounded wait every
+ * pipeline uses, on a transaction barrier nothing ever completes.  The wait
+ * gives up after limit_ns (at most 1 s) and the call returns SCAN_ETIMEOUT;
+ * the CUDA context stays usable.  Any other status means the timeout path is
+ * broken. */
+scan_status scan_selftest_wait_timeout(uint64_t limit_ns, void *stream);
 
 /* Number of SMs and the persistent grid size the scan kernels use for width b. */
 scan_status scan_launch_shape(uint32_t b, uint32_t *sms, uint32_t *ctas, uint32_t *warps_per_cta,

@@ -56,6 +56,12 @@ int batch_grid()
 
 uint32_t tile_blocks_for(uint32_t b) { return static_cast<uint32_t>(gb::shape_of(static_cast<int>(b)).tile_blocks); }
 
+// Control words after the results: one pop counter per width group (u32),
+// then the status word at u32 index kMaxGroups.
+constexpr size_t kMaxGroups = 64;
+constexpr size_t kCtlWords = 40;  // u64 words: 64 + 1 u32 fit in 33
+constexpr int kBranches = 8;      // parallel chains of width-group kernels in the graph
+
 }  // namespace
 
 struct scan_batch {
@@ -68,40 +74,68 @@ struct scan_batch {
     uint32_t ntiles_k[2] = {0, 0};
     uint32_t chunk_k[2] = {1, 1};
     uint32_t tiles_per_pop = 0;
+    struct Group {
+        int kernel, b;
+        uint32_t first, count, ntiles, chunk;
+    };
+    std::vector<Group> groups;  // one width-specialised launch each
     gb::BatchCol* h_table = nullptr;   // pinned
     gb::BatchCol* d_table = nullptr;
     unsigned long long* d_results = nullptr;  // 4 words per column, then 2 pop counters + status
     scan_result* h_results = nullptr;  // pinned copy of the results
     cudaStream_t capture_stream = nullptr;
+    cudaStream_t branch[8] = {};       // capture-time branches (one graph node chain each)
+    cudaEvent_t fork = nullptr, join[8] = {};
     cudaGraphExec_t graph = nullptr;
 };
 
-cudaError_t gb_launch_batch_branchfree(const gb::BatchParams& p, int grid, cudaStream_t st);
-cudaError_t gb_launch_batch_branchy(const gb::BatchParams& p, int grid, cudaStream_t st);
+cudaError_t gb_launch_batch_branchfree(int b, const gb::BatchParams& p, int grid, cudaStream_t st);
+cudaError_t gb_launch_batch_branchy(int b, const gb::BatchParams& p, int grid, cudaStream_t st);
 
 namespace gb {
-static cudaError_t launch_batch_kernel(bool branchy, const BatchParams& p, int grid, cudaStream_t st)
+static cudaError_t launch_batch_kernel(bool branchy, int b, const BatchParams& p, int grid, cudaStream_t st)
 {
-    return branchy ? gb_launch_batch_branchy(p, grid, st) : gb_launch_batch_branchfree(p, grid, st);
+    return branchy ? gb_launch_batch_branchy(b, p, grid, st) : gb_launch_batch_branchfree(b, p, grid, st);
 }
 }  // namespace gb
 
 namespace {
 
-// Lay out the tiles for the current strategies (branch-free columns first).
+// Lay out the tiles for the current strategies: branch-free columns first,
+// and within each kernel by width, so that at any moment the persistent warps
+// of the whole GPU run the same width's decode code (one kernel holds 32
+// fully unrolled width variants; mixing them on an SM thrashes its
+// instruction cache).
 scan_status layout(scan_batch* bt)
 {
     std::vector<uint32_t> order;
+    std::vector<uint32_t> width(bt->ncols);
+    for (uint32_t i = 0; i < bt->ncols; ++i) {
+        const uint2* zm = nullptr;
+        const uint32_t* pk;
+        uint64_t n;
+        uint32_t b, base;
+        gb_column_view(bt->cols[i], &pk, &n, &b, &base, &zm);
+        width[i] = b;
+    }
     for (int k = 0; k < 2; ++k)
-        for (uint32_t i = 0; i < bt->ncols; ++i)
-            if (bt->kernel_of[i] == k) order.push_back(i);
+        for (uint32_t b = 1; b <= 32; ++b)
+            for (uint32_t i = 0; i < bt->ncols; ++i)
+                if (bt->kernel_of[i] == k && width[i] == b) order.push_back(i);
     const size_t table_bytes = std::max<size_t>(1, bt->ncols) * sizeof(gb::BatchCol);
     std::memset(bt->h_table, 0, table_bytes);
     uint32_t tiles[2] = {0, 0};
     bt->ncol_k[0] = bt->ncol_k[1] = 0;
+    bt->groups.clear();
+    uint32_t group_tiles = 0;
     for (uint32_t j = 0; j < order.size(); ++j) {
         const uint32_t i = order[j];
         const int k = bt->kernel_of[i];
+        if (bt->groups.empty() || bt->groups.back().kernel != k ||
+            bt->groups.back().b != static_cast<int>(width[i])) {
+            bt->groups.push_back({k, static_cast<int>(width[i]), j, 0, 0, 1});
+            group_tiles = 0;
+        }
         const uint2* zm = nullptr;
         const uint32_t* pk;
         uint64_t n;
@@ -114,21 +148,25 @@ scan_status layout(scan_batch* bt)
         d.b = b;
         d.base = base;
         d.tile_blocks = tile_blocks_for(b);
-        d.tile_begin = tiles[k];
+        d.tile_begin = group_tiles;  // tile numbers restart in every width group
         d.out = i;
         const uint64_t nblocks = (n + 1023u) >> 10;
         const uint64_t t = (nblocks + d.tile_blocks - 1) / d.tile_blocks;
-        if (tiles[k] + t > 0xffffffffull) return bfail(SCAN_EINVAL, "too many tiles in one batch");
+        if (group_tiles + t > 0xffffffffull) return bfail(SCAN_EINVAL, "too many tiles in one batch");
+        group_tiles += static_cast<uint32_t>(t);
         tiles[k] += static_cast<uint32_t>(t);
+        bt->groups.back().count += 1;
+        bt->groups.back().ntiles = group_tiles;
         bt->slot_of[i] = j;
         bt->ncol_k[k] += 1;
     }
     const uint32_t warps = static_cast<uint32_t>(batch_grid()) * gb::kBatchWarps;
-    for (int k = 0; k < 2; ++k) {
-        bt->ntiles_k[k] = tiles[k];
+    for (int k = 0; k < 2; ++k) bt->ntiles_k[k] = tiles[k];
+    if (bt->groups.size() > kMaxGroups) return bfail(SCAN_EINVAL, "too many width groups");
+    for (auto& g : bt->groups) {
         // default: about eight pops per warp
-        const uint32_t c = bt->tiles_per_pop ? bt->tiles_per_pop : std::max<uint32_t>(1, tiles[k] / (8 * warps));
-        bt->chunk_k[k] = std::min<uint32_t>(c, 1024);
+        const uint32_t c = bt->tiles_per_pop ? bt->tiles_per_pop : std::max<uint32_t>(1, g.ntiles / (8 * warps));
+        g.chunk = std::min<uint32_t>(c, 1024);
     }
     if (bt->graph) {
         cudaGraphExecDestroy(bt->graph);
@@ -340,12 +378,17 @@ scan_status scan_batch_create(scan_column* const* cols, uint32_t ncols, const sc
         }
     }
     const size_t table_bytes = std::max<size_t>(1, ncols) * sizeof(gb::BatchCol);
-    const size_t res_bytes = (4ull * std::max<uint32_t>(1, ncols) + 4) * sizeof(unsigned long long);
+    const size_t res_bytes = (4ull * std::max<uint32_t>(1, ncols) + kCtlWords) * sizeof(unsigned long long);
     cudaError_t e = cudaMallocHost(reinterpret_cast<void**>(&bt->h_table), table_bytes);
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&bt->d_table), table_bytes);
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&bt->d_results), res_bytes);
     if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&bt->h_results), res_bytes);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&bt->capture_stream, cudaStreamNonBlocking);
+    for (int k = 0; k < kBranches && e == cudaSuccess; ++k) {
+        e = cudaStreamCreateWithFlags(&bt->branch[k], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&bt->join[k], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&bt->fork, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         scan_batch_destroy(bt);
         return bcuda(e, "batch allocation");
@@ -365,6 +408,11 @@ scan_status scan_batch_destroy(scan_batch* bt)
     cudaDeviceSynchronize();
     if (bt->graph) cudaGraphExecDestroy(bt->graph);
     if (bt->capture_stream) cudaStreamDestroy(bt->capture_stream);
+    for (int k = 0; k < kBranches; ++k) {
+        if (bt->branch[k]) cudaStreamDestroy(bt->branch[k]);
+        if (bt->join[k]) cudaEventDestroy(bt->join[k]);
+    }
+    if (bt->fork) cudaEventDestroy(bt->fork);
     if (bt->h_table) cudaFreeHost(bt->h_table);
     if (bt->h_results) cudaFreeHost(bt->h_results);
     if (bt->d_table) cudaFree(bt->d_table);
@@ -426,25 +474,45 @@ scan_status scan_batch_exec(scan_batch* bt, const scan_pred* preds, void* stream
     BT_CUDA(cudaStreamSynchronize(st));
     fill_predicates(bt, preds);
     const size_t table_bytes = std::max<size_t>(1, bt->ncols) * sizeof(gb::BatchCol);
-    const size_t res_words = 4ull * std::max<uint32_t>(1, bt->ncols) + 4;
+    const size_t res_words = 4ull * std::max<uint32_t>(1, bt->ncols) + kCtlWords;
     unsigned long long* ctl = bt->d_results + 4ull * std::max<uint32_t>(1, bt->ncols);
     if (!bt->graph) {
+        // copy descriptors -> reset -> {one kernel per width group, as parallel
+        // branches} -> copy results.  Branches let small groups run side by side
+        // and fill each other's tails; a group's grid is sized to its work.
         cudaStream_t cs = bt->capture_stream;
         BT_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
         cudaMemcpyAsync(bt->d_table, bt->h_table, table_bytes, cudaMemcpyHostToDevice, cs);
         cudaMemsetAsync(bt->d_results, 0, res_words * sizeof(unsigned long long), cs);
-        const gb::BatchCol* tbl[2] = {bt->d_table, bt->d_table + bt->ncol_k[0]};
-        for (int k = 0; k < 2; ++k) {
-            if (!bt->ntiles_k[k]) continue;
+        cudaEventRecord(bt->fork, cs);
+        const int sms = batch_grid();
+        bool used[kBranches] = {};
+        int next_branch = 0;
+        for (size_t gi = 0; gi < bt->groups.size(); ++gi) {
+            const auto& g = bt->groups[gi];
+            if (!g.ntiles) continue;
+            const int k = next_branch++ % kBranches;
+            cudaStream_t bs = bt->branch[k];
+            if (!used[k]) cudaStreamWaitEvent(bs, bt->fork, 0);  // joins the capture
+            used[k] = true;
             gb::BatchParams p{};
-            p.cols = tbl[k];
-            p.ncols = bt->ncol_k[k];
-            p.ntiles = bt->ntiles_k[k];
-            p.chunk = bt->chunk_k[k];
-            p.head = reinterpret_cast<unsigned int*>(ctl) + k;
+            p.cols = bt->d_table + g.first;
+            p.ncols = g.count;
+            p.ntiles = g.ntiles;
+            p.chunk = g.chunk;
+            p.head = reinterpret_cast<unsigned int*>(ctl) + gi;
             p.results = bt->d_results;
-            p.status = reinterpret_cast<unsigned int*>(ctl) + 2;
-            gb::launch_batch_kernel(k == 1, p, batch_grid(), cs);
+            p.status = reinterpret_cast<unsigned int*>(ctl) + kMaxGroups;
+            // about 16 tiles per warp, at most one CTA per SM
+            const uint64_t want = (static_cast<uint64_t>(g.ntiles) + 16 * gb::kBatchWarps - 1) /
+                                  (16 * gb::kBatchWarps);
+            const int grid = static_cast<int>(std::max<uint64_t>(1, std::min<uint64_t>(want, sms)));
+            gb::launch_batch_kernel(g.kernel == 1, g.b, p, grid, bs);
+        }
+        for (int k = 0; k < kBranches; ++k) {
+            if (!used[k]) continue;
+            cudaEventRecord(bt->join[k], bt->branch[k]);
+            cudaStreamWaitEvent(cs, bt->join[k], 0);
         }
         cudaMemcpyAsync(bt->h_results, bt->d_results, res_words * sizeof(unsigned long long),
                         cudaMemcpyDeviceToHost, cs);
@@ -462,7 +530,7 @@ scan_status scan_batch_exec(scan_batch* bt, const scan_pred* preds, void* stream
     if (host_out) {
         BT_CUDA(cudaStreamSynchronize(st));
         const unsigned int status = reinterpret_cast<const unsigned int*>(
-            reinterpret_cast<const unsigned long long*>(bt->h_results) + 4ull * std::max<uint32_t>(1, bt->ncols))[2];
+            reinterpret_cast<const unsigned long long*>(bt->h_results) + 4ull * std::max<uint32_t>(1, bt->ncols))[kMaxGroups];
         if (status) return bfail(SCAN_ETIMEOUT, "a device-side wait timed out in the batch kernel");
         std::memcpy(host_out, bt->h_results, sizeof(scan_result) * bt->ncols);
     }

@@ -60,8 +60,8 @@ struct CountSum {
 };
 
 template <int B, bool BRANCHY>
-__device__ __noinline__ CountSum batch_consume_b(const unsigned char* slot, const SlotMeta m,
-                                                 const BatchCol& c, int lane)
+__device__ __forceinline__ CountSum batch_consume_body(const unsigned char* slot, const SlotMeta m,
+                                                       const BatchCol& c, int lane)
 {
     uint64_t cnt = 0, sum = 0;
     const Lanes L = make_lanes<B>(c.lo, c.wm1);
@@ -73,6 +73,13 @@ __device__ __noinline__ CountSum batch_consume_b(const unsigned char* slot, cons
                             lane < Geo<B>::kTpb, static_cast<uint32_t>(c.n & 1023u), q);
     }
     return CountSum{cnt, sum};
+}
+
+template <int B, bool BRANCHY>
+__device__ __noinline__ CountSum batch_consume_b(const unsigned char* slot, const SlotMeta m,
+                                                 const BatchCol& c, int lane)
+{
+    return batch_consume_body<B, BRANCHY>(slot, m, c, lane);
 }
 
 template <bool BRANCHY, int LO, int HI>
@@ -87,7 +94,10 @@ __device__ __forceinline__ CountSum batch_consume_range(int b, const unsigned ch
     }
 }
 
-template <bool BRANCHY>
+// BFIX = 0: any width (switch per tile).  BFIX = b: every column of the
+// launch has width b, and the decode is inlined (one width's code per kernel
+// keeps the instruction cache warm; a batch runs one such kernel per width).
+template <bool BRANCHY, int BFIX>
 __global__ void __launch_bounds__(kBatchWarps * 32, 1) k_scan_batch(const BatchParams P)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -236,8 +246,12 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 1) k_scan_batch(const BatchP
             }
             phase ^= 1u << s;
             const BatchCol& c = P.cols[m.col];
-            const CountSum r =
-                batch_consume_range<BRANCHY, 1, 32>(static_cast<int>(c.b), slots + s * kBatchSlot, m, c, lane);
+            CountSum r;
+            if constexpr (BFIX > 0)
+                r = batch_consume_body<BFIX, BRANCHY>(slots + s * kBatchSlot, m, c, lane);
+            else
+                r = batch_consume_range<BRANCHY, 1, 32>(static_cast<int>(c.b), slots + s * kBatchSlot, m, c,
+                                                        lane);
             cnt += r.cnt;
             sum += r.sum;
             blocks += m.nk;

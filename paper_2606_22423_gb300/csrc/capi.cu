@@ -200,6 +200,21 @@ __global__ void k_encode(const uint32_t* __restrict__ v, uint64_t n, uint32_t b,
     }
 }
 
+// Waits, with the library's bounded wait, on a transaction barrier that
+// nothing ever completes; the wait gives up after limit_ns and records the
+// timeout in the status word exactly as a lost copy would.
+__global__ void k_selftest_wait(unsigned long long limit_ns, unsigned int* status)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        gb::mbar_init(&bar, 1);
+        gb::fence_mbar_init();
+    }
+    __syncwarp();
+    const bool ok = gb::mbar_wait(&bar, 0u, limit_ns);
+    if (!__all_sync(gb::kFull, ok) && threadIdx.x == 0) atomicOr(status, gb::kErrTimeout);
+}
+
 __global__ void k_read_probe(const uint4* __restrict__ p, uint64_t n16, unsigned long long* out)
 {
     const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
@@ -656,6 +671,24 @@ scan_status scan_probe_read(const void* dev_buf, uint64_t bytes, void* stream, u
                                        reinterpret_cast<unsigned long long*>(dev_out));
     GB_CUDA(cudaGetLastError());
     return SCAN_OK;
+}
+
+scan_status scan_selftest_wait_timeout(uint64_t limit_ns, void* stream)
+{
+    g_err.clear();
+    if (limit_ns == 0 || limit_ns > 1000000000ull) return fail(SCAN_EINVAL, "limit_ns must be in (0, 1e9]");
+    cudaStream_t st = as_stream(stream);
+    unsigned int* flag = nullptr;
+    GB_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&flag), sizeof(unsigned int), st));
+    GB_CUDA(cudaMemsetAsync(flag, 0, sizeof(unsigned int), st));
+    k_selftest_wait<<<1, 32, 0, st>>>(limit_ns, flag);
+    GB_CUDA(cudaGetLastError());
+    unsigned int h = 0;
+    GB_CUDA(cudaMemcpyAsync(&h, flag, sizeof h, cudaMemcpyDeviceToHost, st));
+    GB_CUDA(cudaFreeAsync(flag, st));
+    GB_CUDA(cudaStreamSynchronize(st));
+    if (h & gb::kErrTimeout) return fail(SCAN_ETIMEOUT, "the bounded wait gave up as designed");
+    return fail(SCAN_ECUDA, "the bounded wait did not report its timeout");
 }
 
 scan_status scan_launch_shape(uint32_t b, uint32_t* sms, uint32_t* ctas, uint32_t* warps_per_cta,

@@ -31,7 +31,7 @@
 void gb_set_last_error(const char* msg);
 bool gb_column_view(const scan_column* c, const uint32_t** packed, uint64_t* n, uint32_t* b,
                     uint32_t* base, const uint2** zonemap);
-cudaError_t gb_launch_batch_branchfree(const gb::BatchParams& p, int grid, cudaStream_t st);
+cudaError_t gb_launch_batch_branchfree(int b, const gb::BatchParams& p, int grid, cudaStream_t st);
 
 namespace {
 
@@ -52,7 +52,14 @@ struct Query {
     bool done = false;
 };
 
+constexpr size_t kCtlWords = 40;  // per slot: one pop counter per width (u32), status at u32 index 33
+
+struct Group {
+    uint32_t b, first, count, ntiles;
+};
+
 struct Slot {
+    std::vector<Group> groups;
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
     gb::BatchCol* h_tab = nullptr;
@@ -69,6 +76,7 @@ struct Slot {
 
 struct scan_server {
     std::vector<const scan_column*> table;
+    std::vector<uint32_t> width;  // b of every table column
     std::vector<Slot> slots;
     uint32_t max_entries_per_batch = 0;
     uint32_t max_queue = 0;
@@ -84,6 +92,7 @@ struct scan_server {
     // statistics
     uint64_t batches = 0, entries_launched = 0, rejected = 0;
     std::atomic<unsigned int> device_error{0};
+    char error_text[256] = {0};  // first device-side failure, under mu
 };
 
 namespace {
@@ -91,6 +100,7 @@ namespace {
 uint32_t tile_blocks_for(uint32_t b) { return static_cast<uint32_t>(gb::shape_of(static_cast<int>(b)).tile_blocks); }
 
 void fill_entry(gb::BatchCol& d, const scan_column* col, scan_pred pr, uint32_t out, uint32_t& tiles)
+// tiles: running tile count of the entry's width group (numbering restarts per group)
 {
     const uint2* zm = nullptr;
     const uint32_t* pk;
@@ -121,30 +131,53 @@ void fill_entry(gb::BatchCol& d, const scan_column* col, scan_pred pr, uint32_t 
     tiles += static_cast<uint32_t>((nblocks + d.tile_blocks - 1) / d.tile_blocks);
 }
 
-// Launch one slot's batch (descriptors already in h_tab).
-cudaError_t launch_slot(scan_server* sv, Slot& s, uint32_t ntiles)
+// Launch one slot's batch (descriptors in h_tab, grouped by width); *step names a failing call.
+cudaError_t launch_slot(scan_server* sv, Slot& s, const char** step)
 {
     const uint32_t n = s.entries;
+    *step = "descriptor copy";
     cudaError_t e = cudaMemcpyAsync(s.d_tab, s.h_tab, n * sizeof(gb::BatchCol), cudaMemcpyHostToDevice, s.stream);
-    if (e == cudaSuccess)
-        e = cudaMemsetAsync(s.d_res, 0, (4ull * s.cap + 4) * sizeof(unsigned long long), s.stream);
-    if (e == cudaSuccess && ntiles) {
-        gb::BatchParams p{};
-        p.cols = s.d_tab;
-        p.ncols = n;
-        p.ntiles = ntiles;
-        const uint32_t warps = static_cast<uint32_t>(sv->sms) * gb::kBatchWarps;
-        p.chunk = std::max<uint32_t>(1, std::min<uint32_t>(256, ntiles / (8 * warps)));
-        p.head = reinterpret_cast<unsigned int*>(s.d_res + 4ull * s.cap);
-        p.results = s.d_res;
-        p.status = p.head + 2;
-        e = gb_launch_batch_branchfree(p, sv->sms, s.stream);
+    if (e == cudaSuccess) {
+        *step = "result reset";
+        e = cudaMemsetAsync(s.d_res, 0, (4ull * s.cap + kCtlWords) * sizeof(unsigned long long), s.stream);
     }
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(s.h_res, s.d_res, (4ull * n + 4) * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+    unsigned int* ctl = reinterpret_cast<unsigned int*>(s.d_res + 4ull * s.cap);
+    const uint32_t warps = static_cast<uint32_t>(sv->sms) * gb::kBatchWarps;
+    for (size_t gi = 0; e == cudaSuccess && gi < s.groups.size(); ++gi) {
+        const Group& g = s.groups[gi];
+        if (!g.ntiles) continue;
+        *step = "batch kernel launch";
+        gb::BatchParams p{};
+        p.cols = s.d_tab + g.first;
+        p.ncols = g.count;
+        p.ntiles = g.ntiles;
+        p.chunk = std::max<uint32_t>(1, std::min<uint32_t>(256, g.ntiles / (8 * warps)));
+        p.head = ctl + gi;
+        p.results = s.d_res;
+        p.status = ctl + 33;
+        e = gb_launch_batch_branchfree(static_cast<int>(g.b), p, sv->sms, s.stream);
+    }
+    if (e == cudaSuccess) {
+        // results of the n entries, then the control words (pop counters, status)
+        *step = "result copy";
+        e = cudaMemcpyAsync(s.h_res, s.d_res, 4ull * n * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                             s.stream);
-    if (e == cudaSuccess) e = cudaEventRecord(s.done, s.stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(s.h_res + 4ull * s.cap, s.d_res + 4ull * s.cap, kCtlWords * sizeof(unsigned long long),
+                                cudaMemcpyDeviceToHost, s.stream);
+    }
+    if (e == cudaSuccess) {
+        *step = "completion event";
+        e = cudaEventRecord(s.done, s.stream);
+    }
     return e;
+}
+
+void note_error(scan_server* sv, const char* step, cudaError_t e)
+{
+    if (!sv->error_text[0])
+        snprintf(sv->error_text, sizeof sv->error_text, "%s: %s", step,
+                 e == cudaSuccess ? "device wait timed out" : cudaGetErrorString(e));
 }
 
 void dispatcher_loop(scan_server* sv)
@@ -168,25 +201,49 @@ void dispatcher_loop(scan_server* sv)
         s.queries.clear();
         s.entries = 0;
         uint32_t tiles = 0;
+        std::vector<std::pair<uint32_t, uint32_t>> scans;  // (width, entry) of every column scan
         while (!sv->pending.empty()) {
             Query* q = sv->pending.front();
             if (s.entries + q->cols.size() > s.cap) break;
             sv->pending.pop_front();
             for (size_t j = 0; j < q->cols.size(); ++j)
-                fill_entry(s.h_tab[s.entries + j], sv->table[q->cols[j]], q->preds[j],
-                           static_cast<uint32_t>(s.entries + j), tiles);
+                scans.emplace_back(sv->width[q->cols[j]], static_cast<uint32_t>(s.entries + j));
             s.entries += static_cast<uint32_t>(q->cols.size());
             s.queries.push_back(q);
         }
+        // descriptor order by width (instruction-cache locality); results stay per entry
+        std::stable_sort(scans.begin(), scans.end());
+        std::vector<std::pair<uint32_t, scan_pred>> entry_src(s.entries);
+        {
+            uint32_t e = 0;
+            for (Query* q : s.queries)
+                for (size_t j = 0; j < q->cols.size(); ++j, ++e) entry_src[e] = {q->cols[j], q->preds[j]};
+        }
+        s.groups.clear();
+        for (uint32_t pos = 0; pos < scans.size(); ++pos) {
+            const uint32_t e = scans[pos].second;
+            if (s.groups.empty() || s.groups.back().b != scans[pos].first) {
+                s.groups.push_back({scans[pos].first, pos, 0, 0});
+                tiles = 0;
+            }
+            fill_entry(s.h_tab[pos], sv->table[entry_src[e].first], entry_src[e].second, e, tiles);
+            s.groups.back().count += 1;
+            s.groups.back().ntiles = tiles;
+        }
         if (s.queries.empty()) continue;  // cannot happen: queries are capped at submit
-        s.busy = true;
-        sv->inflight.push_back(free_slot);
+        s.busy = true;  // reserved: the dispatcher alone touches it until it is published
         sv->batches += 1;
         sv->entries_launched += s.entries;
         lk.unlock();
-        const cudaError_t e = launch_slot(sv, s, tiles);
-        if (e != cudaSuccess) sv->device_error.fetch_or(1u);
+        const char* step = "";
+        const cudaError_t e = launch_slot(sv, s, &step);
         lk.lock();
+        if (e != cudaSuccess) {
+            sv->device_error.fetch_or(1u);
+            note_error(sv, step, e);
+        }
+        // publish only now: the completion event of this batch has been recorded
+        sv->inflight.push_back(free_slot);
         sv->cv_done.notify_all();
     }
 }
@@ -203,9 +260,15 @@ void completer_loop(scan_server* sv)
         const cudaError_t e = cudaEventSynchronize(s.done);
         const auto now = Clock::now();
         lk.lock();
-        if (e != cudaSuccess) sv->device_error.fetch_or(1u);
-        const unsigned int status = reinterpret_cast<const unsigned int*>(s.h_res + 4ull * s.entries)[2];
-        if (status) sv->device_error.fetch_or(2u);
+        if (e != cudaSuccess) {
+            sv->device_error.fetch_or(1u);
+            note_error(sv, "completion wait", e);
+        }
+        const unsigned int status = reinterpret_cast<const unsigned int*>(s.h_res + 4ull * s.cap)[33];
+        if (status) {
+            sv->device_error.fetch_or(2u);
+            note_error(sv, "batch kernel", cudaSuccess);
+        }
         uint32_t k = 0;
         for (Query* q : s.queries) {
             q->results.resize(q->cols.size());
@@ -238,6 +301,17 @@ scan_status scan_server_create(scan_column* const* cols, uint32_t ncols, uint32_
     auto* sv = new (std::nothrow) scan_server();
     if (!sv) return sfail(SCAN_ENOMEM, "host allocation failed");
     sv->table.assign(cols, cols + ncols);
+    for (uint32_t i = 0; i < ncols; ++i) {
+        const uint2* zm = nullptr;
+        const uint32_t* pk;
+        uint64_t n;
+        uint32_t b = 0, base;
+        if (!cols[i] || !gb_column_view(cols[i], &pk, &n, &b, &base, &zm)) {
+            delete sv;
+            return sfail(SCAN_EINVAL, "a table column is NULL");
+        }
+        sv->width.push_back(b);
+    }
     sv->max_entries_per_batch = static_cast<uint32_t>(std::min<uint64_t>(cap, 1u << 20));
     sv->max_queue = max_queue ? max_queue : 4096;
     int dev = 0;
@@ -251,9 +325,9 @@ scan_status scan_server_create(scan_column* const* cols, uint32_t ncols, uint32_
         if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&s.h_tab), s.cap * sizeof(gb::BatchCol));
         if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&s.d_tab), s.cap * sizeof(gb::BatchCol));
         if (e == cudaSuccess)
-            e = cudaMalloc(reinterpret_cast<void**>(&s.d_res), (4ull * s.cap + 4) * sizeof(unsigned long long));
+            e = cudaMalloc(reinterpret_cast<void**>(&s.d_res), (4ull * s.cap + kCtlWords) * sizeof(unsigned long long));
         if (e == cudaSuccess)
-            e = cudaMallocHost(reinterpret_cast<void**>(&s.h_res), (4ull * s.cap + 4) * sizeof(unsigned long long));
+            e = cudaMallocHost(reinterpret_cast<void**>(&s.h_res), (4ull * s.cap + kCtlWords) * sizeof(unsigned long long));
         if (e != cudaSuccess) {
             scan_server_destroy(sv);
             return sfail(e == cudaErrorMemoryAllocation ? SCAN_ENOMEM : SCAN_ECUDA, "server slot allocation");
@@ -292,6 +366,51 @@ scan_status scan_server_submit(scan_server* sv, const uint32_t* col_ids, const s
     return SCAN_OK;
 }
 
+scan_status scan_server_submit_many(scan_server* sv, uint32_t nqueries, const uint32_t* offsets,
+                                    const uint32_t* col_ids, const scan_pred* preds, uint64_t* query_ids)
+{
+    gb_set_last_error("");
+    if (!sv || !offsets || !col_ids || !preds || !query_ids) return sfail(SCAN_EINVAL, "null pointer");
+    std::vector<Query*> made;
+    made.reserve(nqueries);
+    const auto now = Clock::now();
+    for (uint32_t k = 0; k < nqueries; ++k) {
+        const uint32_t a = offsets[k], b = offsets[k + 1];
+        if (b <= a || b - a > sv->max_entries_per_batch) {
+            for (Query* q : made) delete q;
+            return sfail(SCAN_EINVAL, "a query is empty or larger than one batch slot");
+        }
+        for (uint32_t j = a; j < b; ++j)
+            if (col_ids[j] >= sv->table.size()) {
+                for (Query* q : made) delete q;
+                return sfail(SCAN_EINVAL, "column id out of range");
+            }
+        auto* q = new (std::nothrow) Query();
+        if (!q) {
+            for (Query* x : made) delete x;
+            return sfail(SCAN_ENOMEM, "host allocation failed");
+        }
+        q->cols.assign(col_ids + a, col_ids + b);
+        q->preds.assign(preds + a, preds + b);
+        q->arrived = now;
+        made.push_back(q);
+    }
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (sv->pending.size() + made.size() > sv->max_queue) {
+        sv->rejected += made.size();
+        for (Query* q : made) delete q;
+        return sfail(SCAN_EBUSY, "admission queue is full");
+    }
+    for (uint32_t k = 0; k < made.size(); ++k) {
+        made[k]->id = sv->next_id++;
+        sv->queries[made[k]->id] = made[k];
+        sv->pending.push_back(made[k]);
+        query_ids[k] = made[k]->id;
+    }
+    sv->cv_work.notify_all();
+    return SCAN_OK;
+}
+
 scan_status scan_server_poll(scan_server* sv, uint64_t query_id, int wait, scan_result* out, uint32_t n,
                              double* latency_us, int* done)
 {
@@ -303,7 +422,11 @@ scan_status scan_server_poll(scan_server* sv, uint64_t query_id, int wait, scan_
     Query* q = it->second;
     if (wait)
         sv->cv_done.wait(lk, [&] { return q->done || sv->device_error.load() != 0; });
-    if (sv->device_error.load()) return sfail(SCAN_ETIMEOUT, "a batch failed on the device");
+    if (sv->device_error.load()) {
+        static thread_local char msg[320];
+        snprintf(msg, sizeof msg, "a batch failed on the device (%s)", sv->error_text);
+        return sfail((sv->device_error.load() & 2u) ? SCAN_ETIMEOUT : SCAN_ECUDA, msg);
+    }
     *done = q->done ? 1 : 0;
     if (!q->done) return SCAN_OK;
     if (n < q->cols.size() || !out) return sfail(SCAN_EINVAL, "result buffer too small");

@@ -69,6 +69,7 @@ SIGNATURES = {
     "scan_column_status": (_st, [_vp, _vp]),
     "scan_probe_read": (_st, [_vp, _u64, _vp, _vp]),
     "scan_launch_shape": (_st, [_u32] + [ctypes.POINTER(_u32)] * 5),
+    "scan_selftest_wait_timeout": (_st, [_u64, _vp]),
     "scan_run_packed_noalloc": (_st, [_vp, _u64, _u32, _u32, scan_pred, _st, _vp, _vp, _vp]),
     "scan_batch_create": (_st, [_vp, _u32, _vp, _u32, _vp, ctypes.POINTER(_vp)]),
     "scan_batch_exec": (_st, [_vp, _vp, _vp, _vp, _vp]),
@@ -90,6 +91,7 @@ SIGNATURES = {
     "scan_planner_load": (_st, [_vp, ctypes.c_char_p]),
     "scan_server_create": (_st, [_vp, _u32, _u32, _u64, _u32, ctypes.POINTER(_vp)]),
     "scan_server_submit": (_st, [_vp, _vp, _vp, _u32, ctypes.POINTER(_u64)]),
+    "scan_server_submit_many": (_st, [_vp, _u32, _vp, _vp, _vp, _vp]),
     "scan_server_poll": (_st, [_vp, _u64, ctypes.c_int, _vp, _u32, ctypes.POINTER(ctypes.c_double),
                                ctypes.POINTER(ctypes.c_int)]),
     "scan_server_stats": (_st, [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64), ctypes.POINTER(_u64),
@@ -421,6 +423,22 @@ class Server:
         q = _u64()
         _check(load().scan_server_submit(self._h, ids, pr, n, ctypes.byref(q)))
         return int(q.value)
+
+    def submit_many(self, queries):
+        """Submit a burst of (col_ids, preds) queries atomically; returns their ids."""
+        offs = [0]
+        ids, prs = [], []
+        for c, p in queries:
+            ids += list(c)
+            prs += list(p)
+            offs.append(len(ids))
+        n = len(queries)
+        o = (ctypes.c_uint32 * (n + 1))(*offs)
+        ci = (ctypes.c_uint32 * max(len(ids), 1))(*ids)
+        pr = (scan_pred * max(len(prs), 1))(*[scan_pred(int(lo), int(hi)) for lo, hi in prs])
+        out = (ctypes.c_uint64 * max(n, 1))()
+        _check(load().scan_server_submit_many(self._h, n, o, ci, pr, out))
+        return [int(out[i]) for i in range(n)]
 
     def poll(self, query_id, n, wait=False):
         """(done, results, latency_us); results is a list of scan_result when done."""

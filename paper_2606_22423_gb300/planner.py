@@ -61,13 +61,21 @@ def features(columns, preds, stream=None):
 
 
 def collect(columns, preds, stream, reps=3):
-    """Features (GPU tensor) and log-time labels (GPU tensor, ncols x 4)."""
+    """Features (GPU tensor) and log-time labels (GPU tensor, ncols x 4).
+
+    A label is the marginal device time of the strategy on the column: the
+    one-entry batch's time minus the same batch with an empty predicate
+    (which launches the same kernels and graph but reads no data), plus 1 us,
+    in log milliseconds.  Without the subtraction the fixed per-graph cost
+    hides the differences between strategies on all but the largest columns."""
     torch = _torch()
     X = features(columns, preds, stream)
     T = np.zeros((len(columns), len(STRATEGIES)), dtype=np.float32)
     for i, (c, (lo, hi)) in enumerate(zip(columns, preds)):
+        base = time_strategy(c, 0, 0, "branchfree", stream, reps)
         for s, name in enumerate(STRATEGIES):
-            T[i, s] = math.log(max(time_strategy(c, lo, hi, name, stream, reps), 1e-4))
+            t = time_strategy(c, lo, hi, name, stream, reps)
+            T[i, s] = math.log(max(t - base, 0.0) + 1e-3)
     return X, torch.from_numpy(T).cuda()
 
 
@@ -101,7 +109,7 @@ def choose_law(batch, X, beta_gbs, t_dec_gvals, stream=None):
     return [STRATEGIES[i] for i in out.cpu().tolist()]
 
 
-def training_columns(seed, count=160, n_lo=1 << 20, n_hi=1 << 26, stream=None):
+def training_columns(seed, count=160, n_lo=1 << 22, n_hi=1 << 27, stream=None):
     """Varied training columns: b, N, order and sigma spread over the planner's domain."""
     import synth
 

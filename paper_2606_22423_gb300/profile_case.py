@@ -33,8 +33,12 @@ def main():
     ap.add_argument("--strategy", default="branchfree")
     ap.add_argument("--order", default="uniform", choices=["uniform", "sorted", "swapped"])
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--batch", type=int, default=0,
+                    help="scan a batch of this many mixed columns (batched workload recipe, scaled)")
     a = ap.parse_args()
     gbscan.load()
+    if a.batch:
+        return batch_case(a)
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
         seed = synth.seed_for(7, a.b)
@@ -63,6 +67,44 @@ def main():
     print(json.dumps({"b": a.b, "n": a.n, "strategy": a.strategy, "order": a.order, "ms": ms,
                       "gbs": nbytes / (ms * 1e-3) / 1e9, "count": r[0], "sum": r[1], "blocks": r[2]}))
     col.close()
+
+
+def batch_case(a):
+    """The batched workload recipe scaled to a.batch columns and a.n values in total."""
+    import torch
+
+    import synth
+    from paper_2606_22423_gb300 import gbscan
+
+    s = torch.cuda.Stream()
+    spec = synth.batch_spec(synth.seed_for(4), ncols=a.batch, total=a.n)
+    cols, preds = [], []
+    with torch.cuda.stream(s):
+        for i, (n, b, p, sigma) in enumerate(spec):
+            v = (synth.uniform_values_device(synth.seed_for(4, i), n, b) if p is None
+                 else synth.clustered_values_device(synth.seed_for(4, i), n, b, p))
+            c = gbscan.Column.from_device(v, n, b, stream=s)
+            c.zonemap_build(s)
+            cols.append(c)
+            preds.append(synth.pick_range(synth.seed_for(4, i, 1), b, sigma))
+    torch.cuda.synchronize()
+    bt = gbscan.Batch(cols, [a.strategy] * len(cols))
+    parr = gbscan.Batch.pred_array(preds)
+    out = torch.zeros((len(cols), 4), dtype=torch.int64, device="cuda")
+    ms = 0.0
+    for _ in range(a.reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        bt.run(parr, stream=s, dev_out=out, host=False)
+        e1.record(s)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+    nbytes = sum(gbscan.scan_packed_words(x[0], x[1]) * 4 for x in spec)
+    print(json.dumps({"batch": len(cols), "values": sum(x[0] for x in spec), "strategy": a.strategy, "ms": ms,
+                      "gbs": nbytes / (ms * 1e-3) / 1e9}))
+    bt.close()
+    for c in cols:
+        c.close()
 
 
 if __name__ == "__main__":

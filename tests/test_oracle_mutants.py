@@ -1,0 +1,137 @@
+"""The oracle's pins catch plausible mistakes: each mutant below is the oracle
+source with one planted error, compiled on the CPU; the pin checks must fail
+on every mutant and pass on the unmodified source."""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+import synth
+from tests.test_oracle import hist_count_sum, layout_by_bits
+
+SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "oracle", "gbscan_oracle.c")
+
+MUTANTS = {
+    "inclusive upper bound": [("(int64_t)base;\n        if (lo <= v && v < hi) {",
+                               "(int64_t)base;\n        if (lo <= v && v <= hi) {")],
+    "base not added back": [("int64_t v = (int64_t)code_at(words, i, b) + (int64_t)base;",
+                             "int64_t v = (int64_t)code_at(words, i, b);")],
+    "zone skip off by one": [("if ((int64_t)zmax[k] < lo || (int64_t)zmin[k] >= hi) continue;",
+                              "if ((int64_t)zmax[k] <= lo || (int64_t)zmin[k] >= hi) continue;")],
+    "tail padding in zone map": [("        uint64_t last = first + BLOCK_VALUES < n ? first + BLOCK_VALUES : n;\n"
+                                  "        uint32_t mn = 0xFFFFFFFFu, mx = 0;",
+                                  "        uint64_t last = first + BLOCK_VALUES;\n"
+                                  "        uint32_t mn = 0xFFFFFFFFu, mx = 0;")],
+    "top bit of each code dropped": [("return (uint32_t)((window >> off) & ((1ull << b) - 1ull));",
+                                      "return (uint32_t)((window >> off) & ((1ull << (b - 1)) - 1ull));")],
+    "lane and row swapped": [("uint32_t lane = (uint32_t)(j % LANES);\n        uint64_t row = j / LANES;",
+                              "uint32_t lane = (uint32_t)(j / LANES);\n        uint64_t row = j % LANES;"),
+                             ("uint32_t lane = (uint32_t)(j % LANES);\n    uint64_t row = j / LANES;",
+                              "uint32_t lane = (uint32_t)(j / LANES);\n    uint64_t row = j % LANES;")],
+    "rows in reverse order": [("uint64_t p = row * b;            /* first stream bit of this value */",
+                               "uint64_t p = (31 - row) * b;     /* first stream bit of this value */"),
+                              ("    uint64_t p = row * b;\n    uint64_t w = p / 32;",
+                               "    uint64_t p = (31 - row) * b;\n    uint64_t w = p / 32;")],
+}
+
+
+class Lib:
+    """ctypes view of one compiled oracle variant."""
+
+    def __init__(self, path):
+        self.l = ctypes.CDLL(path)
+        u32p = np.ctypeslib.ndpointer(dtype=np.uint32, flags="C_CONTIGUOUS")
+        i64, u64, u32 = ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32
+        self.l.oracle_pack.argtypes = [u32p, u64, u32, u32, u32p]
+        self.l.oracle_unpack.argtypes = [u32p, u64, u32, u32, u32p]
+        self.l.oracle_scan_packed.argtypes = [u32p, u64, u32, u32, i64, i64, ctypes.POINTER(i64),
+                                              ctypes.POINTER(i64)]
+        self.l.oracle_zonemap.argtypes = [u32p, u64, u32, u32, u32p, u32p]
+        self.l.oracle_scan_zoneskip.argtypes = [u32p, u32p, u32p, u64, u32, u32, i64, i64, ctypes.POINTER(i64),
+                                                ctypes.POINTER(i64), ctypes.POINTER(u64)]
+
+    def pack(self, v, b, base=0):
+        out = np.zeros(((v.size + 1023) // 1024) * 32 * b, np.uint32)
+        assert self.l.oracle_pack(v, v.size, b, base, out) == 0
+        return out
+
+    def unpack(self, w, n, b, base=0):
+        out = np.zeros(n, np.uint32)
+        self.l.oracle_unpack(w, n, b, base, out)
+        return out
+
+    def scan(self, w, n, b, base, lo, hi):
+        c, s = ctypes.c_int64(), ctypes.c_int64()
+        self.l.oracle_scan_packed(w, n, b, base, lo, hi, ctypes.byref(c), ctypes.byref(s))
+        return c.value, s.value
+
+    def zonemap(self, w, n, b, base=0):
+        nb = (n + 1023) // 1024
+        mn, mx = np.zeros(nb, np.uint32), np.zeros(nb, np.uint32)
+        self.l.oracle_zonemap(w, n, b, base, mn, mx)
+        return mn, mx
+
+    def zoneskip(self, w, mn, mx, n, b, base, lo, hi):
+        c, s, t = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_uint64()
+        self.l.oracle_scan_zoneskip(w, mn, mx, n, b, base, lo, hi, ctypes.byref(c), ctypes.byref(s), ctypes.byref(t))
+        return c.value, s.value, t.value
+
+
+def pins(o):
+    """A compact copy of the independent pins (layout bits, round trip, brute force,
+    frame of reference, zone maps, zone-skip exactness and skip rule)."""
+    for b in (3, 8, 13, 32):
+        for n in (1025, 4096 + 7):
+            v = synth.uniform_values(synth.seed_for(77, b, n), n, b)
+            w = o.pack(v, b)
+            np.testing.assert_array_equal(w, layout_by_bits(v, b, 0))
+            np.testing.assert_array_equal(o.unpack(w, n, b), v)
+    v = synth.uniform_values(5, 1025, 3)
+    w = o.pack(v, 3)
+    for lo in range(-1, 10):
+        for hi in range(-1, 10):
+            assert o.scan(w, 1025, 3, 0, lo, hi) == hist_count_sum(v, lo, hi)
+    base, b = 1000, 6
+    v = synth.uniform_values(6, 3000, b, base)
+    w = o.pack(v, b, base)
+    for lo, hi in [(base, base + 64), (base + 5, base + 40)]:
+        m = (v >= lo) & (v < hi)
+        assert o.scan(w, 3000, b, base, lo, hi) == (int(m.sum()), int(v[m].astype(np.int64).sum()))
+    n, b = 5000, 12
+    v = synth.clustered_values(7, n, b, 0.0, 3)
+    w = o.pack(v, b, 3)
+    mn, mx = o.zonemap(w, n, b, 3)
+    pad = np.concatenate([v, np.full(5 * 1024 - n, v[-1], np.uint32)]).reshape(5, 1024)
+    np.testing.assert_array_equal(mn, pad.min(axis=1))
+    np.testing.assert_array_equal(mx, pad.max(axis=1))
+    for lo, hi in [(int(v[1500]), int(v[1500]) + 1), (int(v[2047]), int(v[3100])), (int(mx[0]), int(mx[0]) + 9)]:
+        c, s, t = o.zoneskip(w, mn, mx, n, b, 3, lo, hi)
+        m = (v >= lo) & (v < hi)
+        assert (c, s) == (int(m.sum()), int(v[m].astype(np.int64).sum()))
+        assert t == int(np.sum(~((mx < lo) | (mn >= hi))))
+
+
+def _compile(tmpdir, name, text):
+    src = os.path.join(tmpdir, f"{name}.c")
+    lib = os.path.join(tmpdir, f"{name}.so")
+    with open(src, "w") as f:
+        f.write(text)
+    subprocess.check_call(["gcc", "-O1", "-std=c99", "-fPIC", "-shared", "-pthread", "-o", lib, src])
+    return Lib(lib)
+
+
+def test_pins_pass_on_the_oracle(tmp_path):
+    pins(_compile(str(tmp_path), "original", open(SRC).read()))
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_the_mutant(tmp_path, name):
+    text = open(SRC).read()
+    for old, new in MUTANTS[name]:
+        assert text.count(old) == 1, f"mutation anchor not found once: {old!r}"
+        text = text.replace(old, new)
+    o = _compile(str(tmp_path), "mutant", text)
+    with pytest.raises(AssertionError):
+        pins(o)

@@ -136,7 +136,7 @@ def test_trained_planner_beats_the_fixed_full_scan_on_clustered_low_selectivity_
     from paper_2606_22423_gb300 import planner as plmod
 
     s = torch.cuda.Stream()
-    tcols, tpreds = plmod.training_columns(seed=1, count=80, n_lo=1 << 20, n_hi=1 << 25, stream=s)
+    tcols, tpreds = plmod.training_columns(seed=1, count=80, n_lo=1 << 22, n_hi=1 << 26, stream=s)
     X, T = plmod.collect(tcols, tpreds, s, reps=2)
     pl = gbscan.Planner(4, seed=3)
     plmod.train(pl, X, T, steps=800, lr=3e-3)

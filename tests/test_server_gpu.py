@@ -58,7 +58,7 @@ def test_results_in_the_mix_equal_results_alone(table):
     for ids, preds in qs[:10]:                       # alone is itself the oracle's answer
         for c, (lo, hi) in zip(ids, preds):
             assert cols[c].run(lo, hi).pair() == oracle.scan_values(vals[c], lo, hi)
-    srv = gbscan.Server(cols, slots=3, device_bytes_per_slot=96 * 64)
+    srv = gbscan.Server(cols, slots=3, device_bytes_per_slot=112 * 64)
     got = [None] * len(qs)
 
     def submitter(lo_i, hi_i, delay):
@@ -67,10 +67,14 @@ def test_results_in_the_mix_equal_results_alone(table):
             got[i] = qid
             time.sleep(delay)
 
-    # two producers with different pacing so queries arrive while batches run
-    t1 = threading.Thread(target=submitter, args=(0, 150, 0.0))
-    t2 = threading.Thread(target=submitter, args=(150, 300, 0.0002))
-    t1.start(); t2.start(); t1.join(); t2.join()
+    # two producers with different pacing so queries arrive while batches run ...
+    t1 = threading.Thread(target=submitter, args=(0, 100, 0.0))
+    t2 = threading.Thread(target=submitter, args=(100, 200, 0.0002))
+    t1.start(); t2.start()
+    # ... and bursts that must be packed several queries to a launch
+    for k in range(200, 300, 25):
+        got[k:k + 25] = srv.submit_many(qs[k:k + 25])
+    t1.join(); t2.join()
     lat = []
     for i, (ids, _) in enumerate(qs):
         done, res, us = srv.poll(got[i], len(ids), wait=True)
@@ -86,7 +90,7 @@ def test_results_in_the_mix_equal_results_alone(table):
 
 def test_admission_queue_limit_and_small_slots(table):
     cols, _ = table
-    srv = gbscan.Server(cols, slots=1, device_bytes_per_slot=96 * 8, max_queue=4)
+    srv = gbscan.Server(cols, slots=1, device_bytes_per_slot=112 * 8, max_queue=4)
     qs = _queries(cols, 64, 2)
     ids, busy = [], 0
     for q in qs:
