@@ -368,7 +368,9 @@ def run_ours(args, world, rank, local):
                 "time_share_of_step": share,
                 "traffic": prof["dram_bytes_per_launch"] if prof else None,
                 "traffic_algorithmic": prof["algorithmic_bytes_per_launch"] if prof else None,
-                "traffic_case": prof["case"] if prof else None}
+                "traffic_case": prof["case"] if prof else None,
+                "traffic_ratio": (round(prof["dram_bytes_per_launch"] / prof["algorithmic_bytes_per_launch"], 4)
+                                  if prof else None)}
 
     # ---- realised selectivities
     realised = {}
@@ -465,6 +467,8 @@ def run_ours(args, world, rank, local):
     for c in cols.values():
         c.close()
     torch.cuda.empty_cache()
+    plain = None if args.no_extra else run_plain(args, dev, stream, gbscan, beta_read)
+    zone = None if args.no_extra else run_zone_sweep(args, dev, stream, gbscan)
     tdec = [law["branchfree"]["t_dec_gvals"], law["branchy"]["t_dec_gvals"],
             law["branchfree"]["t_dec_gvals"], law["branchy"]["t_dec_gvals"]]
     batched = None if args.no_batch else run_batched(args, dev, stream, gbscan, beta_read, tdec)
@@ -484,6 +488,8 @@ def run_ours(args, world, rank, local):
         "law": law,
         "per_b": per_b,
         "branch_crossover": branch,
+        "plain_scan": plain,
+        "zone_sweep": zone,
         "batched": batched,
         "serving": serving,
         "realised_sigma": realised,
@@ -495,6 +501,125 @@ def run_ours(args, world, rank, local):
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def run_zone_sweep(args, dev, stream, gbscan):
+    """Zone-map clustering sweep: N = 2^30 values at b = 16, sorted then a fraction p
+    displaced; zone skip vs full scan at each sigma (exact equality checked)."""
+    import torch
+
+    n, b = 1 << 30, 16
+    out = {"workload": "zone sweep: N=2^30 at b=16, sorted then p in {0,0.01,0.1,1} displaced, "
+                       "sigma in {1e-4,1e-3,1e-2,0.1,0.5}", "rows": []}
+    res = torch.zeros((2, 4), dtype=torch.int64, device=dev)
+    for pi, p in enumerate([0.0, 0.01, 0.1, 1.0]):
+        with torch.cuda.stream(stream):
+            v = synth.clustered_values_device(synth.seed_for(3, pi), n, b, p, device=dev)
+            col = gbscan.Column.from_device(v, n, b, stream=stream)
+            del v
+            col.zonemap_build(stream)
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        for si, sigma in enumerate([1e-4, 1e-3, 1e-2, 0.1, 0.5]):
+            lo, hi = synth.pick_range(synth.seed_for(3, pi, si + 1), b, sigma)
+            ts = {}
+            for k, strat in enumerate(["branchfree", "zone_bf"]):
+                col.run_async(lo, hi, res[k], strat, stream)
+                vals = []
+                for _ in range(3):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    col.run_async(lo, hi, res[k], strat, stream)
+                    e1.record(stream)
+                    e1.synchronize()
+                    vals.append(e0.elapsed_time(e1))
+                ts[strat] = statistics.median(vals)
+            col.status(stream)
+            r = res.cpu().numpy()
+            out["rows"].append({"p": p, "sigma": sigma, "realised_sigma": round(int(r[0, 0]) / n, 6),
+                                "ms_full": round(ts["branchfree"], 4), "ms_zone": round(ts["zone_bf"], 4),
+                                "speedup": round(ts["branchfree"] / ts["zone_bf"], 2),
+                                "blocks_read_fraction": round(int(r[1, 2]) / int(r[0, 2]), 6),
+                                "exact": bool((r[0, :2] == r[1, :2]).all())})
+        col.close()
+        torch.cuda.empty_cache()
+    return out
+
+
+def run_plain(args, dev, stream, gbscan, beta_read):
+    """Plain single-column scan (N = 2^24, b = 8, sigma = 0.1): 16 MiB fits in L2, so it is
+    timed both after an L2 flush (HBM) and warm (the 'sub-LLC throughput > beta' control)."""
+    import torch
+
+    n, b = 1 << 24, 8
+    with torch.cuda.stream(stream):
+        v = synth.uniform_values_device(synth.seed_for(1), n, b, device=dev)
+        col = gbscan.Column.from_device(v, n, b, stream=stream)
+        del v
+    lo, hi = synth.pick_range(synth.seed_for(1, 0, 1), b, 0.1)
+    res = torch.zeros(4, dtype=torch.int64, device=dev)
+    flush = torch.empty(1 << 28, dtype=torch.int32, device=dev)   # 1 GiB > 129 MB L2
+    nbytes = gbscan.scan_packed_words(n, b) * 4
+    cold, warm = [], []
+    for _ in range(7):
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        col.run_async(lo, hi, res, "branchfree", stream)
+        e1.record(stream)
+        e1.synchronize()
+        cold.append(e0.elapsed_time(e1))
+    for _ in range(7):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        col.run_async(lo, hi, res, "branchfree", stream)
+        e1.record(stream)
+        e1.synchronize()
+        warm.append(e0.elapsed_time(e1))
+    col.status(stream)
+    r = res.cpu().tolist()
+    col.close()
+    del flush
+    torch.cuda.empty_cache()
+    mc, mw = statistics.median(cold), statistics.median(warm)
+    # negative control (iii) of the paper: data resident in the last-level cache is
+    # read faster than beta.  At b = 8 the kernel is decode-bound, so the control
+    # uses b = 32 (64 MiB, inside the 129 MB L2) where decode is cheap.
+    with torch.cuda.stream(stream):
+        v = synth.uniform_values_device(synth.seed_for(1, 1), n, 32, device=dev)
+        c32 = gbscan.Column.from_device(v, n, 32, stream=stream)
+        del v
+    flush = torch.empty(1 << 28, dtype=torch.int32, device=dev)
+    lo32, hi32 = synth.pick_range(synth.seed_for(1, 1, 1), 32, 0.1)
+    cold32, warm32 = [], []
+    for reps, sink in ((7, cold32), (7, warm32)):
+        for _ in range(reps):
+            if sink is cold32:
+                with torch.cuda.stream(stream):
+                    flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            c32.run_async(lo32, hi32, res, "branchfree", stream)
+            e1.record(stream)
+            e1.synchronize()
+            sink.append(e0.elapsed_time(e1))
+    c32.status(stream)
+    c32.close()
+    del flush
+    torch.cuda.empty_cache()
+    b32 = n * 4
+    gc32 = b32 / (statistics.median(cold32) * 1e-3) / 1e9
+    gw32 = b32 / (statistics.median(warm32) * 1e-3) / 1e9
+    return {"workload": "plain scan: N=2^24 uniform in [0,2^8), b=8, sigma=0.1 (median of 7)",
+            "l2_control": {"case": "N=2^24 at b=32 (64 MiB, L2-resident when warm)",
+                           "gbs_l2_flushed": round(gc32, 1), "gbs_l2_warm": round(gw32, 1),
+                           "beta_read_gbs": round(beta_read, 1), "warm_above_beta_read": bool(gw32 > beta_read)},
+            "count": r[0], "sum": r[1], "realised_sigma": round(r[0] / n, 6),
+            "ms_l2_flushed": round(mc, 5), "gbs_l2_flushed": round(nbytes / (mc * 1e-3) / 1e9, 1),
+            "ms_l2_warm": round(mw, 5), "gbs_l2_warm": round(nbytes / (mw * 1e-3) / 1e9, 1),
+            "gvals_per_s_warm": round(n / (mw * 1e-3) / 1e9, 1),
+            "warm_above_beta_read": bool(nbytes / (mw * 1e-3) / 1e9 > beta_read)}
 
 
 BATCH_WORKLOAD = ("batched: 4096 columns, lengths log-uniform in [2^10, 2^26] scaled to 2^31 values in "
@@ -740,6 +865,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the plain-scan and zone-sweep sections")
     ap.add_argument("--serve-seconds", type=float, default=1.5)
     args = ap.parse_args()
     if args.warmup < 3:

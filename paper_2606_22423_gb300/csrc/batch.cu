@@ -77,8 +77,12 @@ struct scan_batch {
     struct Group {
         int kernel, b;
         uint32_t first, count, ntiles, chunk;
+        int grid;
+        uint32_t chunk_off;  // offset of this group's chunk -> column table
     };
     std::vector<Group> groups;  // one width-specialised launch each
+    uint32_t* d_chunk_col = nullptr;  // all groups' chunk -> first-column tables
+    size_t chunk_cap = 0;
     gb::BatchCol* h_table = nullptr;   // pinned
     gb::BatchCol* d_table = nullptr;
     unsigned long long* d_results = nullptr;  // 4 words per column, then 2 pop counters + status
@@ -160,14 +164,38 @@ scan_status layout(scan_batch* bt)
         bt->slot_of[i] = j;
         bt->ncol_k[k] += 1;
     }
-    const uint32_t warps = static_cast<uint32_t>(batch_grid()) * gb::kBatchWarps;
     for (int k = 0; k < 2; ++k) bt->ntiles_k[k] = tiles[k];
     if (bt->groups.size() > kMaxGroups) return bfail(SCAN_EINVAL, "too many width groups");
+    // per group: a grid sized to its work (about 16 tiles per warp, at most one
+    // CTA per SM), pops of about a quarter of a warp's share (at least 4
+    // tiles), and a host-built table of each pop's first column
+    std::vector<uint32_t> chunk_col;
+    const int sms = batch_grid();
     for (auto& g : bt->groups) {
-        // default: about eight pops per warp
-        const uint32_t c = bt->tiles_per_pop ? bt->tiles_per_pop : std::max<uint32_t>(1, g.ntiles / (8 * warps));
+        const uint64_t want = (static_cast<uint64_t>(g.ntiles) + 16 * gb::kBatchWarps - 1) / (16 * gb::kBatchWarps);
+        g.grid = static_cast<int>(std::max<uint64_t>(1, std::min<uint64_t>(want, sms)));
+        const uint32_t warps = static_cast<uint32_t>(g.grid) * gb::kBatchWarps;
+        const uint32_t c = bt->tiles_per_pop ? bt->tiles_per_pop : std::max<uint32_t>(4, g.ntiles / (4 * warps));
         g.chunk = std::min<uint32_t>(c, 1024);
+        g.chunk_off = static_cast<uint32_t>(chunk_col.size());
+        uint32_t col = g.first;
+        for (uint64_t t0 = 0; t0 < g.ntiles; t0 += g.chunk) {
+            while (col + 1 < g.first + g.count && bt->h_table[col + 1].tile_begin <= t0) ++col;
+            chunk_col.push_back(col - g.first);
+        }
     }
+    if (chunk_col.size() > bt->chunk_cap) {
+        if (bt->d_chunk_col) cudaFree(bt->d_chunk_col);
+        bt->d_chunk_col = nullptr;
+        bt->chunk_cap = 0;
+        if (cudaMalloc(reinterpret_cast<void**>(&bt->d_chunk_col), chunk_col.size() * sizeof(uint32_t)) != cudaSuccess)
+            return bfail(SCAN_ENOMEM, "chunk table allocation");
+        bt->chunk_cap = chunk_col.size();
+    }
+    if (!chunk_col.empty() &&
+        cudaMemcpy(bt->d_chunk_col, chunk_col.data(), chunk_col.size() * sizeof(uint32_t), cudaMemcpyHostToDevice) !=
+            cudaSuccess)
+        return bfail(SCAN_ECUDA, "chunk table upload");
     if (bt->graph) {
         cudaGraphExecDestroy(bt->graph);
         bt->graph = nullptr;
@@ -417,6 +445,7 @@ scan_status scan_batch_destroy(scan_batch* bt)
     if (bt->h_results) cudaFreeHost(bt->h_results);
     if (bt->d_table) cudaFree(bt->d_table);
     if (bt->d_results) cudaFree(bt->d_results);
+    if (bt->d_chunk_col) cudaFree(bt->d_chunk_col);
     delete bt;
     return SCAN_OK;
 }
@@ -485,7 +514,6 @@ scan_status scan_batch_exec(scan_batch* bt, const scan_pred* preds, void* stream
         cudaMemcpyAsync(bt->d_table, bt->h_table, table_bytes, cudaMemcpyHostToDevice, cs);
         cudaMemsetAsync(bt->d_results, 0, res_words * sizeof(unsigned long long), cs);
         cudaEventRecord(bt->fork, cs);
-        const int sms = batch_grid();
         bool used[kBranches] = {};
         int next_branch = 0;
         for (size_t gi = 0; gi < bt->groups.size(); ++gi) {
@@ -497,17 +525,14 @@ scan_status scan_batch_exec(scan_batch* bt, const scan_pred* preds, void* stream
             used[k] = true;
             gb::BatchParams p{};
             p.cols = bt->d_table + g.first;
+            p.chunk_col = bt->d_chunk_col + g.chunk_off;
             p.ncols = g.count;
             p.ntiles = g.ntiles;
             p.chunk = g.chunk;
             p.head = reinterpret_cast<unsigned int*>(ctl) + gi;
             p.results = bt->d_results;
             p.status = reinterpret_cast<unsigned int*>(ctl) + kMaxGroups;
-            // about 16 tiles per warp, at most one CTA per SM
-            const uint64_t want = (static_cast<uint64_t>(g.ntiles) + 16 * gb::kBatchWarps - 1) /
-                                  (16 * gb::kBatchWarps);
-            const int grid = static_cast<int>(std::max<uint64_t>(1, std::min<uint64_t>(want, sms)));
-            gb::launch_batch_kernel(g.kernel == 1, g.b, p, grid, bs);
+            gb::launch_batch_kernel(g.kernel == 1, g.b, p, g.grid, bs);
         }
         for (int k = 0; k < kBranches; ++k) {
             if (!used[k]) continue;

@@ -34,10 +34,10 @@ struct BatchCol {
 
 struct BatchParams {
     const BatchCol* cols;
+    const uint32_t* chunk_col;     // first column of every pop-sized chunk, or null (binary search)
     uint32_t ncols;
     uint32_t ntiles;
     uint32_t chunk;                // tiles per atomic pop
-    uint32_t pad;
     unsigned int* head;            // pop counter, zero before the launch
     unsigned long long* results;   // per output slot: count, sum, blocks, 0
     unsigned int* status;
@@ -131,14 +131,17 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 1) k_scan_batch(const BatchP
             }
             t_next = start;
             t_end = min(start + P.chunk, P.ntiles);
-            // locate the column by binary search over tile_begin
-            uint32_t lo = 0, hi = P.ncols - 1;
-            while (lo < hi) {
-                const uint32_t mid = (lo + hi + 1) >> 1;
-                if (__ldg(&P.cols[mid].tile_begin) <= start) lo = mid;
-                else hi = mid - 1;
+            if (P.chunk_col) {  // host-built table: one load per pop
+                col = __ldg(&P.chunk_col[start / P.chunk]);
+            } else {            // binary search over tile_begin
+                uint32_t lo = 0, hi = P.ncols - 1;
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi + 1) >> 1;
+                    if (__ldg(&P.cols[mid].tile_begin) <= start) lo = mid;
+                    else hi = mid - 1;
+                }
+                col = lo;
             }
-            col = lo;
         }
         t = t_next++;
         while (col + 1 < P.ncols && __ldg(&P.cols[col + 1].tile_begin) <= t) ++col;
