@@ -126,8 +126,16 @@ struct Lanes {
     uint32_t mask;    // 2^B - 1
     uint32_t loi;     // lo' + add
     uint32_t hii;     // hi' + add (B < 32)
+    uint32_t negloi;  // -(lo' + add)
     uint32_t wm1;     // hi' - lo' - 1
 };
+
+__device__ __forceinline__ uint32_t imad(uint32_t a, uint32_t b, uint32_t c)
+{
+    uint32_t d;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
 
 __device__ __forceinline__ uint32_t opaque_one()
 {
@@ -146,6 +154,7 @@ __device__ __forceinline__ Lanes make_lanes(uint32_t lo, uint32_t wm1)
     L.mask = B < 32 ? ((1u << (B & 31)) - 1u) : 0xffffffffu;
     L.loi = lo + L.add;
     L.hii = lo + wm1 + 1u + L.add;  // only used for B < 32, where it cannot wrap
+    L.negloi = 0u - L.loi;
     L.wm1 = wm1;
     return L;
 }
@@ -248,12 +257,15 @@ __device__ __forceinline__ void agg_block(const typename Geo<B>::Vec* rows, cons
         for (int k = 0; k < kLpt; ++k) {
             const uint32_t ui = field_add<B>(W, r, k, L);
             if constexpr (BRANCHY) {
-                const bool m = (ui - L.loi) <= L.wm1;
+                // subtract and add on the FMA pipe unless the extraction already used it
+                const bool top = top_field<B>(r);
+                const uint32_t t = top ? ui - L.loi : imad(ui, L.one, L.negloi);
+                const bool m = t <= L.wm1;
                 if (__ballot_sync(kFull, m) != 0u) {
                     if (m) {
                         if constexpr (kMode != 0) c += 1u;
                         if constexpr (kMode == 2) s64 += ui;
-                        else a[k] += ui;
+                        else a[k] = top ? a[k] + ui : imad(ui, L.one, a[k]);
                     }
                 }
             } else if constexpr (kMode == 0) {
