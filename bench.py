@@ -546,80 +546,84 @@ def run_zone_sweep(args, dev, stream, gbscan):
     return out
 
 
-def run_plain(args, dev, stream, gbscan, beta_read):
-    """Plain single-column scan (N = 2^24, b = 8, sigma = 0.1): 16 MiB fits in L2, so it is
-    timed both after an L2 flush (HBM) and warm (the 'sub-LLC throughput > beta' control)."""
+def _graph_time(fn, stream, reps=20, trials=5):
+    """Device time per call of `fn` (launches on `stream`): a CUDA graph of `reps`
+    back-to-back calls, replayed `trials` times, median / reps.  Excludes host
+    launch latency, which single synchronised launches of small scans include."""
     import torch
 
-    n, b = 1 << 24, 8
-    with torch.cuda.stream(stream):
-        v = synth.uniform_values_device(synth.seed_for(1), n, b, device=dev)
-        col = gbscan.Column.from_device(v, n, b, stream=stream)
-        del v
-    lo, hi = synth.pick_range(synth.seed_for(1, 0, 1), b, 0.1)
-    res = torch.zeros(4, dtype=torch.int64, device=dev)
-    flush = torch.empty(1 << 28, dtype=torch.int32, device=dev)   # 1 GiB > 129 MB L2
-    nbytes = gbscan.scan_packed_words(n, b) * 4
-    cold, warm = [], []
-    for _ in range(7):
-        with torch.cuda.stream(stream):
-            flush.fill_(1)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        col.run_async(lo, hi, res, "branchfree", stream)
-        e1.record(stream)
-        e1.synchronize()
-        cold.append(e0.elapsed_time(e1))
-    for _ in range(7):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        col.run_async(lo, hi, res, "branchfree", stream)
-        e1.record(stream)
-        e1.synchronize()
-        warm.append(e0.elapsed_time(e1))
-    col.status(stream)
-    r = res.cpu().tolist()
-    col.close()
-    del flush
-    torch.cuda.empty_cache()
-    mc, mw = statistics.median(cold), statistics.median(warm)
-    # negative control (iii) of the paper: data resident in the last-level cache is
-    # read faster than beta.  At b = 8 the kernel is decode-bound, so the control
-    # uses b = 32 (64 MiB, inside the 129 MB L2) where decode is cheap.
-    with torch.cuda.stream(stream):
-        v = synth.uniform_values_device(synth.seed_for(1, 1), n, 32, device=dev)
-        c32 = gbscan.Column.from_device(v, n, 32, stream=stream)
-        del v
-    flush = torch.empty(1 << 28, dtype=torch.int32, device=dev)
-    lo32, hi32 = synth.pick_range(synth.seed_for(1, 1, 1), 32, 0.1)
-    cold32, warm32 = [], []
-    for reps, sink in ((7, cold32), (7, warm32)):
+    fn()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
         for _ in range(reps):
-            if sink is cold32:
-                with torch.cuda.stream(stream):
-                    flush.fill_(1)
+            fn()
+    ts = []
+    with torch.cuda.stream(stream):
+        g.replay()
+        torch.cuda.synchronize()
+        for _ in range(trials):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            c32.run_async(lo32, hi32, res, "branchfree", stream)
+            g.replay()
             e1.record(stream)
             e1.synchronize()
-            sink.append(e0.elapsed_time(e1))
-    c32.status(stream)
-    c32.close()
+            ts.append(e0.elapsed_time(e1) / reps)
+    del g
+    return statistics.median(ts)
+
+
+def run_plain(args, dev, stream, gbscan, beta_read):
+    """Plain single-column scan (N = 2^24, b = 8, sigma = 0.1), and the paper's
+    negative control (iii): data resident in the last-level cache is scanned
+    faster than beta.  Each is timed as a CUDA graph of 20 launches, after an L2
+    flush per launch (a 1 GiB write; its own time subtracted) or warm."""
+    import torch
+
+    flush = torch.empty(1 << 28, dtype=torch.int32, device=dev)   # 1 GiB > 129 MB L2
+    res = torch.zeros(4, dtype=torch.int64, device=dev)
+
+    def do_flush():
+        flush.fill_(1)
+
+    ms_flush = _graph_time(do_flush, stream)
+
+    def measure(n, b, seed, sigma):
+        with torch.cuda.stream(stream):
+            v = synth.uniform_values_device(seed, n, b, device=dev)
+            col = gbscan.Column.from_device(v, n, b, stream=stream)
+            del v
+        lo, hi = synth.pick_range(synth.seed_for(1, b, 1), b, sigma)
+
+        def scan():
+            col.run_async(lo, hi, res, "branchfree", stream)
+
+        def flush_scan():
+            flush.fill_(1)
+            col.run_async(lo, hi, res, "branchfree", stream)
+
+        warm = _graph_time(scan, stream)
+        cold = max(_graph_time(flush_scan, stream) - ms_flush, 1e-6)
+        col.status(stream)
+        r = res.cpu().tolist()
+        col.close()
+        nbytes = gbscan.scan_packed_words(n, b) * 4
+        return r, cold, warm, nbytes
+
+    n = 1 << 24
+    r, mc, mw, nbytes = measure(n, 8, synth.seed_for(1), 0.1)
+    r32, c32, w32, nb32 = measure(n, 32, synth.seed_for(1, 1), 0.1)
     del flush
     torch.cuda.empty_cache()
-    b32 = n * 4
-    gc32 = b32 / (statistics.median(cold32) * 1e-3) / 1e9
-    gw32 = b32 / (statistics.median(warm32) * 1e-3) / 1e9
-    return {"workload": "plain scan: N=2^24 uniform in [0,2^8), b=8, sigma=0.1 (median of 7)",
-            "l2_control": {"case": "N=2^24 at b=32 (64 MiB, L2-resident when warm)",
-                           "gbs_l2_flushed": round(gc32, 1), "gbs_l2_warm": round(gw32, 1),
-                           "beta_read_gbs": round(beta_read, 1), "warm_above_beta_read": bool(gw32 > beta_read)},
+    gw32 = nb32 / (w32 * 1e-3) / 1e9
+    return {"workload": "plain scan: N=2^24 uniform in [0,2^8), b=8, sigma=0.1; CUDA graph of 20 launches",
             "count": r[0], "sum": r[1], "realised_sigma": round(r[0] / n, 6),
             "ms_l2_flushed": round(mc, 5), "gbs_l2_flushed": round(nbytes / (mc * 1e-3) / 1e9, 1),
             "ms_l2_warm": round(mw, 5), "gbs_l2_warm": round(nbytes / (mw * 1e-3) / 1e9, 1),
             "gvals_per_s_warm": round(n / (mw * 1e-3) / 1e9, 1),
-            "warm_above_beta_read": bool(nbytes / (mw * 1e-3) / 1e9 > beta_read)}
+            "l2_control": {"case": "N=2^24 at b=32 (64 MiB, L2-resident when warm)",
+                           "gbs_l2_flushed": round(nb32 / (c32 * 1e-3) / 1e9, 1), "gbs_l2_warm": round(gw32, 1),
+                           "beta_read_gbs": round(beta_read, 1), "warm_above_beta_read": bool(gw32 > beta_read)}}
 
 
 BATCH_WORKLOAD = ("batched: 4096 columns, lengths log-uniform in [2^10, 2^26] scaled to 2^31 values in "
