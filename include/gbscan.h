@@ -168,17 +168,18 @@ scan_status scan_column_status(scan_column *col, void *stream);
 
 typedef struct scan_batch scan_batch; /* opaque: a planned batch of column scans */
 
-/* Plan a batch over `ncols` columns (spec batched form, configuration
- * "4096 columns in one persistent CUDA-graph launch"): every column's blocks
- * are cut into tiles of at most 8 KB and numbered consecutively; one
- * persistent kernel per predicate flavour (branch-free, branchy) serves all
- * tiles, warps popping `tiles_per_pop` consecutive tiles per atomic (0 = about
- * eight pops per warp).  strategies[i] picks column i's kernel and whether it
- * skips blocks by zone map (NULL = SCAN_BRANCHFREE for all; SCAN_AUTO counts
- * as branch-free).  Zone-skip columns need a built zone map.  The columns must
- * outlive the plan.  The first scan_batch_exec records a CUDA graph (copy
- * descriptors, reset results, kernels, copy results back) that later calls
- * replay. */
+/* Plan a batch over `ncols` columns (the paper has no batched form; this
+ * runs thousands of column scans as one CUDA-graph launch).  Every column's
+ * blocks are cut into tiles of at most 8 KB; columns are grouped by
+ * (predicate flavour, width) and each group is served by one width-specialised
+ * persistent kernel, the groups recorded as parallel branches of one graph with
+ * grids sized to their work.  Warps pop `tiles_per_pop` consecutive tiles per
+ * atomic (0 = chosen per group: at least 4, about four pops per warp).
+ * strategies[i] picks column i's flavour and whether it skips blocks by zone
+ * map (NULL = SCAN_BRANCHFREE for all; SCAN_AUTO counts as branch-free).
+ * Zone-skip columns need a built zone map.  The columns must outlive the plan.
+ * The first scan_batch_exec records the CUDA graph (copy descriptors, reset
+ * results, kernels, copy results back) that later calls replay. */
 scan_status scan_batch_create(scan_column *const *cols, uint32_t ncols,
                               const scan_strategy *strategies, uint32_t tiles_per_pop,
                               void *stream, scan_batch **out);
@@ -224,7 +225,8 @@ scan_status scan_batch_run(const scan_column *const *cols, const scan_pred *pred
 
 /* ------------------------------------------------------ learned planner */
 
-/* The planner (north-star "learned planner"; the paper has none): an FP32
+/* The learned planner (the paper has none; it picks among the paper's
+ * strategies, which all return the same result): an FP32
  * network 4 -> 64 -> 64 -> n_strategies with ReLU hidden layers that predicts
  * the log time of each strategy from the four features above; the strategy
  * with the smallest prediction is chosen.  Every strategy returns identical
@@ -262,7 +264,7 @@ scan_status scan_planner_load(scan_planner *planner, const char *path);
 
 /* -------------------------------------------------------------- serving */
 
-/* A scan server (spec serving loop; the paper has none): continuous
+/* A scan server (the paper has none): continuous
  * batching of COUNT/SUM queries against a device-resident table of columns.
  * A query names n table columns (ids into `cols`), each with its own
  * predicate.  Admission is by device memory: each of `slots` in-flight

@@ -1,17 +1,19 @@
-// Batched scan: thousands of columns of any width in one persistent launch.
+// Batched scan: thousands of columns in one CUDA-graph launch.
 //
-// The host lays every column's 1024-value blocks out as tiles (the same
-// per-width tile size as the single-column scan, at most 8 KB) and numbers the
-// tiles of all columns consecutively.  Persistent warps pop chunks of
-// consecutive tile numbers from one atomic counter, so a warp usually stays on
-// one column for many tiles; each tile is fetched into the warp's slot ring by
-// bulk TMA copies and decoded by the width-specialised code of the
-// single-column scan, picked by a switch on the column's width.  Columns marked
-// for zone skipping test their blocks' (min, max) before the copy and fetch
-// only the surviving runs.  A warp keeps running (count, sum) totals while the
-// column does not change and adds them to the column's result with three
-// atomics when it does.  The frame of reference is applied per flush
-// (SUM_v = SUM_u + base*COUNT is linear).
+// The host cuts every column's 1024-value blocks into tiles (the same
+// per-width tile size as the single-column scan, at most 8 KB), groups the
+// columns by width and numbers each group's tiles consecutively.  One
+// persistent kernel serves a group: warps pop chunks of consecutive tile
+// numbers from the group's atomic counter (a host-built table gives each
+// chunk's first column), so a warp usually stays on one column for many
+// tiles; each tile is fetched into the warp's slot ring by bulk TMA copies and
+// decoded by the width-specialised code of the single-column scan, compiled
+// for that group's width only (BFIX), which keeps the instruction cache warm.
+// Columns marked for zone skipping test their blocks' (min, max) before the
+// copy and fetch only the surviving runs.  A warp keeps running (count, sum)
+// totals while the column does not change and adds them to the column's
+// result with three atomics when it does.  The frame of reference is applied
+// per flush (SUM_v = SUM_u + base*COUNT is linear).
 #pragma once
 #include "scan_kernels.cuh"
 
