@@ -196,6 +196,35 @@ __device__ __forceinline__ uint32_t field_add(const typename Geo<B>::Vec (&W)[B]
     }
 }
 
+// For a field in the middle of its word or straddling two words the
+// extraction already costs two ALU operations; every other such value moves
+// its subtraction to the FMA pipe (one compare left on the ALU) so both pipes
+// stay busy: about 3.5 ALU and 1.5 IMAD per value.
+template <int B>
+__device__ __forceinline__ bool sub_on_fma(int r, int k)
+{
+    const int s = (r * B) & 31;
+    return B < 32 && s != 0 && !top_field<B>(r) && ((r + k) & 1) != 0;
+}
+
+__device__ __forceinline__ void acc0_fma(uint32_t& a, uint32_t ui, const Lanes& L)
+{
+    asm("{\n\t.reg .pred p;\n\t.reg .b32 t;\n\t"
+        "mad.lo.u32 t, %1, %4, %2;\n\t"
+        "setp.le.u32 p, t, %3;\n\t"
+        "@p mad.lo.u32 %0, %1, %4, %0;\n\t}"
+        : "+r"(a) : "r"(ui), "r"(L.negloi), "r"(L.wm1), "r"(L.one));
+}
+__device__ __forceinline__ void acc1_fma(uint32_t& c, uint32_t& a, uint32_t ui, const Lanes& L)
+{
+    asm("{\n\t.reg .pred p;\n\t.reg .b32 t;\n\t"
+        "mad.lo.u32 t, %2, %5, %3;\n\t"
+        "setp.le.u32 p, t, %4;\n\t"
+        "@p add.u32 %0, %0, 1;\n\t"
+        "@p mad.lo.u32 %1, %2, %5, %1;\n\t}"
+        : "+r"(c), "+r"(a) : "r"(ui), "r"(L.negloi), "r"(L.wm1), "r"(L.one));
+}
+
 // packed accumulator: a += v + add when lo <= v < hi (compares on the ALU)
 __device__ __forceinline__ void acc0_imad(uint32_t& a, uint32_t ui, const Lanes& L)
 {
@@ -270,9 +299,11 @@ __device__ __forceinline__ void agg_block(const typename Geo<B>::Vec* rows, cons
                 }
             } else if constexpr (kMode == 0) {
                 if (top_field<B>(r)) acc0_alu(a[k], ui, L);
+                else if (sub_on_fma<B>(r, k)) acc0_fma(a[k], ui, L);
                 else acc0_imad(a[k], ui, L);
             } else if constexpr (kMode == 1) {
                 if (top_field<B>(r)) acc1_alu(c, a[k], ui, L);
+                else if (sub_on_fma<B>(r, k)) acc1_fma(c, a[k], ui, L);
                 else acc1_imad(c, a[k], ui, L);
             } else {
                 // 64-bit sums: plain compare and add
