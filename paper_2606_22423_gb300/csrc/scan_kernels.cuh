@@ -290,7 +290,7 @@ __device__ __forceinline__ void agg_block(const typename Geo<B>::Vec* rows, cons
                 const bool top = top_field<B>(r);
                 const uint32_t t = top ? ui - L.loi : imad(ui, L.one, L.negloi);
                 const bool m = t <= L.wm1;
-                if (__ballot_sync(kFull, m) != 0u) {
+                if (__any_sync(kFull, m)) {  // vote.any: the predicate directly, no compare
                     if (m) {
                         if constexpr (kMode != 0) c += 1u;
                         if constexpr (kMode == 2) s64 += ui;
