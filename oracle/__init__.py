@@ -73,6 +73,11 @@ def _load():
             lib.oracle_scan_zoneskip.argtypes = [
                 _u32p, _u32p, _u32p, _u64, _u32, _u32, _i64, _i64,
                 ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_u64)]
+            lib.oracle_select_values.restype = _u64
+            lib.oracle_select_values.argtypes = [_u32p, _u64, _i64, _i64, _u32p, _u64]
+            lib.oracle_select_packed.restype = ctypes.c_int
+            lib.oracle_select_packed.argtypes = [
+                _u32p, _u64, _u32, _u32, _i64, _i64, _u32p, _u64, ctypes.POINTER(_u64)]
             lib.oracle_scan_packed_threads.restype = ctypes.c_int
             lib.oracle_scan_packed_threads.argtypes = [
                 _u32p, _u64, _u32, _u32, _i64, _i64, ctypes.c_int,
@@ -171,3 +176,25 @@ def scan_zoneskip(words, zmin, zmax, n: int, b: int, base: int, lo: int, hi: int
     if rc != OK:
         raise ValueError("oracle_scan_zoneskip rejected the input")
     return c.value, s.value, t.value
+
+
+def select_values(values, lo: int, hi: int, capacity: int | None = None):
+    """Positions (uint32, increasing) of raw values in [lo, hi), and the full count."""
+    v = _u32arr(values)
+    cap = v.size if capacity is None else capacity
+    out = np.zeros(max(cap, 1), np.uint32)
+    k = int(_load().oracle_select_values(v if v.size else np.zeros(1, np.uint32), v.size, lo, hi, out, cap))
+    return out[:min(k, cap)], k
+
+
+def select_packed(words, n: int, b: int, base: int, lo: int, hi: int, capacity: int | None = None):
+    """Materializing select over a packed column: (positions, full count)."""
+    w = _u32arr(words)
+    cap = n if capacity is None else capacity
+    out = np.zeros(max(cap, 1), np.uint32)
+    k = _u64()
+    rc = _load().oracle_select_packed(w if w.size else np.zeros(1, np.uint32), n, b, base, lo, hi, out, cap,
+                                      ctypes.byref(k))
+    if rc != OK:
+        raise ValueError("oracle_select_packed rejected the input")
+    return out[:min(k.value, cap)], int(k.value)

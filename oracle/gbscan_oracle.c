@@ -205,6 +205,44 @@ int oracle_scan_zoneskip(const uint32_t *words, const uint32_t *zmin, const uint
 }
 
 /*
+ * Materializing select (paper §3 lists "a materializing select" beside the
+ * counts; §4 "Branch" measures it): the positions i of the values with
+ * lo <= v_i < hi, in increasing order.  The first min(count, capacity)
+ * positions go to `pos` (which may be NULL when capacity is 0); the return
+ * value is the full count, so a caller can size a second attempt.
+ */
+uint64_t oracle_select_values(const uint32_t *values, uint64_t n, int64_t lo, int64_t hi,
+                              uint32_t *pos, uint64_t capacity)
+{
+    uint64_t i, k = 0;
+    for (i = 0; i < n; ++i) {
+        int64_t v = (int64_t)values[i];
+        if (lo <= v && v < hi) {
+            if (k < capacity) pos[k] = (uint32_t)i;
+            k += 1;
+        }
+    }
+    return k;
+}
+
+/* The same select over a packed column: decode each value, then test it. */
+int oracle_select_packed(const uint32_t *words, uint64_t n, uint32_t b, uint32_t base, int64_t lo,
+                         int64_t hi, uint32_t *pos, uint64_t capacity, uint64_t *count)
+{
+    uint64_t i, k = 0;
+    if (!width_ok(b, base)) return ORACLE_EINVAL;
+    for (i = 0; i < n; ++i) {
+        int64_t v = (int64_t)code_at(words, i, b) + (int64_t)base;
+        if (lo <= v && v < hi) {
+            if (k < capacity) pos[k] = (uint32_t)i;
+            k += 1;
+        }
+    }
+    *count = k;
+    return ORACLE_OK;
+}
+
+/*
  * The same fused scan split over `threads` disjoint block ranges, one POSIX
  * thread each, with the per-thread (count, sum) added at the end.  Integer
  * addition is associative, so the result equals oracle_scan_packed exactly.

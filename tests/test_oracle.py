@@ -9,7 +9,8 @@ Each test names what fixes the expected value:
   * closed forms (a permutation of 0..N-1 sums to N(N-1)/2);
   * invariants (range additivity, frame-of-reference shift, zone-skip
     exactness, multiset invariance under displacement);
-  * the probability of a zone-map skip on i.i.d. uniform data.
+  * the probability of a zone-map skip on i.i.d. uniform data;
+  * np.flatnonzero over the raw values for the materializing select.
 A plausible mistake in the oracle (swapped lane/row, MSB-first streams, a
 dropped carry word, an inclusive upper bound, base not added back, a tail
 block counted) fails at least one of them.
@@ -265,3 +266,59 @@ def test_pick_range_hits_target_selectivity():
             lo, hi = synth.pick_range(1, b, sigma)
             assert 0 <= lo < hi <= (1 << b)
             assert hi - lo == max(1, round(sigma * (1 << b)))
+
+
+# ------------------------------------------------------- materializing select
+@pytest.mark.parametrize("b", [1, 5, 8, 13, 24, 32])
+def test_select_matches_flatnonzero(b):
+    """Paper §3 "a materializing select": positions of the matches, in order,
+    fixed by numpy's flatnonzero over the generator's raw values."""
+    base = 0 if b == 32 else 17
+    for n in (1, 1023, 1024, 5 * 1024 + 77):
+        v = synth.uniform_values(synth.seed_for(31, b, n), n, b, base)
+        w = oracle.pack(v, b, base)
+        for sigma in (1e-3, 0.1, 0.5, 1.0):
+            lo, hi = synth.pick_range(synth.seed_for(32, b, n), b, sigma, base)
+            want = np.flatnonzero((v.astype(np.int64) >= lo) & (v.astype(np.int64) < hi))
+            got, k = oracle.select_packed(w, n, b, base, lo, hi)
+            assert k == want.size
+            np.testing.assert_array_equal(got, want.astype(np.uint32))
+            raw, k2 = oracle.select_values(v, lo, hi)
+            assert k2 == k
+            np.testing.assert_array_equal(raw, got)
+
+
+def test_select_agrees_with_count_and_sum():
+    """The selected positions carry exactly COUNT values whose sum is SUM."""
+    b, n, base = 11, 20_000, 5
+    v = synth.uniform_values(41, n, b, base)
+    w = oracle.pack(v, b, base)
+    for lo, hi in [(base, base + 100), (base + 700, base + 1500), (0, 1 << 40)]:
+        pos, k = oracle.select_packed(w, n, b, base, lo, hi)
+        c, sm = hist_count_sum(v, lo, hi)
+        assert k == c
+        assert int(v[pos].astype(np.int64).sum()) == sm
+        assert np.all(np.diff(pos.astype(np.int64)) > 0)
+
+
+def test_select_capacity_truncates_but_counts_everything():
+    b, n = 6, 3000
+    v = synth.uniform_values(42, n, b)
+    w = oracle.pack(v, b)
+    full, k = oracle.select_packed(w, n, b, 0, 10, 40)
+    for cap in (0, 1, 7, k - 1, k, k + 5):
+        got, kk = oracle.select_packed(w, n, b, 0, 10, 40, capacity=cap)
+        assert kk == k
+        np.testing.assert_array_equal(got, full[:min(cap, k)])
+
+
+def test_select_empty_and_degenerate():
+    v = synth.uniform_values(43, 4096, 9)
+    w = oracle.pack(v, 9)
+    assert oracle.select_packed(w, 4096, 9, 0, 50, 50)[1] == 0      # empty range
+    assert oracle.select_packed(w, 4096, 9, 0, 60, 50)[1] == 0      # inverted range
+    assert oracle.select_packed(w, 0, 9, 0, 0, 512)[1] == 0         # no values
+    pos, k = oracle.select_packed(w, 4096, 9, 0, 0, 512)            # full domain
+    assert k == 4096
+    np.testing.assert_array_equal(pos, np.arange(4096, dtype=np.uint32))
+

@@ -14,10 +14,22 @@ from tests.test_oracle import hist_count_sum, layout_by_bits
 SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "oracle", "gbscan_oracle.c")
 
 MUTANTS = {
-    "inclusive upper bound": [("(int64_t)base;\n        if (lo <= v && v < hi) {",
-                               "(int64_t)base;\n        if (lo <= v && v <= hi) {")],
-    "base not added back": [("int64_t v = (int64_t)code_at(words, i, b) + (int64_t)base;",
-                             "int64_t v = (int64_t)code_at(words, i, b);")],
+    "inclusive upper bound": [("(int64_t)base;\n        if (lo <= v && v < hi) {\n            c += 1;",
+                               "(int64_t)base;\n        if (lo <= v && v <= hi) {\n            c += 1;")],
+    "base not added back": [("int64_t v = (int64_t)code_at(words, i, b) + (int64_t)base;\n        if (lo <= v && v < hi) {\n"
+                             "            c += 1;",
+                             "int64_t v = (int64_t)code_at(words, i, b);\n        if (lo <= v && v < hi) {\n"
+                             "            c += 1;")],
+    "select inclusive upper bound": [("(int64_t)base;\n        if (lo <= v && v < hi) {\n            if (k < capacity)",
+                                      "(int64_t)base;\n        if (lo <= v && v <= hi) {\n            if (k < capacity)")],
+    "select position off by one": [("if (k < capacity) pos[k] = (uint32_t)i;\n            k += 1;\n        }\n    }\n"
+                                    "    *count = k;",
+                                    "if (k < capacity) pos[k] = (uint32_t)(i + 1);\n            k += 1;\n        }\n    }\n"
+                                    "    *count = k;")],
+    "select count stops at capacity": [("if (k < capacity) pos[k] = (uint32_t)i;\n            k += 1;\n        }\n    }\n"
+                                        "    *count = k;",
+                                        "if (k < capacity) { pos[k] = (uint32_t)i; k += 1; }\n        }\n    }\n"
+                                        "    *count = k;")],
     "zone skip off by one": [("if ((int64_t)zmax[k] < lo || (int64_t)zmin[k] >= hi) continue;",
                               "if ((int64_t)zmax[k] <= lo || (int64_t)zmin[k] >= hi) continue;")],
     "tail padding in zone map": [("        uint64_t last = first + BLOCK_VALUES < n ? first + BLOCK_VALUES : n;\n"
@@ -51,6 +63,7 @@ class Lib:
         self.l.oracle_zonemap.argtypes = [u32p, u64, u32, u32, u32p, u32p]
         self.l.oracle_scan_zoneskip.argtypes = [u32p, u32p, u32p, u64, u32, u32, i64, i64, ctypes.POINTER(i64),
                                                 ctypes.POINTER(i64), ctypes.POINTER(u64)]
+        self.l.oracle_select_packed.argtypes = [u32p, u64, u32, u32, i64, i64, u32p, u64, ctypes.POINTER(u64)]
 
     def pack(self, v, b, base=0):
         out = np.zeros(((v.size + 1023) // 1024) * 32 * b, np.uint32)
@@ -73,6 +86,11 @@ class Lib:
         self.l.oracle_zonemap(w, n, b, base, mn, mx)
         return mn, mx
 
+    def select(self, w, n, b, base, lo, hi, cap):
+        out, k = np.zeros(max(cap, 1), np.uint32), ctypes.c_uint64()
+        self.l.oracle_select_packed(w, n, b, base, lo, hi, out, cap, ctypes.byref(k))
+        return out[:min(cap, k.value)], k.value
+
     def zoneskip(self, w, mn, mx, n, b, base, lo, hi):
         c, s, t = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_uint64()
         self.l.oracle_scan_zoneskip(w, mn, mx, n, b, base, lo, hi, ctypes.byref(c), ctypes.byref(s), ctypes.byref(t))
@@ -81,7 +99,7 @@ class Lib:
 
 def pins(o):
     """A compact copy of the independent pins (layout bits, round trip, brute force,
-    frame of reference, zone maps, zone-skip exactness and skip rule)."""
+    frame of reference, zone maps, zone-skip exactness and skip rule, select positions)."""
     for b in (3, 8, 13, 32):
         for n in (1025, 4096 + 7):
             v = synth.uniform_values(synth.seed_for(77, b, n), n, b)
@@ -111,6 +129,18 @@ def pins(o):
         m = (v >= lo) & (v < hi)
         assert (c, s) == (int(m.sum()), int(v[m].astype(np.int64).sum()))
         assert t == int(np.sum(~((mx < lo) | (mn >= hi))))
+    # materializing select: positions fixed by flatnonzero; capacity keeps the full count
+    n, b, base = 3000, 7, 40
+    v = synth.uniform_values(8, n, b, base)
+    w = o.pack(v, b, base)
+    for lo, hi in [(base + 3, base + 20), (base + 100, base + 128)]:
+        want = np.flatnonzero((v >= lo) & (v < hi)).astype(np.uint32)
+        got, k = o.select(w, n, b, base, lo, hi, n)
+        assert k == want.size
+        np.testing.assert_array_equal(got, want)
+        got, k = o.select(w, n, b, base, lo, hi, 5)
+        assert k == want.size
+        np.testing.assert_array_equal(got, want[:5])
 
 
 def _compile(tmpdir, name, text):
