@@ -468,6 +468,7 @@ def run_ours(args, world, rank, local):
         c.close()
     torch.cuda.empty_cache()
     plain = None if args.no_extra else run_plain(args, dev, stream, gbscan, beta_read)
+    select = None if args.no_extra else run_select(args, dev, stream, gbscan, peaks().get("hbm_gbs", 6800.0))
     zone = None if args.no_extra else run_zone_sweep(args, dev, stream, gbscan)
     tdec = [law["branchfree"]["t_dec_gvals"], law["branchy"]["t_dec_gvals"],
             law["branchfree"]["t_dec_gvals"], law["branchy"]["t_dec_gvals"]]
@@ -490,6 +491,7 @@ def run_ours(args, world, rank, local):
         "branch_crossover": branch,
         "plain_scan": plain,
         "zone_sweep": zone,
+        "select": select,
         "batched": batched,
         "serving": serving,
         "realised_sigma": realised,
@@ -571,6 +573,94 @@ def _graph_time(fn, stream, reps=20, trials=5):
             ts.append(e0.elapsed_time(e1) / reps)
     del g
     return statistics.median(ts)
+
+
+SELECT_SIGMAS = [1e-4, 1e-3, 1e-2, 0.05, 0.1, 0.3, 0.5, 0.7, 0.9, 0.99, 1.0]
+
+
+def run_select(args, dev, stream, gbscan, hbm_gbs):
+    """Materializing select (paper §3 lists it beside the counts; §4 "Branch" compares
+    its branchy and predicated forms): N = 2^28 uniform values at b = 32 (the plain
+    array, a decode-free select) and b = 16; every matching position written in order;
+    branch-free vs branchy over a selectivity sweep, the counting scan timed beside it.
+    Bytes per launch = packed column + 4 bytes per position written."""
+    import torch
+
+    from paper_2606_22423_gb300 import lawfit
+
+    n = 1 << 28
+    out = {"workload": "materializing select: N=2^28 uniform values at b=32 (plain array) and b=16; "
+                       f"sigma in {SELECT_SIGMAS}; positions (uint32) written in index order; "
+                       "branch-free vs branchy; the counting scan (branch-free) timed on the same predicate",
+           "bytes": "packed column + 4 B per position written", "rows": [], "by_b": {}}
+    pos = torch.empty(n, dtype=torch.int32, device=dev)
+    ref = torch.empty(n, dtype=torch.int32, device=dev)
+    cnt = torch.zeros(2, dtype=torch.int64, device=dev)
+    res = torch.zeros(4, dtype=torch.int64, device=dev)
+    for b in (32, 16):
+        with torch.cuda.stream(stream):
+            v = synth.uniform_values_device(synth.seed_for(9, b), n, b, device=dev)
+            col = gbscan.Column.from_device(v, n, b, stream=stream)
+            del v
+        torch.cuda.synchronize()
+        rows = []
+        for si, sigma in enumerate(SELECT_SIGMAS):
+            lo, hi = synth.pick_range(synth.seed_for(9, b, si + 1), b, sigma)
+            ts = {}
+            for k, strat in enumerate(["branchfree", "branchy", "count"]):
+                def launch():
+                    if strat == "count":
+                        col.run_async(lo, hi, res, "branchfree", stream)
+                    else:
+                        col.select_async(lo, hi, pos, cnt[k:k + 1], strat, stream=stream)
+                launch()
+                vals = []
+                for _ in range(3):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    launch()
+                    e1.record(stream)
+                    e1.synchronize()
+                    vals.append(e0.elapsed_time(e1))
+                ts[strat] = statistics.median(vals)
+                if strat == "branchfree":
+                    col.status(stream)
+                    kk = int(cnt[0].item())
+                    ref[:kk].copy_(pos[:kk])
+            col.status(stream)
+            c = cnt.cpu().tolist()
+            k = c[0]
+            exact = c[0] == c[1] == int(res[0].item()) and bool(torch.equal(pos[:k], ref[:k]))
+            nbytes = gbscan.scan_packed_words(n, b) * 4 + 4 * k
+            rows.append({"b": b, "sigma": sigma, "realised_sigma": round(k / n, 6),
+                         "us_branchfree": round(ts["branchfree"] * 1e3, 1), "us_branchy": round(ts["branchy"] * 1e3, 1),
+                         "us_count": round(ts["count"] * 1e3, 1),
+                         "gbs_branchfree": round(nbytes / (ts["branchfree"] * 1e-3) / 1e9, 1),
+                         "gbs_branchy": round(nbytes / (ts["branchy"] * 1e-3) / 1e9, 1),
+                         "frac_branchfree": round(nbytes / (ts["branchfree"] * 1e-3) / 1e9 / hbm_gbs, 4),
+                         "exact": exact})
+        col.close()
+        torch.cuda.empty_cache()
+        s_ = np.array([r["realised_sigma"] for r in rows])
+        tb = np.array([r["us_branchy"] for r in rows])
+        tf = np.array([r["us_branchfree"] for r in rows])
+        d = tb - tf
+        a1, b1 = lawfit.fit_affine(s_ * (1 - s_), d)
+        a2, b2 = lawfit.fit_affine(s_, d)
+        err = lambda a, bb, x: float(np.median(np.abs(a + bb * x - d)))  # noqa: E731
+        out["by_b"][str(b)] = {
+            "branchfree_wins_at_sigma": [r["sigma"] for r in rows if r["us_branchfree"] < r["us_branchy"]],
+            "excess_branchy_us_fit_parabola": {"A": round(a1, 2), "B": round(b1, 2),
+                                               "median_abs_err_us": round(err(a1, b1, s_ * (1 - s_)), 2)},
+            "excess_branchy_us_fit_linear": {"A": round(a2, 2), "B": round(b2, 2),
+                                             "median_abs_err_us": round(err(a2, b2, s_), 2)},
+            "best_frac_branchfree": max(r["frac_branchfree"] for r in rows),
+        }
+        out["rows"].extend(rows)
+    del pos, ref
+    torch.cuda.empty_cache()
+    out["exact"] = all(r["exact"] for r in out["rows"])
+    return out
 
 
 def run_plain(args, dev, stream, gbscan, beta_read):

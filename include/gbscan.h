@@ -164,6 +164,29 @@ scan_status scan_run_async(scan_column *col, scan_pred pred, scan_strategy strat
  * column's kernels: SCAN_OK or SCAN_ETIMEOUT. */
 scan_status scan_column_status(scan_column *col, void *stream);
 
+/* ------------------------------------------------- materializing select */
+
+/* Materializing select (paper §3: "a materializing select" beside the count
+ * aggregates; §4 "Branch": the branchy and predicated forms of that select).
+ * Writes the positions i, in increasing order, of the values with
+ * pred.lo <= v_i < pred.hi as uint32 to dev_positions (device memory, at
+ * least `capacity` of them; may be NULL when capacity is 0) and the full
+ * number of matches to *host_count.  Only the first min(count, capacity)
+ * positions are written, so a count above capacity tells the caller how much
+ * to allocate for a second call.  strategy: SCAN_BRANCHFREE (every 32-value
+ * row runs the predicated store) or SCAN_BRANCHY (a warp vote per row skips
+ * rows without a match); SCAN_AUTO means branch-free; the zone-skip
+ * strategies are SCAN_EINVAL.  Both give the same positions.  One read of
+ * the packed column; calls on one column must be ordered on one stream.
+ * Waits for the stream; SCAN_ETIMEOUT if a bounded device wait gave up. */
+scan_status scan_select(scan_column *col, scan_pred pred, scan_strategy strategy, uint32_t *dev_positions,
+                        uint64_t capacity, void *stream, uint64_t *host_count);
+
+/* As scan_select, but the count goes to device memory (8 bytes) and the call
+ * returns without waiting; check scan_column_status afterwards. */
+scan_status scan_select_async(scan_column *col, scan_pred pred, scan_strategy strategy,
+                              uint32_t *dev_positions, uint64_t capacity, void *stream, uint64_t *dev_count);
+
 /* -------------------------------------------------------------- batches */
 
 typedef struct scan_batch scan_batch; /* opaque: a planned batch of column scans */

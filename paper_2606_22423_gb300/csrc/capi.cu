@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "../../include/gbscan.h"
+#include "internal.h"
 #include "scan_kernels.cuh"
 
 namespace {
@@ -147,6 +148,9 @@ struct scan_column {
     void* ws_raw = nullptr;
     Workspace ws{};
     scan_result* host_result = nullptr;  // pinned staging, 48 bytes (result + status)
+    unsigned long long* sel_agg = nullptr;  // materializing select: tagged CTA totals
+    uint64_t sel_words = 0;
+    uint32_t sel_epoch = 0;
 };
 
 // Read-only view of a column for the batch planner (not part of the C ABI).
@@ -160,6 +164,31 @@ bool gb_column_view(const scan_column* c, const uint32_t** packed, uint64_t* n, 
     *base = c->base;
     *zonemap = c->zonemap_valid ? c->zonemap : nullptr;
     return true;
+}
+
+cudaError_t gb_column_select_ws(scan_column* c, uint64_t words, cudaStream_t st, GbSelectWs* out)
+{
+    cudaError_t e = cudaSuccess;
+    if (words > c->sel_words) {
+        if (c->sel_agg) cudaFree(c->sel_agg);
+        c->sel_agg = nullptr;
+        c->sel_words = 0;
+        if ((e = cudaMalloc(&c->sel_agg, words * sizeof(unsigned long long))) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(c->sel_agg, 0, words * sizeof(unsigned long long), st)) != cudaSuccess) return e;
+        c->sel_words = words;
+        c->sel_epoch = 0;
+    }
+    if (++c->sel_epoch == 0) {  // the tag wrapped: words from 2^32 launches ago would match again
+        if ((e = cudaMemsetAsync(c->sel_agg, 0, c->sel_words * sizeof(unsigned long long), st)) != cudaSuccess)
+            return e;
+        c->sel_epoch = 1;
+    }
+    out->agg = c->sel_agg;
+    out->epoch = c->sel_epoch;
+    out->status = c->ws.status;
+    out->result = c->ws.result;
+    out->host_result = c->host_result;
+    return cudaSuccess;
 }
 
 // ---------------------------------------------------------------- encoders
@@ -565,6 +594,7 @@ scan_status scan_column_destroy(scan_column* col)
     if (col->cand) cudaFree(col->cand);
     if (col->ws_raw) cudaFree(col->ws_raw);
     if (col->host_result) cudaFreeHost(col->host_result);
+    if (col->sel_agg) cudaFree(col->sel_agg);
     delete col;
     return SCAN_OK;
 }

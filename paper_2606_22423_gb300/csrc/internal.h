@@ -1,0 +1,28 @@
+// Host-side declarations shared between the library's translation units
+// (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../../include/gbscan.h"
+
+// Sets the message scan_last_error() returns on this thread.
+void gb_set_last_error(const char* msg);
+
+// Read-only view of a column.
+bool gb_column_view(const scan_column* c, const uint32_t** packed, uint64_t* n, uint32_t* b,
+                    uint32_t* base, const uint2** zonemap);
+
+// Workspace of the materializing select on one column.
+struct GbSelectWs {
+    unsigned long long* agg;   // tagged per-iteration CTA totals
+    uint32_t epoch;            // this launch's tag
+    unsigned int* status;      // the column's device status word
+    long long* result;         // the column's device result slot (4 words, status follows)
+    scan_result* host_result;  // pinned staging for result + status (36 bytes)
+};
+
+// Grows the column's select workspace to at least `words` tagged words and
+// hands out a fresh tag (clearing the words when the tag wraps).
+cudaError_t gb_column_select_ws(scan_column* c, uint64_t words, cudaStream_t st, GbSelectWs* out);

@@ -1,0 +1,194 @@
+// Host side of the materializing select: argument checks, predicate
+// translation to code space, the per-column workspace of tagged CTA totals,
+// and a cooperative launch of the width-specialised k_select kernel.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+
+#include "internal.h"
+#include "select_kernels.cuh"
+
+namespace {
+
+scan_status sfail(scan_status s, const char* msg)
+{
+    gb_set_last_error(msg);
+    return s;
+}
+
+scan_status scuda(cudaError_t e, const char* what)
+{
+    static thread_local char buf[256];
+    snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
+    gb_set_last_error(buf);
+    return e == cudaErrorMemoryAllocation ? SCAN_ENOMEM : SCAN_ECUDA;
+}
+
+#define SL_CUDA(call)                                  \
+    do {                                               \
+        cudaError_t e_ = (call);                       \
+        if (e_ != cudaSuccess) return scuda(e_, #call); \
+    } while (0)
+
+struct Device {
+    int id = -1, sms = 0, coop = 0;
+};
+
+Device device()
+{
+    Device d;
+    if (cudaGetDevice(&d.id) != cudaSuccess) return d;
+    cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, d.id);
+    cudaDeviceGetAttribute(&d.coop, cudaDevAttrCooperativeLaunch, d.id);
+    return d;
+}
+
+template <int B, bool BRANCHY>
+cudaError_t launch_one(const gb::SelectParams& p, int grid, cudaStream_t st)
+{
+    using S = gb::SelShape<B>;
+    auto kernel = gb::k_select<B, BRANCHY>;
+    static int configured_for = -1;  // device whose attribute is set
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (configured_for != dev) {
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kSmemBytes);
+        if (e != cudaSuccess) return e;
+        configured_for = dev;
+    }
+    gb::SelectParams q = p;
+    void* args[] = {&q};
+    return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(kernel), dim3(grid),
+                                       dim3(gb::kSelWarps * 32), args, S::kSmemBytes, st);
+}
+
+template <bool BRANCHY, int LO, int HI>
+cudaError_t launch_range(int b, const gb::SelectParams& p, int grid, cudaStream_t st)
+{
+    if constexpr (LO > HI) {
+        return cudaErrorInvalidValue;
+    } else {
+        if (b == LO) return launch_one<LO, BRANCHY>(p, grid, st);
+        return launch_range<BRANCHY, LO + 1, HI>(b, p, grid, st);
+    }
+}
+
+template <int LO, int HI>
+int tile_blocks_range(int b)
+{
+    if constexpr (LO > HI) {
+        return 1;
+    } else {
+        if (b == LO) return gb::SelShape<LO>::kTB;
+        return tile_blocks_range<LO + 1, HI>(b);
+    }
+}
+
+// Enqueue the select; *empty = true when no value can match (nothing launched).
+scan_status enqueue_select(scan_column* col, scan_pred pred, scan_strategy strategy, uint32_t* dev_positions,
+                           uint64_t capacity, cudaStream_t st, unsigned long long* dev_count, bool* empty,
+                           GbSelectWs* ws_out)
+{
+    *empty = false;
+    if (!col) return sfail(SCAN_EINVAL, "col is NULL");
+    if (capacity && !dev_positions) return sfail(SCAN_EINVAL, "dev_positions is NULL with capacity > 0");
+    bool branchy;
+    switch (strategy) {
+    case SCAN_AUTO:
+    case SCAN_BRANCHFREE: branchy = false; break;
+    case SCAN_BRANCHY: branchy = true; break;
+    default: return sfail(SCAN_EINVAL, "select takes SCAN_BRANCHFREE, SCAN_BRANCHY or SCAN_AUTO");
+    }
+    const uint32_t* packed = nullptr;
+    const uint2* zm = nullptr;
+    uint64_t n = 0;
+    uint32_t b = 0, base = 0;
+    gb_column_view(col, &packed, &n, &b, &base, &zm);
+    // [lo, hi) on decoded values -> code space, clipped to the column's domain
+    const int64_t lo_v = static_cast<int64_t>(base);
+    const int64_t hi_v = static_cast<int64_t>(base) + (1ll << b);
+    const int64_t lo = std::max(pred.lo, lo_v);
+    const int64_t hi = std::min(pred.hi, hi_v);
+    if (n == 0 || lo >= hi) {
+        *empty = true;
+        return SCAN_OK;
+    }
+    static const Device dev = device();
+    if (!dev.coop) return sfail(SCAN_ENOTSUP, "the device cannot launch cooperative kernels");
+    const int grid = std::min(dev.sms, 256);  // the kernel polls up to 256 CTA totals per iteration
+    const uint64_t nblocks = (n + 1023u) >> 10;
+    const uint64_t tb = static_cast<uint64_t>(tile_blocks_range<1, 32>(static_cast<int>(b)));
+    const uint64_t ntiles = (nblocks + tb - 1) / tb;
+    const uint64_t warps = static_cast<uint64_t>(grid) * gb::kSelWarps;
+    const uint64_t niter = (ntiles + warps - 1) / warps;
+    GbSelectWs ws{};
+    SL_CUDA(gb_column_select_ws(col, niter * static_cast<uint64_t>(grid), st, &ws));
+    gb::SelectParams p{};
+    p.packed = packed;
+    p.n = n;
+    p.lo = static_cast<uint32_t>(lo - lo_v);
+    p.wm1 = static_cast<uint32_t>(hi - lo - 1);
+    p.pos = dev_positions;
+    p.capacity = capacity;
+    p.agg = ws.agg;
+    p.epoch = ws.epoch;
+    p.niter = static_cast<uint32_t>(niter);
+    p.count = dev_count ? dev_count : reinterpret_cast<unsigned long long*>(ws.result);
+    p.status = ws.status;
+    const cudaError_t e = branchy ? launch_range<true, 1, 32>(static_cast<int>(b), p, grid, st)
+                                  : launch_range<false, 1, 32>(static_cast<int>(b), p, grid, st);
+    if (e != cudaSuccess) return scuda(e, "select kernel launch");
+    if (ws_out) *ws_out = ws;
+    return SCAN_OK;
+}
+
+cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
+
+}  // namespace
+
+extern "C" {
+
+scan_status scan_select_async(scan_column* col, scan_pred pred, scan_strategy strategy, uint32_t* dev_positions,
+                              uint64_t capacity, void* stream, uint64_t* dev_count)
+{
+    gb_set_last_error("");
+    if (!dev_count) return sfail(SCAN_EINVAL, "dev_count is NULL");
+    bool empty = false;
+    const scan_status s = enqueue_select(col, pred, strategy, dev_positions, capacity, as_stream(stream),
+                                         reinterpret_cast<unsigned long long*>(dev_count), &empty, nullptr);
+    if (s != SCAN_OK) return s;
+    if (empty) SL_CUDA(cudaMemsetAsync(dev_count, 0, sizeof(uint64_t), as_stream(stream)));
+    return SCAN_OK;
+}
+
+scan_status scan_select(scan_column* col, scan_pred pred, scan_strategy strategy, uint32_t* dev_positions,
+                        uint64_t capacity, void* stream, uint64_t* host_count)
+{
+    gb_set_last_error("");
+    if (!host_count) return sfail(SCAN_EINVAL, "host_count is NULL");
+    cudaStream_t st = as_stream(stream);
+    bool empty = false;
+    GbSelectWs ws{};
+    const scan_status s = enqueue_select(col, pred, strategy, dev_positions, capacity, st, nullptr, &empty, &ws);
+    if (s != SCAN_OK) return s;
+    if (empty) {
+        *host_count = 0;
+        return SCAN_OK;
+    }
+    // result slot (32 B) and status word (4 B) are adjacent: one small copy
+    SL_CUDA(cudaMemcpyAsync(ws.host_result, ws.result, 36, cudaMemcpyDeviceToHost, st));
+    SL_CUDA(cudaStreamSynchronize(st));
+    unsigned int dev_status = 0;
+    std::memcpy(&dev_status, reinterpret_cast<unsigned char*>(ws.host_result) + 32, 4);
+    if (dev_status) {
+        SL_CUDA(cudaMemset(ws.status, 0, sizeof(unsigned int)));
+        return sfail(SCAN_ETIMEOUT, "a device-side wait timed out in the select kernel");
+    }
+    *host_count = static_cast<uint64_t>(ws.host_result->count);
+    return SCAN_OK;
+}
+
+}  // extern "C"

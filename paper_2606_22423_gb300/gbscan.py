@@ -67,6 +67,8 @@ SIGNATURES = {
     "scan_run": (_st, [_vp, scan_pred, _st, _vp, ctypes.POINTER(scan_result)]),
     "scan_run_async": (_st, [_vp, scan_pred, _st, _vp, _vp]),
     "scan_column_status": (_st, [_vp, _vp]),
+    "scan_select": (_st, [_vp, scan_pred, _st, _vp, _u64, _vp, ctypes.POINTER(_u64)]),
+    "scan_select_async": (_st, [_vp, scan_pred, _st, _vp, _u64, _vp, _vp]),
     "scan_probe_read": (_st, [_vp, _u64, _vp, _vp]),
     "scan_launch_shape": (_st, [_u32] + [ctypes.POINTER(_u32)] * 5),
     "scan_selftest_wait_timeout": (_st, [_u64, _vp]),
@@ -248,6 +250,26 @@ class Column:
     def run_async(self, lo: int, hi: int, dev_out, strategy="branchfree", stream=None):
         st = STRATEGIES[strategy] if isinstance(strategy, str) else int(strategy)
         _check(load().scan_run_async(self._h, scan_pred(lo, hi), st, _stream(stream), _ptr(dev_out)))
+
+    def select(self, lo: int, hi: int, positions=None, strategy="branchfree", stream=None,
+               capacity=None) -> int:
+        """Materializing select: positions (uint32 bits in a device int32 tensor, in
+        increasing order) of the values in [lo, hi); returns the full match count.
+        Only the first min(count, capacity) positions are written."""
+        st = STRATEGIES[strategy] if isinstance(strategy, str) else int(strategy)
+        cap = (0 if positions is None else positions.numel()) if capacity is None else int(capacity)
+        count = _u64()
+        _check(load().scan_select(self._h, scan_pred(lo, hi), st, _ptr(positions), cap, _stream(stream),
+                                  ctypes.byref(count)))
+        return int(count.value)
+
+    def select_async(self, lo: int, hi: int, positions, dev_count, strategy="branchfree", stream=None,
+                     capacity=None):
+        """As select, with the count written to device memory (one int64)."""
+        st = STRATEGIES[strategy] if isinstance(strategy, str) else int(strategy)
+        cap = (0 if positions is None else positions.numel()) if capacity is None else int(capacity)
+        _check(load().scan_select_async(self._h, scan_pred(lo, hi), st, _ptr(positions), cap, _stream(stream),
+                                        _ptr(dev_count)))
 
     def status(self, stream=None):
         _check(load().scan_column_status(self._h, _stream(stream)))

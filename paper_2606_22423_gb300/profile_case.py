@@ -33,6 +33,8 @@ def main():
     ap.add_argument("--strategy", default="branchfree")
     ap.add_argument("--order", default="uniform", choices=["uniform", "sorted", "swapped"])
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--select", action="store_true",
+                    help="run the materializing select (positions) instead of the counting scan")
     ap.add_argument("--batch", type=int, default=0,
                     help="scan a batch of this many mixed columns (batched workload recipe, scaled)")
     a = ap.parse_args()
@@ -52,19 +54,24 @@ def main():
         col.zonemap_build(s)
     lo, hi = synth.pick_range(synth.seed_for(7, a.b, 1), a.b, a.sigma)
     out = torch.zeros(4, dtype=torch.int64, device="cuda")
+    pos = torch.empty(a.n if a.select else 1, dtype=torch.int32, device="cuda")
     torch.cuda.synchronize()
     ms = 0.0
     for _ in range(a.reps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(s)
-        col.run_async(lo, hi, out, a.strategy, s)
+        if a.select:
+            col.select_async(lo, hi, pos, out, a.strategy, stream=s)
+        else:
+            col.run_async(lo, hi, out, a.strategy, s)
         e1.record(s)
         e1.synchronize()
         ms = e0.elapsed_time(e1)
     col.status(s)
     r = out.cpu().tolist()
-    nbytes = gbscan.scan_packed_words(a.n, a.b) * 4
-    print(json.dumps({"b": a.b, "n": a.n, "strategy": a.strategy, "order": a.order, "ms": ms,
+    nbytes = gbscan.scan_packed_words(a.n, a.b) * 4 + (4 * r[0] if a.select else 0)
+    print(json.dumps({"b": a.b, "n": a.n, "strategy": a.strategy, "order": a.order,
+                      "op": "select" if a.select else "count", "ms": ms,
                       "gbs": nbytes / (ms * 1e-3) / 1e9, "count": r[0], "sum": r[1], "blocks": r[2]}))
     col.close()
 
