@@ -796,7 +796,10 @@ def run_batched(args, dev, stream, gbscan, beta_gbs, t_dec_gvals):
     torch.cuda.synchronize()
     law_plan = plmod.choose_law(probe, feats, beta_gbs, t_dec_gvals, stream)
     probe.close()
-    mlp_plan = plmod.choose(net, feats, stream)
+    # switch away from the default plan only on a predicted gain above the
+    # network's own RMS error in log time (the final training loss is an MSE)
+    margin = float(np.sqrt(max(hist[-1], 0.0)))
+    mlp_plan = plmod.choose(net, feats, stream, margin=margin)
     net.close()
     plans = {"branchfree": ["branchfree"] * ncols, "law": law_plan, "planned_mlp": mlp_plan}
     res_b = torch.zeros((ncols, 4), dtype=torch.int64, device=dev)
@@ -822,6 +825,7 @@ def run_batched(args, dev, stream, gbscan, beta_gbs, t_dec_gvals):
             "per_column_launches": ncols, "plans": out,
             "planner": {"training_columns": 120, "labels": "log of each strategy's marginal device time as a one-entry batch",
                         "steps": 1500, "loss_first": round(hist[0], 4), "loss_last": round(hist[-1], 4),
+                        "decision_margin_log_time": round(margin, 4),
                         "train_and_label_s": round(train_s, 1)}}
 
 

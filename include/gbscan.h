@@ -281,6 +281,12 @@ scan_status scan_planner_train_step(scan_planner *planner, const float *dev_x, c
 /* dev_choice[rows] = argmin over strategies of the predicted log time. */
 scan_status scan_planner_choose(scan_planner *planner, const float *dev_x, uint32_t rows,
                                 int32_t *dev_choice, void *stream);
+/* As scan_planner_choose, but strategy 0 (the default plan) is kept unless
+ * another strategy's predicted log time is lower by more than `margin`
+ * (>= 0; e.g. the network's RMS error in log time, so that a plan changes
+ * only on a predicted gain larger than the model's own error). */
+scan_status scan_planner_choose_margin(scan_planner *planner, const float *dev_x, uint32_t rows,
+                                       float margin, int32_t *dev_choice, void *stream);
 /* Binary checkpoint: 16-byte header (magic, version 1, S, count) + floats. */
 scan_status scan_planner_save(const scan_planner *planner, const char *path);
 scan_status scan_planner_load(scan_planner *planner, const char *path);

@@ -126,13 +126,20 @@ __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float
     p[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
 }
 
-__global__ void k_argmin_rows(const float* __restrict__ y, int rows, int S, int32_t* __restrict__ out)
+// Strategy 0 (the default plan) is kept unless another strategy's predicted
+// log time is lower by more than `margin`; among those, the lowest wins.
+__global__ void k_argmin_rows(const float* __restrict__ y, int rows, int S, float margin,
+                              int32_t* __restrict__ out)
 {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= rows) return;
     int best = 0;
+    float bestv = y[n * S] - margin;
     for (int s = 1; s < S; ++s)
-        if (y[n * S + s] < y[n * S + best]) best = s;
+        if (y[n * S + s] < bestv) {
+            best = s;
+            bestv = y[n * S + s];
+        }
     out[n] = best;
 }
 
@@ -358,18 +365,25 @@ scan_status scan_planner_train_step(scan_planner* pl, const float* dev_x, const 
     return SCAN_OK;
 }
 
-scan_status scan_planner_choose(scan_planner* pl, const float* dev_x, uint32_t rows, int32_t* dev_choice,
-                                void* stream)
+scan_status scan_planner_choose_margin(scan_planner* pl, const float* dev_x, uint32_t rows, float margin,
+                                       int32_t* dev_choice, void* stream)
 {
+    if (!(margin >= 0.0f)) return pfail(SCAN_EINVAL, "margin must be >= 0");
     scan_status s = ensure_ws(pl, rows ? rows : 1);
     if (s != SCAN_OK) return s;
     const Acts a = acts(pl);
     s = scan_planner_forward(pl, dev_x, rows, a.y, stream);
     if (s != SCAN_OK || !rows) return s;
     k_argmin_rows<<<blocks_for(rows), 256, 0, static_cast<cudaStream_t>(stream)>>>(a.y, static_cast<int>(rows),
-                                                                                  pl->S, dev_choice);
+                                                                                  pl->S, margin, dev_choice);
     PL_CUDA(cudaGetLastError());
     return SCAN_OK;
+}
+
+scan_status scan_planner_choose(scan_planner* pl, const float* dev_x, uint32_t rows, int32_t* dev_choice,
+                                void* stream)
+{
+    return scan_planner_choose_margin(pl, dev_x, rows, 0.0f, dev_choice, stream);
 }
 
 scan_status scan_planner_save(const scan_planner* pl, const char* path)

@@ -89,6 +89,7 @@ SIGNATURES = {
     "scan_planner_gradients": (_st, [_vp, _vp, _vp, _u32, _vp, _vp, _vp]),
     "scan_planner_train_step": (_st, [_vp, _vp, _vp, _u32, ctypes.c_float, _vp, _vp]),
     "scan_planner_choose": (_st, [_vp, _vp, _u32, _vp, _vp]),
+    "scan_planner_choose_margin": (_st, [_vp, _vp, _u32, ctypes.c_float, _vp, _vp]),
     "scan_planner_save": (_st, [_vp, ctypes.c_char_p]),
     "scan_planner_load": (_st, [_vp, ctypes.c_char_p]),
     "scan_server_create": (_st, [_vp, _u32, _u32, _u64, _u32, ctypes.POINTER(_vp)]),
@@ -405,8 +406,12 @@ class Planner:
                                               _stream(stream), ctypes.byref(loss) if want_loss else None))
         return float(loss.value) if want_loss else None
 
-    def choose(self, dev_x, rows, dev_choice, stream=None):
-        _check(load().scan_planner_choose(self._h, _ptr(dev_x), rows, _ptr(dev_choice), _stream(stream)))
+    def choose(self, dev_x, rows, dev_choice, stream=None, margin=0.0):
+        if margin:
+            _check(load().scan_planner_choose_margin(self._h, _ptr(dev_x), rows, float(margin), _ptr(dev_choice),
+                                                     _stream(stream)))
+        else:
+            _check(load().scan_planner_choose(self._h, _ptr(dev_x), rows, _ptr(dev_choice), _stream(stream)))
 
     def save(self, path):
         _check(load().scan_planner_save(self._h, path.encode()))
