@@ -73,6 +73,18 @@ def _load():
             lib.oracle_scan_zoneskip.argtypes = [
                 _u32p, _u32p, _u32p, _u64, _u32, _u32, _i64, _i64,
                 ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_u64)]
+            lib.oracle_pack_rowmajor.restype = ctypes.c_int
+            lib.oracle_pack_rowmajor.argtypes = [_u32p, _u64, _u32, _u32, _u32p]
+            lib.oracle_unpack_rowmajor.restype = ctypes.c_int
+            lib.oracle_unpack_rowmajor.argtypes = [_u32p, _u64, _u32, _u32, _u32p]
+            lib.oracle_scan_rowmajor.restype = ctypes.c_int
+            lib.oracle_scan_rowmajor.argtypes = [
+                _u32p, _u64, _u32, _u32, _i64, _i64, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]
+            lib.oracle_pack_bytes.restype = ctypes.c_int
+            lib.oracle_pack_bytes.argtypes = [_u32p, _u64, _u32, _u32, _u32p]
+            lib.oracle_scan_bytes.restype = ctypes.c_int
+            lib.oracle_scan_bytes.argtypes = [
+                _u32p, _u64, _u32, _u32, _i64, _i64, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]
             lib.oracle_select_values.restype = _u64
             lib.oracle_select_values.argtypes = [_u32p, _u64, _i64, _i64, _u32p, _u64]
             lib.oracle_select_packed.restype = ctypes.c_int
@@ -198,3 +210,47 @@ def select_packed(words, n: int, b: int, base: int, lo: int, hi: int, capacity: 
     if rc != OK:
         raise ValueError("oracle_select_packed rejected the input")
     return out[:min(k.value, cap)], int(k.value)
+
+
+def pack_rowmajor(values, b: int, base: int = 0) -> np.ndarray:
+    """Row-major bit stream (paper §3 strategy (i)) of ``values``, padded to whole blocks."""
+    v = _u32arr(values)
+    out = np.zeros(max(packed_words(v.size, b), 1), np.uint32)
+    if _load().oracle_pack_rowmajor(v if v.size else np.zeros(1, np.uint32), v.size, b, base, out) != OK:
+        raise ValueError("oracle_pack_rowmajor rejected the input")
+    return out[:packed_words(v.size, b)]
+
+
+def unpack_rowmajor(words, n: int, b: int, base: int = 0) -> np.ndarray:
+    w = _u32arr(words)
+    out = np.zeros(max(n, 1), np.uint32)
+    if _load().oracle_unpack_rowmajor(w if w.size else np.zeros(2, np.uint32), n, b, base, out) != OK:
+        raise ValueError("oracle_unpack_rowmajor rejected the input")
+    return out[:n]
+
+
+def scan_rowmajor(words, n: int, b: int, base: int, lo: int, hi: int):
+    w = _u32arr(words)
+    c, s = _i64(), _i64()
+    if _load().oracle_scan_rowmajor(w if w.size else np.zeros(2, np.uint32), n, b, base, lo, hi,
+                                    ctypes.byref(c), ctypes.byref(s)) != OK:
+        raise ValueError("oracle_scan_rowmajor rejected the input")
+    return c.value, s.value
+
+
+def pack_bytes(values, b: int, base: int = 0) -> np.ndarray:
+    """Byte-aligned codes (paper §3 strategy (iii), b in {8, 16, 32}) as 32-bit words, padded to whole blocks."""
+    v = _u32arr(values)
+    out = np.zeros(max(packed_words(v.size, b), 1), np.uint32)
+    if _load().oracle_pack_bytes(v if v.size else np.zeros(1, np.uint32), v.size, b, base, out) != OK:
+        raise ValueError("oracle_pack_bytes rejected the input")
+    return out[:packed_words(v.size, b)]
+
+
+def scan_bytes(words, n: int, b: int, base: int, lo: int, hi: int):
+    w = _u32arr(words)
+    c, s = _i64(), _i64()
+    if _load().oracle_scan_bytes(w if w.size else np.zeros(1, np.uint32), n, b, base, lo, hi,
+                                 ctypes.byref(c), ctypes.byref(s)) != OK:
+        raise ValueError("oracle_scan_bytes rejected the input")
+    return c.value, s.value

@@ -205,6 +205,121 @@ int oracle_scan_zoneskip(const uint32_t *words, const uint32_t *zmin, const uint
 }
 
 /*
+ * Two further layouts of the same codes (paper §3 lists three decode
+ * strategies; the transposed one above is strategy (ii)).
+ *
+ * Row-major bit packing, strategy (i) ("scalar row-major bit-unpacking"):
+ * value i's code occupies bits [i*b, i*b + b) of one stream of 32-bit words,
+ * least significant bit first; bit p is bit (p mod 32) of word floor(p/32).
+ * The stream is zero-padded to whole 1024-value blocks, so it has the same
+ * oracle_packed_words(n, b) words as the transposed layout.
+ *
+ * Byte-aligned widths, strategy (iii): for b in {8, 16, 32} the codes form a
+ * plain little-endian array of b-bit integers (the same bytes as row-major
+ * packing at those widths), zero-padded the same way.
+ */
+int oracle_pack_rowmajor(const uint32_t *values, uint64_t n, uint32_t b, uint32_t base, uint32_t *out)
+{
+    uint64_t i, total = oracle_packed_words(n, b);
+    uint32_t k;
+    if (!width_ok(b, base)) return ORACLE_EINVAL;
+    for (i = 0; i < n; ++i) {
+        if (values[i] < base || (uint64_t)(values[i] - base) > ((1ull << b) - 1ull)) return ORACLE_EINVAL;
+    }
+    memset(out, 0, (size_t)total * sizeof(uint32_t));
+    for (i = 0; i < n; ++i) {
+        uint32_t u = values[i] - base;
+        for (k = 0; k < b; ++k) {
+            uint64_t p = i * (uint64_t)b + k;
+            if ((u >> k) & 1u) out[p / 32] |= 1u << (p % 32);
+        }
+    }
+    return ORACLE_OK;
+}
+
+/* Code of value i of a row-major stream (a 64-bit window over two words). */
+static uint32_t rowmajor_code_at(const uint32_t *words, uint64_t i, uint32_t b)
+{
+    uint64_t p = i * (uint64_t)b;
+    uint64_t w = p / 32;
+    uint32_t off = (uint32_t)(p % 32);
+    uint64_t window = words[w];
+    if (off + b > 32) window |= (uint64_t)words[w + 1] << 32;
+    return (uint32_t)((window >> off) & ((1ull << b) - 1ull));
+}
+
+int oracle_unpack_rowmajor(const uint32_t *words, uint64_t n, uint32_t b, uint32_t base, uint32_t *values)
+{
+    uint64_t i;
+    if (!width_ok(b, base)) return ORACLE_EINVAL;
+    for (i = 0; i < n; ++i) values[i] = rowmajor_code_at(words, i, b) + base;
+    return ORACLE_OK;
+}
+
+int oracle_scan_rowmajor(const uint32_t *words, uint64_t n, uint32_t b, uint32_t base, int64_t lo, int64_t hi,
+                         int64_t *count, int64_t *sum)
+{
+    int64_t c = 0, s = 0;
+    uint64_t i;
+    if (!width_ok(b, base)) return ORACLE_EINVAL;
+    for (i = 0; i < n; ++i) {
+        int64_t v = (int64_t)rowmajor_code_at(words, i, b) + (int64_t)base;
+        if (lo <= v && v < hi) {
+            c += 1;
+            s += v;
+        }
+    }
+    *count = c;
+    *sum = s;
+    return ORACLE_OK;
+}
+
+/* Byte-aligned codes: element i of a uint8/uint16/uint32 array. */
+static uint32_t bytes_code_at(const void *codes, uint64_t i, uint32_t b)
+{
+    if (b == 8) return ((const uint8_t *)codes)[i];
+    if (b == 16) return ((const uint16_t *)codes)[i];
+    return ((const uint32_t *)codes)[i];
+}
+
+int oracle_pack_bytes(const uint32_t *values, uint64_t n, uint32_t b, uint32_t base, void *out)
+{
+    uint64_t i, total = oracle_packed_words(n, b);
+    if (b != 8 && b != 16 && b != 32) return ORACLE_EINVAL;
+    if (!width_ok(b, base)) return ORACLE_EINVAL;
+    for (i = 0; i < n; ++i) {
+        if (values[i] < base || (uint64_t)(values[i] - base) > ((1ull << b) - 1ull)) return ORACLE_EINVAL;
+    }
+    memset(out, 0, (size_t)total * sizeof(uint32_t));
+    for (i = 0; i < n; ++i) {
+        uint32_t u = values[i] - base;
+        if (b == 8) ((uint8_t *)out)[i] = (uint8_t)u;
+        else if (b == 16) ((uint16_t *)out)[i] = (uint16_t)u;
+        else ((uint32_t *)out)[i] = u;
+    }
+    return ORACLE_OK;
+}
+
+int oracle_scan_bytes(const void *codes, uint64_t n, uint32_t b, uint32_t base, int64_t lo, int64_t hi,
+                      int64_t *count, int64_t *sum)
+{
+    int64_t c = 0, s = 0;
+    uint64_t i;
+    if (b != 8 && b != 16 && b != 32) return ORACLE_EINVAL;
+    if (!width_ok(b, base)) return ORACLE_EINVAL;
+    for (i = 0; i < n; ++i) {
+        int64_t v = (int64_t)bytes_code_at(codes, i, b) + (int64_t)base;
+        if (lo <= v && v < hi) {
+            c += 1;
+            s += v;
+        }
+    }
+    *count = c;
+    *sum = s;
+    return ORACLE_OK;
+}
+
+/*
  * Materializing select (paper §3 lists "a materializing select" beside the
  * counts; §4 "Branch" measures it): the positions i of the values with
  * lo <= v_i < hi, in increasing order.  The first min(count, capacity)

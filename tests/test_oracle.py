@@ -322,3 +322,57 @@ def test_select_empty_and_degenerate():
     assert k == 4096
     np.testing.assert_array_equal(pos, np.arange(4096, dtype=np.uint32))
 
+
+# ------------------------------------------- row-major and byte-aligned layouts
+def rowmajor_by_bits(values: np.ndarray, b: int, base: int) -> np.ndarray:
+    """Paper §3 strategy (i) written at bit level: code i's bit k is stream bit
+    i*b + k; stream bit p is bit p mod 32 of word p // 32; padded to whole blocks."""
+    n = values.size
+    u = (values.astype(np.uint64) - base)
+    bits = ((u[:, None] >> np.arange(b, dtype=np.uint64)) & 1).astype(np.uint8).reshape(-1)
+    nblocks = (n + 1023) // 1024
+    stream = np.zeros(nblocks * 1024 * b, dtype=np.uint8)
+    stream[:bits.size] = bits
+    words = stream.reshape(-1, 32).astype(np.uint64)
+    return (words << np.arange(32, dtype=np.uint64)).sum(axis=1).astype(np.uint32)
+
+
+@pytest.mark.parametrize("b", [1, 3, 7, 8, 13, 16, 21, 31, 32])
+def test_rowmajor_pack_matches_bit_level_stream(b):
+    base = 0 if b == 32 else 9
+    for n in (1, 33, 1024, 3 * 1024 + 17):
+        v = synth.uniform_values(synth.seed_for(61, b, n), n, b, base)
+        w = oracle.pack_rowmajor(v, b, base)
+        np.testing.assert_array_equal(w, rowmajor_by_bits(v, b, base))
+        np.testing.assert_array_equal(oracle.unpack_rowmajor(w, n, b, base), v)
+
+
+def test_rowmajor_at_byte_widths_is_the_plain_array():
+    for b, dt in [(8, np.uint8), (16, np.uint16), (32, np.uint32)]:
+        n = 5000
+        v = synth.uniform_values(62, n, b)
+        w = oracle.pack_rowmajor(v, b)
+        np.testing.assert_array_equal(w.view(dt)[:n], v.astype(dt))
+        np.testing.assert_array_equal(oracle.pack_bytes(v, b), w)
+        assert not w.view(dt)[n:].any()                      # zero padding to whole blocks
+
+
+@pytest.mark.parametrize("b", [2, 5, 8, 12, 16, 19, 27, 32])
+def test_rowmajor_and_bytes_scans_match_histogram(b):
+    base = 0 if b == 32 else 100
+    n = 7000
+    v = synth.uniform_values(synth.seed_for(63, b), n, b, base)
+    w = oracle.pack_rowmajor(v, b, base)
+    for i, sigma in enumerate([1e-3, 0.1, 0.5, 1.0]):
+        lo, hi = synth.pick_range(synth.seed_for(64, b, i), b, sigma, base)
+        m = (v.astype(np.int64) >= lo) & (v.astype(np.int64) < hi)
+        want = (int(m.sum()), int(v[m].astype(np.int64).sum()))
+        assert oracle.scan_rowmajor(w, n, b, base, lo, hi) == want
+        if b in (8, 16, 32):
+            assert oracle.scan_bytes(oracle.pack_bytes(v, b, base), n, b, base, lo, hi) == want
+
+
+def test_byte_layout_rejects_other_widths():
+    with pytest.raises(ValueError):
+        oracle.pack_bytes(np.arange(10, dtype=np.uint32), 12)
+

@@ -9,17 +9,26 @@ import numpy as np
 import pytest
 
 import synth
-from tests.test_oracle import hist_count_sum, layout_by_bits
+from tests.test_oracle import hist_count_sum, layout_by_bits, rowmajor_by_bits
 
 SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "oracle", "gbscan_oracle.c")
 
 MUTANTS = {
-    "inclusive upper bound": [("(int64_t)base;\n        if (lo <= v && v < hi) {\n            c += 1;",
-                               "(int64_t)base;\n        if (lo <= v && v <= hi) {\n            c += 1;")],
+    "inclusive upper bound": [("(int64_t)code_at(words, i, b) + (int64_t)base;\n        if (lo <= v && v < hi) {\n"
+                               "            c += 1;",
+                               "(int64_t)code_at(words, i, b) + (int64_t)base;\n        if (lo <= v && v <= hi) {\n"
+                               "            c += 1;")],
     "base not added back": [("int64_t v = (int64_t)code_at(words, i, b) + (int64_t)base;\n        if (lo <= v && v < hi) {\n"
                              "            c += 1;",
                              "int64_t v = (int64_t)code_at(words, i, b);\n        if (lo <= v && v < hi) {\n"
                              "            c += 1;")],
+    "row-major stream written MSB first": [("if ((u >> k) & 1u) out[p / 32] |= 1u << (p % 32);",
+                                            "if ((u >> k) & 1u) out[p / 32] |= 1u << (31 - p % 32);")],
+    "row-major straddling high word dropped": [("    if (off + b > 32) window |= (uint64_t)words[w + 1] << 32;\n"
+                                                "    return (uint32_t)((window >> off) & ((1ull << b) - 1ull));\n}\n\n"
+                                                "int oracle_unpack_rowmajor",
+                                                "    return (uint32_t)((window >> off) & ((1ull << b) - 1ull));\n}\n\n"
+                                                "int oracle_unpack_rowmajor")],
     "select inclusive upper bound": [("(int64_t)base;\n        if (lo <= v && v < hi) {\n            if (k < capacity)",
                                       "(int64_t)base;\n        if (lo <= v && v <= hi) {\n            if (k < capacity)")],
     "select position off by one": [("if (k < capacity) pos[k] = (uint32_t)i;\n            k += 1;\n        }\n    }\n"
@@ -36,8 +45,8 @@ MUTANTS = {
                                   "        uint32_t mn = 0xFFFFFFFFu, mx = 0;",
                                   "        uint64_t last = first + BLOCK_VALUES;\n"
                                   "        uint32_t mn = 0xFFFFFFFFu, mx = 0;")],
-    "top bit of each code dropped": [("return (uint32_t)((window >> off) & ((1ull << b) - 1ull));",
-                                      "return (uint32_t)((window >> off) & ((1ull << (b - 1)) - 1ull));")],
+    "top bit of each code dropped": [("lane)] << 32;\n    return (uint32_t)((window >> off) & ((1ull << b) - 1ull));",
+                                      "lane)] << 32;\n    return (uint32_t)((window >> off) & ((1ull << (b - 1)) - 1ull));")],
     "lane and row swapped": [("uint32_t lane = (uint32_t)(j % LANES);\n        uint64_t row = j / LANES;",
                               "uint32_t lane = (uint32_t)(j / LANES);\n        uint64_t row = j % LANES;"),
                              ("uint32_t lane = (uint32_t)(j % LANES);\n    uint64_t row = j / LANES;",
@@ -64,6 +73,9 @@ class Lib:
         self.l.oracle_scan_zoneskip.argtypes = [u32p, u32p, u32p, u64, u32, u32, i64, i64, ctypes.POINTER(i64),
                                                 ctypes.POINTER(i64), ctypes.POINTER(u64)]
         self.l.oracle_select_packed.argtypes = [u32p, u64, u32, u32, i64, i64, u32p, u64, ctypes.POINTER(u64)]
+        self.l.oracle_pack_rowmajor.argtypes = [u32p, u64, u32, u32, u32p]
+        self.l.oracle_scan_rowmajor.argtypes = [u32p, u64, u32, u32, i64, i64, ctypes.POINTER(i64),
+                                                ctypes.POINTER(i64)]
 
     def pack(self, v, b, base=0):
         out = np.zeros(((v.size + 1023) // 1024) * 32 * b, np.uint32)
@@ -86,6 +98,16 @@ class Lib:
         self.l.oracle_zonemap(w, n, b, base, mn, mx)
         return mn, mx
 
+    def pack_rowmajor(self, v, b, base=0):
+        out = np.zeros(((v.size + 1023) // 1024) * 32 * b, np.uint32)
+        assert self.l.oracle_pack_rowmajor(v, v.size, b, base, out) == 0
+        return out
+
+    def scan_rowmajor(self, w, n, b, base, lo, hi):
+        c, s = ctypes.c_int64(), ctypes.c_int64()
+        self.l.oracle_scan_rowmajor(w, n, b, base, lo, hi, ctypes.byref(c), ctypes.byref(s))
+        return c.value, s.value
+
     def select(self, w, n, b, base, lo, hi, cap):
         out, k = np.zeros(max(cap, 1), np.uint32), ctypes.c_uint64()
         self.l.oracle_select_packed(w, n, b, base, lo, hi, out, cap, ctypes.byref(k))
@@ -99,7 +121,8 @@ class Lib:
 
 def pins(o):
     """A compact copy of the independent pins (layout bits, round trip, brute force,
-    frame of reference, zone maps, zone-skip exactness and skip rule, select positions)."""
+    frame of reference, zone maps, zone-skip exactness and skip rule, row-major streams,
+    select positions)."""
     for b in (3, 8, 13, 32):
         for n in (1025, 4096 + 7):
             v = synth.uniform_values(synth.seed_for(77, b, n), n, b)
@@ -129,6 +152,14 @@ def pins(o):
         m = (v >= lo) & (v < hi)
         assert (c, s) == (int(m.sum()), int(v[m].astype(np.int64).sum()))
         assert t == int(np.sum(~((mx < lo) | (mn >= hi))))
+    # row-major layout: bit-level stream and brute-force scans
+    for b in (3, 13, 24):
+        v = synth.uniform_values(synth.seed_for(78, b), 2100, b)
+        w = o.pack_rowmajor(v, b)
+        np.testing.assert_array_equal(w, rowmajor_by_bits(v, b, 0))
+        lo, hi = int(v[7]), int(v[7]) + (1 << (b - 1))
+        m = (v.astype(np.int64) >= lo) & (v.astype(np.int64) < hi)
+        assert o.scan_rowmajor(w, 2100, b, 0, lo, hi) == (int(m.sum()), int(v[m].astype(np.int64).sum()))
     # materializing select: positions fixed by flatnonzero; capacity keeps the full count
     n, b, base = 3000, 7, 40
     v = synth.uniform_values(8, n, b, base)
