@@ -469,6 +469,7 @@ def run_ours(args, world, rank, local):
     torch.cuda.empty_cache()
     plain = None if args.no_extra else run_plain(args, dev, stream, gbscan, beta_read)
     select = None if args.no_extra else run_select(args, dev, stream, gbscan, peaks().get("hbm_gbs", 6800.0))
+    layouts = None if args.no_extra else run_layouts(args, dev, stream, gbscan, beta_read)
     zone = None if args.no_extra else run_zone_sweep(args, dev, stream, gbscan)
     tdec = [law["branchfree"]["t_dec_gvals"], law["branchy"]["t_dec_gvals"],
             law["branchfree"]["t_dec_gvals"], law["branchy"]["t_dec_gvals"]]
@@ -492,6 +493,7 @@ def run_ours(args, world, rank, local):
         "plain_scan": plain,
         "zone_sweep": zone,
         "select": select,
+        "layouts": layouts,
         "batched": batched,
         "serving": serving,
         "realised_sigma": realised,
@@ -573,6 +575,61 @@ def _graph_time(fn, stream, reps=20, trials=5):
             ts.append(e0.elapsed_time(e1) / reps)
     del g
     return statistics.median(ts)
+
+
+def run_layouts(args, dev, stream, gbscan, beta_read):
+    """The paper's three decode strategies (§3) on the GPU and the law refitted per
+    strategy (the analogue of Table tab:fit): lane-interleaved ("transposed", ii),
+    row-major bit stream ("scalar", i) for b = 1..32, byte-aligned plain arrays (iii)
+    for b in {8, 16, 32}; N = 2^28 uniform values per column, sigma = 0.1, branch-free,
+    median of 3 single-launch CUDA-event times, each column read from HBM (the column
+    before is a different one and every column at b >= 4 is larger than L2)."""
+    import torch
+
+    from paper_2606_22423_gb300 import lawfit
+
+    n = 1 << 28
+    res = torch.zeros(4, dtype=torch.int64, device=dev)
+    plan = [("lanes", list(range(1, 33))), ("rowmajor", list(range(1, 33))), ("bytes", [8, 16, 32])]
+    out = {"workload": "decode strategies: N=2^28 uniform values per column, sigma=0.1, branch-free; "
+                       "lanes and row-major for b=1..32, byte-aligned for b in {8,16,32}",
+           "beta_read_gbs": round(beta_read, 1), "per_layout": {}}
+    for layout, widths in plan:
+        rows = {}
+        for b in widths:
+            with torch.cuda.stream(stream):
+                v = synth.uniform_values_device(synth.seed_for(12, b), n, b, device=dev)
+                col = gbscan.Column.from_device(v, n, b, stream=stream, layout=layout)
+                del v
+            torch.cuda.synchronize()
+            lo, hi = synth.pick_range(synth.seed_for(12, b, 1), b, 0.1)
+            col.run_async(lo, hi, res, "branchfree", stream)
+            ts = []
+            for _ in range(3):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                col.run_async(lo, hi, res, "branchfree", stream)
+                e1.record(stream)
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            col.status(stream)
+            ms = statistics.median(ts)
+            gbs = gbscan.scan_packed_words(n, b) * 4 / (ms * 1e-3) / 1e9
+            rows[b] = {"gbs": round(gbs, 1), "gvals_per_s": round(n / (ms * 1e-3) / 1e9, 1),
+                       "f": round(gbs / beta_read, 4)}
+            col.close()
+        bb = np.array(sorted(rows), dtype=float)
+        ff = np.array([rows[b]["f"] for b in sorted(rows)])
+        t_dec, med = lawfit.fit_tdec(bb, ff, beta_read * 1e9)
+        out["per_layout"][layout] = {
+            "per_b": {str(b): r for b, r in rows.items()},
+            "t_dec_gvals": round(t_dec / 1e9, 1), "b_star": round(lawfit.ridge(t_dec, beta_read * 1e9), 2),
+            "median_abs_err": round(med, 4),
+            "t_dec_below_ridge_gvals": round(float(np.median([rows[b]["gvals_per_s"] for b in rows
+                                                               if rows[b]["f"] < 0.7] or [float("nan")])), 1),
+        }
+    torch.cuda.empty_cache()
+    return out
 
 
 SELECT_SIGMAS = [1e-4, 1e-3, 1e-2, 0.05, 0.1, 0.3, 0.5, 0.7, 0.9, 0.99, 1.0]

@@ -108,6 +108,36 @@ scan_status scan_encode_host(const uint32_t *host_values, uint64_t n, uint32_t b
 scan_status scan_encode_device(const uint32_t *dev_values, uint64_t n, uint32_t b, uint32_t base,
                                uint32_t *dev_out, void *stream);
 
+/* ------------------------------------------------------------- layouts */
+
+/* Order of the codes inside each 1024-value block (paper §3, three decode
+ * strategies).  Every layout occupies the same scan_packed_words(n, b) words,
+ * block k at words [32*b*k, 32*b*(k+1)), the last block zero-padded.
+ *   SCAN_LAYOUT_LANES   : lane-interleaved ("FastLanes-style transposed",
+ *                         strategy ii; see scan_encode_host).  Default.
+ *   SCAN_LAYOUT_ROWMAJOR: value i at bits [i*b, i*b + b) of one LSB-first
+ *                         stream of 32-bit words ("scalar row-major",
+ *                         strategy i).
+ *   SCAN_LAYOUT_BYTES   : b in {8, 16, 32}: the codes as a plain uint8 /
+ *                         uint16 / uint32 array ("byte-aligned", strategy
+ *                         iii) -- the same bytes as SCAN_LAYOUT_ROWMAJOR at
+ *                         those widths, read by a byte-permute decoder.
+ * At b = 32 all three are the plain array (and read by the same kernel).
+ * Only lane-interleaved columns take zone maps, zone-skip strategies, the
+ * select, batches and the server (SCAN_EINVAL otherwise). */
+typedef enum {
+    SCAN_LAYOUT_LANES = 0,
+    SCAN_LAYOUT_ROWMAJOR = 1,
+    SCAN_LAYOUT_BYTES = 2
+} scan_layout;
+
+/* scan_encode_host / scan_encode_device for any layout (SCAN_EINVAL for
+ * SCAN_LAYOUT_BYTES unless b is 8, 16 or 32). */
+scan_status scan_encode_host_layout(const uint32_t *host_values, uint64_t n, uint32_t b, uint32_t base,
+                                    scan_layout layout, uint32_t *host_out);
+scan_status scan_encode_device_layout(const uint32_t *dev_values, uint64_t n, uint32_t b, uint32_t base,
+                                      scan_layout layout, uint32_t *dev_out, void *stream);
+
 /* -------------------------------------------------------------- columns */
 
 /* Encode host values on the host, allocate device memory and upload.
@@ -123,6 +153,17 @@ scan_status scan_column_create_device(const uint32_t *dev_values, uint64_t n, ui
  * 16-byte aligned) without copying; the caller keeps ownership. */
 scan_status scan_column_create_packed(const uint32_t *dev_packed, uint64_t n, uint32_t b,
                                       uint32_t base, void *stream, scan_column **out);
+
+/* The three creators for a given layout (the ones above use SCAN_LAYOUT_LANES). */
+scan_status scan_column_create_layout(const uint32_t *host_values, uint64_t n, uint32_t b, uint32_t base,
+                                      scan_layout layout, void *stream, scan_column **out);
+scan_status scan_column_create_device_layout(const uint32_t *dev_values, uint64_t n, uint32_t b,
+                                             uint32_t base, scan_layout layout, void *stream,
+                                             scan_column **out);
+scan_status scan_column_create_packed_layout(const uint32_t *dev_packed, uint64_t n, uint32_t b,
+                                             uint32_t base, scan_layout layout, void *stream,
+                                             scan_column **out);
+scan_status scan_column_get_layout(const scan_column *col, scan_layout *layout);
 
 /* Overwrite the column's packed bytes from a host buffer of
  * scan_packed_words(n, b) words (asynchronous if host_packed is pinned).

@@ -388,8 +388,15 @@ scan_status scan_batch_create(scan_column* const* cols, uint32_t ncols, const sc
     gb_set_last_error("");
     if (!out || (ncols && !cols)) return bfail(SCAN_EINVAL, "null pointer");
     *out = nullptr;
-    for (uint32_t i = 0; i < ncols; ++i)
+    for (uint32_t i = 0; i < ncols; ++i) {
         if (!cols[i]) return bfail(SCAN_EINVAL, "a column pointer is NULL");
+        const uint32_t* pk;
+        const uint2* zm;
+        uint64_t n;
+        uint32_t b, base;
+        if (!gb_column_view(cols[i], &pk, &n, &b, &base, &zm))
+            return bfail(SCAN_EINVAL, "batched scans take lane-interleaved columns");
+    }
     auto* bt = new (std::nothrow) scan_batch();
     if (!bt) return bfail(SCAN_ENOMEM, "host allocation failed");
     bt->ncols = ncols;

@@ -148,6 +148,7 @@ struct scan_column {
     void* ws_raw = nullptr;
     Workspace ws{};
     scan_result* host_result = nullptr;  // pinned staging, 48 bytes (result + status)
+    int layout = SCAN_LAYOUT_LANES;         // order of the codes inside each block
     unsigned long long* sel_agg = nullptr;  // materializing select: tagged CTA totals
     uint64_t sel_words = 0;
     uint32_t sel_epoch = 0;
@@ -157,7 +158,7 @@ struct scan_column {
 bool gb_column_view(const scan_column* c, const uint32_t** packed, uint64_t* n, uint32_t* b,
                     uint32_t* base, const uint2** zonemap)
 {
-    if (!c) return false;
+    if (!c || c->layout != SCAN_LAYOUT_LANES) return false;
     *packed = c->packed;
     *n = c->n;
     *b = c->b;
@@ -229,6 +230,36 @@ __global__ void k_encode(const uint32_t* __restrict__ v, uint64_t n, uint32_t b,
     }
 }
 
+// Row-major stream (§3 strategy i; at b = 8/16/32 also the byte-aligned
+// array): one thread per output word; word t holds stream bits
+// [32t, 32t + 32), i.e. parts of values floor(32t/b) .. floor((32t+31)/b).
+__global__ void k_encode_rowmajor(const uint32_t* __restrict__ v, uint64_t n, uint32_t b, uint32_t base,
+                                  uint32_t* __restrict__ out, uint64_t words, unsigned int* status)
+{
+    const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+    const uint64_t mask = (b == 32) ? 0xffffffffull : ((1ull << b) - 1ull);
+    for (uint64_t t = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; t < words; t += stride) {
+        const uint64_t bit0 = 32ull * t;
+        const uint64_t first = bit0 / b, last = (bit0 + 31u) / b;
+        uint64_t acc = 0;
+        bool bad = false;
+        for (uint64_t j = first; j <= last; ++j) {
+            uint64_t u = 0;
+            if (j < n) {
+                const uint32_t x = v[j];
+                u = static_cast<uint64_t>(x) - base;
+                // the thread holding the value's first bit checks its range
+                if (j * b >= bit0 && (x < base || (u & ~mask))) bad = true;
+                u &= mask;
+            }
+            const int64_t sh = static_cast<int64_t>(j * b) - static_cast<int64_t>(bit0);
+            acc |= sh >= 0 ? (u << sh) : (u >> (-sh));
+        }
+        out[t] = static_cast<uint32_t>(acc);
+        if (bad) atomicOr(status, gb::kErrRange);
+    }
+}
+
 // Waits, with the library's bounded wait, on a transaction barrier that
 // nothing ever completes; the wait gives up after limit_ns and records the
 // timeout in the status word exactly as a lost copy would.
@@ -288,6 +319,34 @@ void encode_blocks(const uint32_t* v, uint64_t n, uint32_t b, uint32_t base, uin
             }
         }
     }
+}
+
+void encode_rowmajor_blocks(const uint32_t* v, uint64_t n, uint32_t b, uint32_t base, uint32_t* out,
+                            uint64_t k0, uint64_t k1)
+{
+    // value by value: append each code to a 64-bit bit buffer, spill whole words
+    for (uint64_t k = k0; k < k1; ++k) {
+        uint32_t* blk = out + k * 32ull * b;
+        uint64_t bits = 0;
+        uint32_t fill = 0, w = 0;
+        for (uint32_t j = 0; j < 1024; ++j) {
+            const uint64_t i = (k << 10) + j;
+            const uint64_t u = i < n ? static_cast<uint64_t>(v[i] - base) : 0ull;
+            bits |= u << fill;
+            fill += b;
+            if (fill >= 32) {
+                blk[w++] = static_cast<uint32_t>(bits);
+                bits >>= 32;
+                fill -= 32;
+            }
+        }
+    }
+}
+
+bool layout_ok(uint32_t b, scan_layout layout)
+{
+    if (layout == SCAN_LAYOUT_LANES || layout == SCAN_LAYOUT_ROWMAJOR) return true;
+    return layout == SCAN_LAYOUT_BYTES && (b == 8 || b == 16 || b == 32);
 }
 
 scan_status check_values_host(const uint32_t* v, uint64_t n, uint32_t b, uint32_t base)
@@ -389,6 +448,16 @@ scan_status enqueue_scan(scan_column* c, scan_pred pred, scan_strategy strategy,
     case SCAN_ZONE_SKIP_BR: op = gb::kOpQueueBR; break;
     default: return fail(SCAN_EINVAL, "unknown strategy %d", static_cast<int>(strategy));
     }
+    // at b = 32 every layout is the plain array, which the lane kernels read
+    if (c->layout != SCAN_LAYOUT_LANES && c->b != 32) {
+        const bool branchy = op == gb::kOpFullBR;
+        if (op != gb::kOpFullBF && op != gb::kOpFullBR)
+            return fail(SCAN_EINVAL, "zone-skip strategies need a lane-interleaved column");
+        if (c->layout == SCAN_LAYOUT_ROWMAJOR) op = branchy ? gb::kOpRowBR : gb::kOpRowBF;
+        else op = branchy ? gb::kOpBytesBR : gb::kOpBytesBF;
+    } else if (c->layout != SCAN_LAYOUT_LANES && op != gb::kOpFullBF && op != gb::kOpFullBR) {
+        return fail(SCAN_EINVAL, "zone-skip strategies need a lane-interleaved column");
+    }
     if (op == gb::kOpQueueBF || op == gb::kOpQueueBR) {
         if (!c->zonemap_valid) return fail(SCAN_EINVAL, "zone-skip strategy needs scan_zonemap_build first");
         const uint64_t full = c->n >> 10;
@@ -433,25 +502,34 @@ uint64_t scan_packed_words(uint64_t n, uint32_t b)
 scan_status scan_encode_host(const uint32_t* host_values, uint64_t n, uint32_t b, uint32_t base,
                              uint32_t* host_out)
 {
+    return scan_encode_host_layout(host_values, n, b, base, SCAN_LAYOUT_LANES, host_out);
+}
+
+scan_status scan_encode_host_layout(const uint32_t* host_values, uint64_t n, uint32_t b, uint32_t base,
+                                    scan_layout layout, uint32_t* host_out)
+{
     g_err.clear();
     if (!width_ok(b, base)) return fail(SCAN_EINVAL, "bad width b=%u / base=%u", b, base);
+    if (!layout_ok(b, layout)) return fail(SCAN_EINVAL, "layout %d does not take b=%u", static_cast<int>(layout), b);
     if (n > kMaxValues) return fail(SCAN_EINVAL, "n=%llu exceeds 2^31", static_cast<unsigned long long>(n));
     if (n == 0) return SCAN_OK;
     if (!host_values || !host_out) return fail(SCAN_EINVAL, "null pointer");
     scan_status s = check_values_host(host_values, n, b, base);
     if (s != SCAN_OK) return s;
     const uint64_t nb = n_blocks(n);
+    // the lane layout at b = 32 and the byte layouts are the row-major stream
+    auto* enc = layout == SCAN_LAYOUT_LANES ? encode_blocks : encode_rowmajor_blocks;
     unsigned hw = std::max(1u, std::thread::hardware_concurrency());
     const unsigned threads = static_cast<unsigned>(std::min<uint64_t>(std::min(hw, 64u), (nb + 63) / 64));
     if (threads <= 1) {
-        encode_blocks(host_values, n, b, base, host_out, 0, nb);
+        enc(host_values, n, b, base, host_out, 0, nb);
         return SCAN_OK;
     }
     std::vector<std::thread> pool;
     const uint64_t per = (nb + threads - 1) / threads;
     for (unsigned t = 0; t < threads; ++t) {
         const uint64_t k0 = std::min(nb, t * per), k1 = std::min(nb, k0 + per);
-        pool.emplace_back(encode_blocks, host_values, n, b, base, host_out, k0, k1);
+        pool.emplace_back(enc, host_values, n, b, base, host_out, k0, k1);
     }
     for (auto& th : pool) th.join();
     return SCAN_OK;
@@ -460,8 +538,15 @@ scan_status scan_encode_host(const uint32_t* host_values, uint64_t n, uint32_t b
 scan_status scan_encode_device(const uint32_t* dev_values, uint64_t n, uint32_t b, uint32_t base,
                                uint32_t* dev_out, void* stream)
 {
+    return scan_encode_device_layout(dev_values, n, b, base, SCAN_LAYOUT_LANES, dev_out, stream);
+}
+
+scan_status scan_encode_device_layout(const uint32_t* dev_values, uint64_t n, uint32_t b, uint32_t base,
+                                      scan_layout layout, uint32_t* dev_out, void* stream)
+{
     g_err.clear();
     if (!width_ok(b, base)) return fail(SCAN_EINVAL, "bad width b=%u / base=%u", b, base);
+    if (!layout_ok(b, layout)) return fail(SCAN_EINVAL, "layout %d does not take b=%u", static_cast<int>(layout), b);
     if (n > kMaxValues) return fail(SCAN_EINVAL, "n exceeds 2^31");
     if (n == 0) return SCAN_OK;
     if (!dev_values || !dev_out) return fail(SCAN_EINVAL, "null pointer");
@@ -472,7 +557,10 @@ scan_status scan_encode_device(const uint32_t* dev_values, uint64_t n, uint32_t 
     GB_CUDA(cudaMemsetAsync(flag, 0, sizeof(unsigned int), st));
     const uint64_t words = scan_packed_words(n, b);
     const int grid = persistent_grid() * 8;
-    k_encode<<<grid, 256, 0, st>>>(dev_values, n, b, base, dev_out, words, flag);
+    if (layout == SCAN_LAYOUT_LANES)
+        k_encode<<<grid, 256, 0, st>>>(dev_values, n, b, base, dev_out, words, flag);
+    else
+        k_encode_rowmajor<<<grid, 256, 0, st>>>(dev_values, n, b, base, dev_out, words, flag);
     GB_CUDA(cudaGetLastError());
     unsigned int hflag = 0;
     GB_CUDA(cudaMemcpyAsync(&hflag, flag, sizeof hflag, cudaMemcpyDeviceToHost, st));
@@ -485,10 +573,17 @@ scan_status scan_encode_device(const uint32_t* dev_values, uint64_t n, uint32_t 
 scan_status scan_column_create(const uint32_t* host_values, uint64_t n, uint32_t b, uint32_t base,
                                void* stream, scan_column** out)
 {
+    return scan_column_create_layout(host_values, n, b, base, SCAN_LAYOUT_LANES, stream, out);
+}
+
+scan_status scan_column_create_layout(const uint32_t* host_values, uint64_t n, uint32_t b, uint32_t base,
+                                      scan_layout layout, void* stream, scan_column** out)
+{
     g_err.clear();
     if (!out) return fail(SCAN_EINVAL, "out is NULL");
     *out = nullptr;
     if (!width_ok(b, base)) return fail(SCAN_EINVAL, "bad width b=%u / base=%u", b, base);
+    if (!layout_ok(b, layout)) return fail(SCAN_EINVAL, "layout %d does not take b=%u", static_cast<int>(layout), b);
     if (n > kMaxValues) return fail(SCAN_EINVAL, "n exceeds 2^31");
     if (n && !host_values) return fail(SCAN_EINVAL, "host_values is NULL");
     const uint64_t words = scan_packed_words(n, b);
@@ -498,11 +593,12 @@ scan_status scan_column_create(const uint32_t* host_values, uint64_t n, uint32_t
     } catch (...) {
         return fail(SCAN_ENOMEM, "host staging allocation failed");
     }
-    scan_status s = scan_encode_host(host_values, n, b, base, packed.data());
+    scan_status s = scan_encode_host_layout(host_values, n, b, base, layout, packed.data());
     if (s != SCAN_OK) return s;
     scan_column* c = nullptr;
     s = new_column(n, b, base, &c);
     if (s != SCAN_OK) return s;
+    c->layout = layout;
     cudaError_t e = cudaMalloc(&c->packed, std::max<uint64_t>(words, 4) * 4);
     if (e != cudaSuccess) {
         scan_column_destroy(c);
@@ -524,10 +620,17 @@ scan_status scan_column_create(const uint32_t* host_values, uint64_t n, uint32_t
 scan_status scan_column_create_device(const uint32_t* dev_values, uint64_t n, uint32_t b,
                                       uint32_t base, void* stream, scan_column** out)
 {
+    return scan_column_create_device_layout(dev_values, n, b, base, SCAN_LAYOUT_LANES, stream, out);
+}
+
+scan_status scan_column_create_device_layout(const uint32_t* dev_values, uint64_t n, uint32_t b, uint32_t base,
+                                             scan_layout layout, void* stream, scan_column** out)
+{
     g_err.clear();
     if (!out) return fail(SCAN_EINVAL, "out is NULL");
     *out = nullptr;
     if (!width_ok(b, base)) return fail(SCAN_EINVAL, "bad width b=%u / base=%u", b, base);
+    if (!layout_ok(b, layout)) return fail(SCAN_EINVAL, "layout %d does not take b=%u", static_cast<int>(layout), b);
     if (n > kMaxValues) return fail(SCAN_EINVAL, "n exceeds 2^31");
     if (n && !dev_values) return fail(SCAN_EINVAL, "dev_values is NULL");
     scan_column* c = nullptr;
@@ -540,7 +643,8 @@ scan_status scan_column_create_device(const uint32_t* dev_values, uint64_t n, ui
         return cuda_fail(e, "cudaMalloc(packed)");
     }
     c->owns_packed = true;
-    s = scan_encode_device(dev_values, n, b, base, c->packed, stream);
+    c->layout = layout;
+    s = scan_encode_device_layout(dev_values, n, b, base, layout, c->packed, stream);
     if (s != SCAN_OK) {
         std::string msg = g_err;
         scan_column_destroy(c);
@@ -554,11 +658,18 @@ scan_status scan_column_create_device(const uint32_t* dev_values, uint64_t n, ui
 scan_status scan_column_create_packed(const uint32_t* dev_packed, uint64_t n, uint32_t b,
                                       uint32_t base, void* stream, scan_column** out)
 {
+    return scan_column_create_packed_layout(dev_packed, n, b, base, SCAN_LAYOUT_LANES, stream, out);
+}
+
+scan_status scan_column_create_packed_layout(const uint32_t* dev_packed, uint64_t n, uint32_t b, uint32_t base,
+                                             scan_layout layout, void* stream, scan_column** out)
+{
     (void)stream;
     g_err.clear();
     if (!out) return fail(SCAN_EINVAL, "out is NULL");
     *out = nullptr;
     if (!width_ok(b, base)) return fail(SCAN_EINVAL, "bad width b=%u / base=%u", b, base);
+    if (!layout_ok(b, layout)) return fail(SCAN_EINVAL, "layout %d does not take b=%u", static_cast<int>(layout), b);
     if (n > kMaxValues) return fail(SCAN_EINVAL, "n exceeds 2^31");
     if (n && !dev_packed) return fail(SCAN_EINVAL, "dev_packed is NULL");
     if (reinterpret_cast<uintptr_t>(dev_packed) & 15u)
@@ -568,7 +679,16 @@ scan_status scan_column_create_packed(const uint32_t* dev_packed, uint64_t n, ui
     if (s != SCAN_OK) return s;
     c->packed = const_cast<uint32_t*>(dev_packed);
     c->owns_packed = false;
+    c->layout = layout;
     *out = c;
+    return SCAN_OK;
+}
+
+scan_status scan_column_get_layout(const scan_column* col, scan_layout* layout)
+{
+    g_err.clear();
+    if (!col || !layout) return fail(SCAN_EINVAL, "null pointer");
+    *layout = static_cast<scan_layout>(col->layout);
     return SCAN_OK;
 }
 
@@ -617,6 +737,7 @@ scan_status scan_zonemap_build(scan_column* col, void* stream)
 {
     g_err.clear();
     if (!col) return fail(SCAN_EINVAL, "col is NULL");
+    if (col->layout != SCAN_LAYOUT_LANES) return fail(SCAN_EINVAL, "zone maps are built on lane-interleaved columns");
     if (col->zonemap_valid) return SCAN_OK;
     const uint64_t nb = n_blocks(col->n);
     if (!col->zonemap) {

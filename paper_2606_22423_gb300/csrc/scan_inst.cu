@@ -46,6 +46,15 @@ cudaError_t launch_b(int op, const ScanParams& p, int grid, cudaStream_t st)
     case kOpQueueBF: return launch_one<B, kOpQueueBF>(k_scan_queue<B, false>, p, grid, st);
     case kOpQueueBR: return launch_one<B, kOpQueueBR>(k_scan_queue<B, true>, p, grid, st);
     case kOpZoneBuild: return launch_one<B, kOpZoneBuild>(k_zonemap_build<B>, p, grid, st);
+    case kOpRowBF: return launch_one<B, kOpRowBF>(k_scan_full<B, false, kLayRow>, p, grid, st);
+    case kOpRowBR: return launch_one<B, kOpRowBR>(k_scan_full<B, true, kLayRow>, p, grid, st);
+    case kOpBytesBF:
+    case kOpBytesBR:
+        if constexpr (B == 8 || B == 16) {
+            if (op == kOpBytesBF) return launch_one<B, kOpBytesBF>(k_scan_full<B, false, kLayBytes>, p, grid, st);
+            return launch_one<B, kOpBytesBR>(k_scan_full<B, true, kLayBytes>, p, grid, st);
+        }
+        return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
     }
 }

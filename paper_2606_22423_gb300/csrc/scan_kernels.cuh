@@ -389,6 +389,172 @@ __device__ __forceinline__ const typename Geo<B>::Vec* block_rows(const unsigned
     return reinterpret_cast<const typename Geo<B>::Vec*>(blk) + q;
 }
 
+// ------------------------------------------- the other layouts (§3 i, iii)
+// A column's 1024-value blocks occupy the same 128*b bytes in every layout;
+// only the order of the codes inside a block differs:
+//   kLayLanes : lane-interleaved (strategy ii, everything above);
+//   kLayRow   : row-major bit stream, value j of the block at bits
+//               [j*b, j*b + b) of the block's 32*b words (strategy i);
+//   kLayBytes : b in {8, 16}: the codes as a plain uint8/uint16 array
+//               (strategy iii; b = 32 is the lane layout byte for byte).
+// The staging pipeline is shared; these consumers put all 32 lanes on one
+// block at a time, 32 codes per lane, with the accumulators of agg_block.
+enum Layout : int { kLayLanes = 0, kLayRow = 1, kLayBytes = 2 };
+
+template <int B, bool BRANCHY>
+__device__ __forceinline__ void acc_one(uint32_t ui, const Lanes& L, uint32_t& a, uint32_t& c, uint64_t& s64)
+{
+    constexpr int kMode = B <= 21 ? 0 : (B <= 27 ? 1 : 2);
+    if constexpr (BRANCHY) {
+        const uint32_t t = imad(ui, L.one, L.negloi);
+        const bool m = t <= L.wm1;
+        if (__any_sync(kFull, m)) {
+            if (m) {
+                if constexpr (kMode != 0) c += 1u;
+                if constexpr (kMode == 2) s64 += ui;
+                else a = imad(ui, L.one, a);
+            }
+        }
+    } else if constexpr (kMode == 0) {
+        acc0_imad(a, ui, L);
+    } else if constexpr (kMode == 1) {
+        acc1_imad(c, a, ui, L);
+    } else {
+        if ((ui - L.loi) <= L.wm1) {
+            c += 1u;
+            s64 += ui;
+        }
+    }
+}
+
+// Fold one lane's 32 codes of accumulation into the 64-bit totals.
+template <int B>
+__device__ __forceinline__ void acc_flush(uint32_t a, uint32_t c, uint64_t s64, uint64_t& cnt, uint64_t& sum)
+{
+    constexpr int kMode = B <= 21 ? 0 : (B <= 27 ? 1 : 2);
+    if constexpr (kMode == 0) {
+        constexpr int kSB = (B + 5) & 31;
+        cnt += a >> kSB;
+        sum += a & ((1u << kSB) - 1u);
+    } else if constexpr (kMode == 1) {
+        cnt += c;
+        sum += a;
+    } else {
+        cnt += c;
+        sum += s64;
+    }
+}
+
+// Row-major block: lane l takes values j = l + 32m (m = 0..31), whose bits
+// start at l*B + 32*B*m: the word offset grows by B per m (an immediate) and
+// the shift (l*B) mod 32 is fixed per lane -- a variable-shift extractor, one
+// funnel shift over a two-word window per value.  The high word of the
+// block's last value lies one word past the block; it is read from shared
+// memory (the slot's neighbour) and contributes no bits.
+template <int B, bool BRANCHY>
+__device__ __forceinline__ void agg_block_row(const uint32_t* words, int lane, const Lanes& L, uint64_t& cnt,
+                                              uint64_t& sum)
+{
+    const uint32_t bit0 = static_cast<uint32_t>(lane) * B;
+    const uint32_t* w = words + (bit0 >> 5);
+    const uint32_t sh = bit0 & 31u;
+    uint32_t a = 0u, c = 0u;
+    uint64_t s64 = 0u;
+#pragma unroll
+    for (int m = 0; m < 32; ++m) {
+        uint32_t ui;
+        if constexpr (B == 32) {
+            ui = w[32 * m];
+        } else {
+            const uint32_t x = __funnelshift_r(w[B * m], w[B * m + 1], sh);
+            asm("lop3.b32 %0, %1, %2, %3, 0xEA;" : "=r"(ui) : "r"(x), "r"(L.mask), "r"(L.add));  // (x & mask) | add
+        }
+        acc_one<B, BRANCHY>(ui, L, a, c, s64);
+    }
+    acc_flush<B>(a, c, s64, cnt, sum);
+}
+
+// Byte-aligned block (B = 8 or 16): lane l reads the 16-byte chunks l and
+// l + 32 (B = 8) or l + 32h, h < 4 (B = 16); one byte permute per value
+// takes the code and ORs in the packed-count bit of L.add at once.
+template <int B, bool BRANCHY>
+__device__ __forceinline__ void agg_block_bytes(const unsigned char* blk, int lane, const Lanes& L,
+                                                uint64_t& cnt, uint64_t& sum)
+{
+    static_assert(B == 8 || B == 16, "byte-aligned widths are 8 and 16 (32 is the lane layout)");
+    const uint4* q4 = reinterpret_cast<const uint4*>(blk);
+    uint32_t a = 0u, c = 0u;
+    uint64_t s64 = 0u;
+#pragma unroll
+    for (int h = 0; h < B / 4; ++h) {
+        const uint4 q = q4[lane + 32 * h];
+        const uint32_t x[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+#pragma unroll
+            for (int k = 0; k < 32 / B; ++k) {
+                // B = 8 : bytes (x.k, add.1, add.0, add.0); add = 1 << 13 -> its byte 1 is 0x20
+                // B = 16: bytes (x.2k, x.2k+1, add.2, add.0); add = 1 << 21 -> its byte 2 is 0x20
+                constexpr unsigned kSel8 = 0x4450u;
+                constexpr unsigned kSel16 = 0x4600u;
+                const unsigned sel = B == 8 ? kSel8 + static_cast<unsigned>(k)
+                                            : kSel16 + static_cast<unsigned>(2 * k) +
+                                                  (static_cast<unsigned>(2 * k + 1) << 4);
+                const uint32_t ui = __byte_perm(x[e], L.add, sel);
+                acc_one<B, BRANCHY>(ui, L, a, c, s64);
+            }
+        }
+    }
+    acc_flush<B>(a, c, s64, cnt, sum);
+}
+
+// All `nb` blocks of a staged tile in a non-lane layout.
+template <int B, bool BRANCHY, int LAY>
+__device__ __forceinline__ void scan_tile_layout(const unsigned char* tile, uint32_t nb, int lane, const Lanes& L,
+                                                 uint64_t& cnt, uint64_t& sum)
+{
+    constexpr uint32_t kBB = 128u * B;
+#pragma unroll 1
+    for (uint32_t g = 0; g < nb; ++g) {
+        if constexpr (LAY == kLayRow) {
+            agg_block_row<B, BRANCHY>(reinterpret_cast<const uint32_t*>(tile + g * kBB), lane, L, cnt, sum);
+        } else if constexpr (LAY == kLayBytes && (B == 8 || B == 16)) {
+            agg_block_bytes<B, BRANCHY>(tile + g * kBB, lane, L, cnt, sum);
+        }
+    }
+}
+
+// Tail block (n mod 1024 values) of a non-lane layout, from global memory.
+template <int B, int LAY>
+__device__ __forceinline__ void scan_tail_layout(const ScanParams& p, int lane, uint64_t& cnt, uint64_t& sum)
+{
+    const uint32_t* blk = p.packed + (p.n >> 10) * 32u * B;
+    const uint32_t rem = static_cast<uint32_t>(p.n & 1023u);
+    uint32_t c = 0u;
+    uint64_t s = 0u;
+    for (uint32_t j = static_cast<uint32_t>(lane); j < rem; j += 32u) {
+        uint32_t u;
+        if constexpr (LAY == kLayBytes && B == 8) {
+            u = reinterpret_cast<const uint8_t*>(blk)[j];
+        } else if constexpr (LAY == kLayBytes && B == 16) {
+            u = reinterpret_cast<const uint16_t*>(blk)[j];
+        } else if constexpr (B == 32) {
+            u = blk[j];
+        } else {
+            const uint32_t bit = j * B;
+            const uint32_t w = bit >> 5, sh = bit & 31u;
+            const uint32_t hi = sh + B > 32u ? blk[w + 1] : 0u;  // within the block when the value straddles
+            u = __funnelshift_r(blk[w], hi, sh) & ((1u << B) - 1u);
+        }
+        if ((u - p.lo) <= p.wm1) {
+            c += 1u;
+            s += u;
+        }
+    }
+    cnt += c;
+    sum += s;
+}
+
 // All `nb` blocks of a staged tile (blocks are contiguous in the slot).
 template <int B, bool BRANCHY>
 __device__ __forceinline__ void scan_tile(const unsigned char* tile, uint32_t nb, int lane,
@@ -498,7 +664,7 @@ __device__ __forceinline__ void scan_tail(const ScanParams& p, int lane, uint64_
 }
 
 // ------------------------------------------------------------- full scan
-template <int B, bool BRANCHY>
+template <int B, bool BRANCHY, int LAY = kLayLanes>
 __global__ void __launch_bounds__(Shape<B>::kWarps * 32, 1) k_scan_full(const ScanParams p)
 {
     using S = Shape<B>;
@@ -548,7 +714,10 @@ __global__ void __launch_bounds__(Shape<B>::kWarps * 32, 1) k_scan_full(const Sc
         }
         const uint64_t left = full_blocks - t * S::kTB;
         const uint32_t nb = left < S::kTB ? static_cast<uint32_t>(left) : S::kTB;
-        scan_tile<B, BRANCHY>(slots + s * S::kTileBytes, nb, lane, L, p.lo, p.wm1, cnt, sum);
+        if constexpr (LAY == kLayLanes)
+            scan_tile<B, BRANCHY>(slots + s * S::kTileBytes, nb, lane, L, p.lo, p.wm1, cnt, sum);
+        else
+            scan_tile_layout<B, BRANCHY, LAY>(slots + s * S::kTileBytes, nb, lane, L, cnt, sum);
         __syncwarp();
         const uint64_t tn = t + static_cast<uint64_t>(S::kStages) * GW;
         if (lane == 0 && tn < ntiles) {
@@ -566,7 +735,12 @@ __global__ void __launch_bounds__(Shape<B>::kWarps * 32, 1) k_scan_full(const Sc
             mbar_wait(&bars[jt % S::kStages], (jt / S::kStages) & 1u, kDrainLimitNs);
         }
     }
-    if ((p.n & 1023u) && gw == GW - 1) scan_tail<B>(p, lane, cnt, sum);
+    if ((p.n & 1023u) && gw == GW - 1) {
+        if constexpr (LAY == kLayLanes)
+            scan_tail<B>(p, lane, cnt, sum);
+        else
+            scan_tail_layout<B, LAY>(p, lane, cnt, sum);
+    }
     grid_finish<S::kWarps>(p, cnt, sum, false, (p.n + 1023u) >> 10);
 }
 
@@ -779,6 +953,10 @@ enum OpKind : int {
     kOpQueueBF = 2,
     kOpQueueBR = 3,
     kOpZoneBuild = 4,
+    kOpRowBF = 5,     // row-major layout (§3 strategy i)
+    kOpRowBR = 6,
+    kOpBytesBF = 7,   // byte-aligned layout, b = 8 or 16 (§3 strategy iii)
+    kOpBytesBR = 8,
 };
 
 struct ShapeInfo {

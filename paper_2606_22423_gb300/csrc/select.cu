@@ -106,7 +106,8 @@ scan_status enqueue_select(scan_column* col, scan_pred pred, scan_strategy strat
     const uint2* zm = nullptr;
     uint64_t n = 0;
     uint32_t b = 0, base = 0;
-    gb_column_view(col, &packed, &n, &b, &base, &zm);
+    if (!gb_column_view(col, &packed, &n, &b, &base, &zm))
+        return sfail(SCAN_EINVAL, "the select takes lane-interleaved columns");
     // [lo, hi) on decoded values -> code space, clipped to the column's domain
     const int64_t lo_v = static_cast<int64_t>(base);
     const int64_t hi_v = static_cast<int64_t>(base) + (1ll << b);

@@ -308,7 +308,7 @@ scan_status scan_server_create(scan_column* const* cols, uint32_t ncols, uint32_
         uint32_t b = 0, base;
         if (!cols[i] || !gb_column_view(cols[i], &pk, &n, &b, &base, &zm)) {
             delete sv;
-            return sfail(SCAN_EINVAL, "a table column is NULL");
+            return sfail(SCAN_EINVAL, "a table column is NULL or not lane-interleaved");
         }
         sv->width.push_back(b);
     }

@@ -16,6 +16,8 @@ LIB_PATH = os.path.join(HERE, "libgbscan.so")
 
 SCAN_OK, SCAN_EINVAL, SCAN_ENOMEM, SCAN_ECUDA, SCAN_ETIMEOUT, SCAN_EBUSY, SCAN_ENOTSUP = range(7)
 SCAN_AUTO, SCAN_BRANCHFREE, SCAN_BRANCHY, SCAN_ZONE_SKIP_BF, SCAN_ZONE_SKIP_BR = range(5)
+SCAN_LAYOUT_LANES, SCAN_LAYOUT_ROWMAJOR, SCAN_LAYOUT_BYTES = range(3)
+LAYOUTS = {"lanes": SCAN_LAYOUT_LANES, "rowmajor": SCAN_LAYOUT_ROWMAJOR, "bytes": SCAN_LAYOUT_BYTES}
 STRATEGIES = {
     "auto": SCAN_AUTO,
     "branchfree": SCAN_BRANCHFREE,
@@ -67,6 +69,12 @@ SIGNATURES = {
     "scan_run": (_st, [_vp, scan_pred, _st, _vp, ctypes.POINTER(scan_result)]),
     "scan_run_async": (_st, [_vp, scan_pred, _st, _vp, _vp]),
     "scan_column_status": (_st, [_vp, _vp]),
+    "scan_encode_host_layout": (_st, [_vp, _u64, _u32, _u32, ctypes.c_int, _vp]),
+    "scan_encode_device_layout": (_st, [_vp, _u64, _u32, _u32, ctypes.c_int, _vp, _vp]),
+    "scan_column_create_layout": (_st, [_vp, _u64, _u32, _u32, ctypes.c_int, _vp, ctypes.POINTER(_vp)]),
+    "scan_column_create_device_layout": (_st, [_vp, _u64, _u32, _u32, ctypes.c_int, _vp, ctypes.POINTER(_vp)]),
+    "scan_column_create_packed_layout": (_st, [_vp, _u64, _u32, _u32, ctypes.c_int, _vp, ctypes.POINTER(_vp)]),
+    "scan_column_get_layout": (_st, [_vp, ctypes.POINTER(ctypes.c_int)]),
     "scan_select": (_st, [_vp, scan_pred, _st, _vp, _u64, _vp, ctypes.POINTER(_u64)]),
     "scan_select_async": (_st, [_vp, scan_pred, _st, _vp, _u64, _vp, _vp]),
     "scan_probe_read": (_st, [_vp, _u64, _vp, _vp]),
@@ -154,7 +162,7 @@ def scan_packed_words(n: int, b: int) -> int:
     return int(load().scan_packed_words(n, b))
 
 
-def scan_encode_host(values, b: int, base: int = 0, out=None):
+def scan_encode_host(values, b: int, base: int = 0, out=None, layout="lanes"):
     """Encode a uint32 numpy array on the host; returns the packed uint32 array."""
     import numpy as np
 
@@ -162,7 +170,10 @@ def scan_encode_host(values, b: int, base: int = 0, out=None):
     words = scan_packed_words(v.size, b)
     if out is None:
         out = np.zeros(max(words, 1), dtype=np.uint32)
-    _check(load().scan_encode_host(_ptr(v), v.size, b, base, _ptr(out)))
+    if layout == "lanes":
+        _check(load().scan_encode_host(_ptr(v), v.size, b, base, _ptr(out)))
+    else:
+        _check(load().scan_encode_host_layout(_ptr(v), v.size, b, base, LAYOUTS[layout], _ptr(out)))
     return out[:words]
 
 
@@ -201,30 +212,33 @@ class Column:
                                        ctypes.byref(dp), ctypes.byref(dz)))
         self.n, self.b, self.base = int(n.value), int(b.value), int(base.value)
         self.dev_packed = dp.value or 0
+        lay = ctypes.c_int()
+        _check(load().scan_column_get_layout(self._h, ctypes.byref(lay)))
+        self.layout = {v: k for k, v in LAYOUTS.items()}[lay.value]
 
-    # constructors mirror scan_column_create{,_device,_packed}
+    # constructors mirror scan_column_create{,_device,_packed}{,_layout}
     @classmethod
-    def from_host(cls, values, b: int, base: int = 0, stream=None) -> "Column":
+    def from_host(cls, values, b: int, base: int = 0, stream=None, layout="lanes") -> "Column":
         import numpy as np
 
         v = np.ascontiguousarray(values, dtype=np.uint32)
         h = _vp()
-        _check(load().scan_column_create(_ptr(v) if v.size else None, v.size, b, base, _stream(stream),
-                                         ctypes.byref(h)))
+        _check(load().scan_column_create_layout(_ptr(v) if v.size else None, v.size, b, base, LAYOUTS[layout],
+                                                _stream(stream), ctypes.byref(h)))
         return cls(h.value)
 
     @classmethod
-    def from_device(cls, dev_values, n: int, b: int, base: int = 0, stream=None) -> "Column":
+    def from_device(cls, dev_values, n: int, b: int, base: int = 0, stream=None, layout="lanes") -> "Column":
         h = _vp()
-        _check(load().scan_column_create_device(_ptr(dev_values), n, b, base, _stream(stream),
-                                                ctypes.byref(h)))
+        _check(load().scan_column_create_device_layout(_ptr(dev_values), n, b, base, LAYOUTS[layout],
+                                                       _stream(stream), ctypes.byref(h)))
         return cls(h.value)
 
     @classmethod
-    def from_packed(cls, dev_packed, n: int, b: int, base: int = 0, stream=None) -> "Column":
+    def from_packed(cls, dev_packed, n: int, b: int, base: int = 0, stream=None, layout="lanes") -> "Column":
         h = _vp()
-        _check(load().scan_column_create_packed(_ptr(dev_packed), n, b, base, _stream(stream),
-                                                ctypes.byref(h)))
+        _check(load().scan_column_create_packed_layout(_ptr(dev_packed), n, b, base, LAYOUTS[layout],
+                                                       _stream(stream), ctypes.byref(h)))
         return cls(h.value, keepalive=dev_packed)
 
     @property

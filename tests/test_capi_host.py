@@ -58,6 +58,21 @@ def test_host_encoder_is_byte_identical_to_the_oracle(lib, b):
         np.testing.assert_array_equal(got, oracle.pack(v, b, base))
 
 
+@pytest.mark.parametrize("b", [1, 3, 8, 11, 16, 24, 31, 32])
+def test_host_rowmajor_and_byte_encoders_match_the_oracle(lib, b):
+    """Paper §3 strategies (i) and (iii): the host encoder writes the oracle's
+    row-major stream; the byte layout is that stream at b = 8/16/32."""
+    for n, base in [(1, 0), (1500, 0 if b == 32 else 3), (5 * 1024 + 7, 0)]:
+        v = synth.uniform_values(synth.seed_for(81, b, n), n, b, base)
+        got = gbscan.scan_encode_host(v, b, base, layout="rowmajor")
+        np.testing.assert_array_equal(got, oracle.pack_rowmajor(v, b, base))
+        if b in (8, 16, 32):
+            np.testing.assert_array_equal(gbscan.scan_encode_host(v, b, base, layout="bytes"),
+                                          oracle.pack_bytes(v, b, base))
+    with pytest.raises(gbscan.ScanError):
+        gbscan.scan_encode_host(np.arange(10, dtype=np.uint32), 12, 0, layout="bytes")
+
+
 def test_host_encoder_rejects_bad_input(lib):
     v = np.array([1, 2, 3, 400], dtype=np.uint32)
     for b, base, why in [(8, 0, "outside"), (0, 0, "width"), (33, 0, "width"), (9, 2, "outside"),
