@@ -31,6 +31,7 @@ OK = 0
 EINVAL = 1
 
 _u32p = np.ctypeslib.ndpointer(dtype=np.uint32, flags="C_CONTIGUOUS")
+_u64p = np.ctypeslib.ndpointer(dtype=np.uint64, flags="C_CONTIGUOUS")
 _i64 = ctypes.c_int64
 _u64 = ctypes.c_uint64
 _u32 = ctypes.c_uint32
@@ -73,6 +74,12 @@ def _load():
             lib.oracle_scan_zoneskip.argtypes = [
                 _u32p, _u32p, _u32p, _u64, _u32, _u32, _i64, _i64,
                 ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_u64)]
+            lib.oracle_blocksums.restype = ctypes.c_int
+            lib.oracle_blocksums.argtypes = [_u32p, _u64, _u32, _u32, _u64p]
+            lib.oracle_scan_zoneagg.restype = ctypes.c_int
+            lib.oracle_scan_zoneagg.argtypes = [
+                _u32p, _u32p, _u32p, _u64p, _u64, _u32, _u32, _i64, _i64, ctypes.POINTER(_i64),
+                ctypes.POINTER(_i64), ctypes.POINTER(_u64)]
             lib.oracle_pack_rowmajor.restype = ctypes.c_int
             lib.oracle_pack_rowmajor.argtypes = [_u32p, _u64, _u32, _u32, _u32p]
             lib.oracle_unpack_rowmajor.restype = ctypes.c_int
@@ -254,3 +261,29 @@ def scan_bytes(words, n: int, b: int, base: int, lo: int, hi: int):
                                  ctypes.byref(c), ctypes.byref(s)) != OK:
         raise ValueError("oracle_scan_bytes rejected the input")
     return c.value, s.value
+
+
+def blocksums(words, n: int, b: int, base: int = 0) -> np.ndarray:
+    """Per-block sum of decoded values over valid positions (uint64)."""
+    w = _u32arr(words)
+    nb = n_blocks(n)
+    out = np.zeros(max(nb, 1), np.uint64)
+    if _load().oracle_blocksums(w if w.size else np.zeros(1, np.uint32), n, b, base, out) != OK:
+        raise ValueError("oracle_blocksums rejected the input")
+    return out[:nb]
+
+
+def scan_zoneagg(words, zmin, zmax, sums, n: int, b: int, base: int, lo: int, hi: int):
+    """Scan answering blocks wholly inside [lo, hi) from (min, max, sum); returns
+    (count, sum, blocks_scanned)."""
+    w = _u32arr(words)
+    zmn, zmx = _u32arr(zmin), _u32arr(zmax)
+    sm = np.ascontiguousarray(sums, dtype=np.uint64)
+    c, s, t = _i64(), _i64(), _u64()
+    one, one64 = np.zeros(1, np.uint32), np.zeros(1, np.uint64)
+    rc = _load().oracle_scan_zoneagg(w if w.size else one, zmn if zmn.size else one, zmx if zmx.size else one,
+                                     sm if sm.size else one64, n, b, base, lo, hi,
+                                     ctypes.byref(c), ctypes.byref(s), ctypes.byref(t))
+    if rc != OK:
+        raise ValueError("oracle_scan_zoneagg rejected the input")
+    return c.value, s.value, t.value

@@ -205,6 +205,56 @@ int oracle_scan_zoneskip(const uint32_t *words, const uint32_t *zmin, const uint
 }
 
 /*
+ * Per-block aggregate metadata (an extension of the zone maps, not in the
+ * paper): the sum of the block's decoded values over its valid positions.
+ * With (min, max, sum) a block whose values all satisfy the predicate
+ * (lo <= min and max < hi) contributes (valid count, sum) without reading
+ * its data; a block outside it is skipped; only the remaining blocks are
+ * scanned.  The result equals the full scan exactly.
+ */
+int oracle_blocksums(const uint32_t *words, uint64_t n, uint32_t b, uint32_t base, uint64_t *sums)
+{
+    uint64_t k, i, nb = oracle_n_blocks(n);
+    if (!width_ok(b, base)) return ORACLE_EINVAL;
+    for (k = 0; k < nb; ++k) {
+        uint64_t first = k * BLOCK_VALUES;
+        uint64_t last = first + BLOCK_VALUES < n ? first + BLOCK_VALUES : n;
+        uint64_t acc = 0;
+        for (i = first; i < last; ++i) acc += (uint64_t)code_at(words, i, b) + base;
+        sums[k] = acc;
+    }
+    return ORACLE_OK;
+}
+
+int oracle_scan_zoneagg(const uint32_t *words, const uint32_t *zmin, const uint32_t *zmax, const uint64_t *sums,
+                        uint64_t n, uint32_t b, uint32_t base, int64_t lo, int64_t hi, int64_t *count,
+                        int64_t *sum, uint64_t *blocks_scanned)
+{
+    uint64_t k, nb = oracle_n_blocks(n), touched = 0;
+    int64_t c = 0, s = 0;
+    if (!width_ok(b, base)) return ORACLE_EINVAL;
+    for (k = 0; k < nb; ++k) {
+        uint64_t first = k * BLOCK_VALUES;
+        uint64_t last = first + BLOCK_VALUES < n ? first + BLOCK_VALUES : n;
+        int64_t bc, bs;
+        if ((int64_t)zmax[k] < lo || (int64_t)zmin[k] >= hi) continue;      /* no value can match */
+        if (lo <= (int64_t)zmin[k] && (int64_t)zmax[k] < hi) {                /* every value matches */
+            c += (int64_t)(last - first);
+            s += (int64_t)sums[k];
+            continue;
+        }
+        touched += 1;
+        scan_range(words, first, last, b, base, lo, hi, &bc, &bs);
+        c += bc;
+        s += bs;
+    }
+    *count = c;
+    *sum = s;
+    *blocks_scanned = touched;
+    return ORACLE_OK;
+}
+
+/*
  * Two further layouts of the same codes (paper §3 lists three decode
  * strategies; the transposed one above is strategy (ii)).
  *

@@ -376,3 +376,35 @@ def test_byte_layout_rejects_other_widths():
     with pytest.raises(ValueError):
         oracle.pack_bytes(np.arange(10, dtype=np.uint32), 12)
 
+
+# ----------------------------------------------- per-block aggregate metadata
+@pytest.mark.parametrize("b", [1, 9, 16, 32])
+def test_blocksums_match_numpy_block_reductions(b):
+    n = 5 * 1024 + 300
+    base = 0 if b == 32 else 7
+    v = synth.uniform_values(synth.seed_for(71, b), n, b, base)
+    w = oracle.pack(v, b, base)
+    pad = np.concatenate([v.astype(np.uint64), np.zeros(6 * 1024 - n, np.uint64)]).reshape(6, 1024)
+    np.testing.assert_array_equal(oracle.blocksums(w, n, b, base), pad.sum(axis=1))
+
+
+@pytest.mark.parametrize("p", [0.0, 0.01, 1.0])
+def test_zoneagg_is_exact_and_sorted_data_scans_at_most_two_blocks(p):
+    """Answering wholly-inside blocks from metadata never changes the result;
+    on sorted data only the (at most two) blocks holding a range end are scanned."""
+    n, b = 40 * 1024 + 77, 14
+    v = synth.clustered_values(synth.seed_for(72, int(p * 100)), n, b, p)
+    w = oracle.pack(v, b)
+    mn, mx = oracle.zonemap(w, n, b)
+    sm = oracle.blocksums(w, n, b)
+    for lo, hi in [(0, 1 << b), (100, 9000), (int(v[n // 3]), int(v[n // 3]) + 1), (5000, 5000), (16000, 1 << 20)]:
+        m = (v.astype(np.int64) >= lo) & (v.astype(np.int64) < hi)
+        c, s, t = oracle.scan_zoneagg(w, mn, mx, sm, n, b, 0, lo, hi)
+        assert (c, s) == (int(m.sum()), int(v[m].astype(np.int64).sum()))
+        # the scanned blocks are exactly those neither outside nor wholly inside
+        inside = (mn.astype(np.int64) >= lo) & (mx.astype(np.int64) < hi)
+        outside = (mx.astype(np.int64) < lo) | (mn.astype(np.int64) >= hi)
+        assert t == int(np.sum(~inside & ~outside))
+        if p == 0.0:
+            assert t <= 2
+

@@ -29,6 +29,10 @@ MUTANTS = {
                                                 "int oracle_unpack_rowmajor",
                                                 "    return (uint32_t)((window >> off) & ((1ull << b) - 1ull));\n}\n\n"
                                                 "int oracle_unpack_rowmajor")],
+    "wholly-inside test includes hi": [("if (lo <= (int64_t)zmin[k] && (int64_t)zmax[k] < hi) {",
+                                        "if (lo <= (int64_t)zmin[k] && (int64_t)zmax[k] <= hi) {")],
+    "inside tail block counted whole": [("            c += (int64_t)(last - first);\n            s += (int64_t)sums[k];",
+                                         "            c += (int64_t)BLOCK_VALUES;\n            s += (int64_t)sums[k];")],
     "select inclusive upper bound": [("(int64_t)base;\n        if (lo <= v && v < hi) {\n            if (k < capacity)",
                                       "(int64_t)base;\n        if (lo <= v && v <= hi) {\n            if (k < capacity)")],
     "select position off by one": [("if (k < capacity) pos[k] = (uint32_t)i;\n            k += 1;\n        }\n    }\n"
@@ -39,8 +43,8 @@ MUTANTS = {
                                         "    *count = k;",
                                         "if (k < capacity) { pos[k] = (uint32_t)i; k += 1; }\n        }\n    }\n"
                                         "    *count = k;")],
-    "zone skip off by one": [("if ((int64_t)zmax[k] < lo || (int64_t)zmin[k] >= hi) continue;",
-                              "if ((int64_t)zmax[k] <= lo || (int64_t)zmin[k] >= hi) continue;")],
+    "zone skip off by one": [("if ((int64_t)zmax[k] < lo || (int64_t)zmin[k] >= hi) continue;\n        touched += 1;",
+                              "if ((int64_t)zmax[k] <= lo || (int64_t)zmin[k] >= hi) continue;\n        touched += 1;")],
     "tail padding in zone map": [("        uint64_t last = first + BLOCK_VALUES < n ? first + BLOCK_VALUES : n;\n"
                                   "        uint32_t mn = 0xFFFFFFFFu, mx = 0;",
                                   "        uint64_t last = first + BLOCK_VALUES;\n"
@@ -73,6 +77,10 @@ class Lib:
         self.l.oracle_scan_zoneskip.argtypes = [u32p, u32p, u32p, u64, u32, u32, i64, i64, ctypes.POINTER(i64),
                                                 ctypes.POINTER(i64), ctypes.POINTER(u64)]
         self.l.oracle_select_packed.argtypes = [u32p, u64, u32, u32, i64, i64, u32p, u64, ctypes.POINTER(u64)]
+        u64p = np.ctypeslib.ndpointer(dtype=np.uint64, flags="C_CONTIGUOUS")
+        self.l.oracle_blocksums.argtypes = [u32p, u64, u32, u32, u64p]
+        self.l.oracle_scan_zoneagg.argtypes = [u32p, u32p, u32p, u64p, u64, u32, u32, i64, i64,
+                                               ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(u64)]
         self.l.oracle_pack_rowmajor.argtypes = [u32p, u64, u32, u32, u32p]
         self.l.oracle_scan_rowmajor.argtypes = [u32p, u64, u32, u32, i64, i64, ctypes.POINTER(i64),
                                                 ctypes.POINTER(i64)]
@@ -97,6 +105,14 @@ class Lib:
         mn, mx = np.zeros(nb, np.uint32), np.zeros(nb, np.uint32)
         self.l.oracle_zonemap(w, n, b, base, mn, mx)
         return mn, mx
+
+    def zoneagg(self, w, mn, mx, n, b, base, lo, hi):
+        sums = np.zeros((n + 1023) // 1024, np.uint64)
+        self.l.oracle_blocksums(w, n, b, base, sums)
+        c, s, t = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_uint64()
+        self.l.oracle_scan_zoneagg(w, mn, mx, sums, n, b, base, lo, hi, ctypes.byref(c), ctypes.byref(s),
+                                   ctypes.byref(t))
+        return c.value, s.value, t.value
 
     def pack_rowmajor(self, v, b, base=0):
         out = np.zeros(((v.size + 1023) // 1024) * 32 * b, np.uint32)
@@ -152,6 +168,16 @@ def pins(o):
         m = (v >= lo) & (v < hi)
         assert (c, s) == (int(m.sum()), int(v[m].astype(np.int64).sum()))
         assert t == int(np.sum(~((mx < lo) | (mn >= hi))))
+    # block aggregates: exact on sorted data with a wholly-inside run and a partial tail block
+    n, b = 6 * 1024 + 500, 12
+    v = synth.clustered_values(9, n, b, 0.0)
+    w = o.pack(v, b)
+    mn, mx = o.zonemap(w, n, b)
+    for lo, hi in [(0, 1 << b), (int(v[2000]), int(mx[-1]) + 1), (int(mn[2]), int(mx[4]) + 1),
+                   (int(mn[2]), int(mx[4]))]:
+        m = (v.astype(np.int64) >= lo) & (v.astype(np.int64) < hi)
+        c, s_, t = o.zoneagg(w, mn, mx, n, b, 0, lo, hi)
+        assert (c, s_) == (int(m.sum()), int(v[m].astype(np.int64).sum()))
     # row-major layout: bit-level stream and brute-force scans
     for b in (3, 13, 24):
         v = synth.uniform_values(synth.seed_for(78, b), 2100, b)
