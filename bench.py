@@ -514,8 +514,9 @@ def run_zone_sweep(args, dev, stream, gbscan):
 
     n, b = 1 << 30, 16
     out = {"workload": "zone sweep: N=2^30 at b=16, sorted then p in {0,0.01,0.1,1} displaced, "
-                       "sigma in {1e-4,1e-3,1e-2,0.1,0.5}", "rows": []}
-    res = torch.zeros((2, 4), dtype=torch.int64, device=dev)
+                       "sigma in {1e-4,1e-3,1e-2,0.1,0.5}; full scan, zone skip, and zone skip answering "
+                       "wholly-inside blocks from per-block (min, max, sum)", "rows": []}
+    res = torch.zeros((3, 4), dtype=torch.int64, device=dev)
     for pi, p in enumerate([0.0, 0.01, 0.1, 1.0]):
         with torch.cuda.stream(stream):
             v = synth.clustered_values_device(synth.seed_for(3, pi), n, b, p, device=dev)
@@ -527,7 +528,7 @@ def run_zone_sweep(args, dev, stream, gbscan):
         for si, sigma in enumerate([1e-4, 1e-3, 1e-2, 0.1, 0.5]):
             lo, hi = synth.pick_range(synth.seed_for(3, pi, si + 1), b, sigma)
             ts = {}
-            for k, strat in enumerate(["branchfree", "zone_bf"]):
+            for k, strat in enumerate(["branchfree", "zone_bf", "zone_agg_bf"]):
                 col.run_async(lo, hi, res[k], strat, stream)
                 vals = []
                 for _ in range(3):
@@ -544,7 +545,10 @@ def run_zone_sweep(args, dev, stream, gbscan):
                                 "ms_full": round(ts["branchfree"], 4), "ms_zone": round(ts["zone_bf"], 4),
                                 "speedup": round(ts["branchfree"] / ts["zone_bf"], 2),
                                 "blocks_read_fraction": round(int(r[1, 2]) / int(r[0, 2]), 6),
-                                "exact": bool((r[0, :2] == r[1, :2]).all())})
+                                "ms_zone_agg": round(ts["zone_agg_bf"], 4),
+                                "speedup_zone_agg": round(ts["branchfree"] / ts["zone_agg_bf"], 2),
+                                "blocks_read_fraction_zone_agg": round(int(r[2, 2]) / int(r[0, 2]), 6),
+                                "exact": bool((r[0, :2] == r[1, :2]).all() and (r[0, :2] == r[2, :2]).all())})
         col.close()
         torch.cuda.empty_cache()
     return out

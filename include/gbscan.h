@@ -64,7 +64,15 @@ typedef enum {
     SCAN_BRANCHFREE = 1,   /* full scan, predicated (mask) aggregation */
     SCAN_BRANCHY = 2,      /* full scan, warp-vote early-out per 32-value group */
     SCAN_ZONE_SKIP_BF = 3, /* zone-map block skipping + persistent queue, branch-free */
-    SCAN_ZONE_SKIP_BR = 4  /* zone-map block skipping + persistent queue, branchy */
+    SCAN_ZONE_SKIP_BR = 4, /* zone-map block skipping + persistent queue, branchy */
+    /* Zone skipping that also answers every block wholly inside [lo, hi)
+     * (lo <= min and max < hi) from its metadata -- its valid count and the
+     * per-block sum built by scan_zonemap_build -- without reading its data;
+     * only blocks that straddle a bound are scanned (an extension of the
+     * paper's zone maps; the result is the same).  Lane layout only; not
+     * taken by batches or the planner. */
+    SCAN_ZONE_AGG_BF = 5,
+    SCAN_ZONE_AGG_BR = 6
 } scan_strategy;
 
 typedef struct {
@@ -182,9 +190,14 @@ scan_status scan_column_info(const scan_column *col, uint64_t *n, uint32_t *b, u
 /* ------------------------------------------------------------ zone maps */
 
 /* Build the per-block (min, max) zone map (paper §3, "per-block zone maps
- * (min/max skipping)"; §6 clustering crossover).  Idempotent; one read of the
- * packed column, 8 bytes written per block. */
+ * (min/max skipping)"; §6 clustering crossover) and, in the same pass, the
+ * per-block sum of decoded values (uint64, over valid positions) that the
+ * SCAN_ZONE_AGG_* strategies use.  Idempotent; one read of the packed
+ * column, 16 bytes written per block.  Lane-interleaved columns only. */
 scan_status scan_zonemap_build(scan_column *col, void *stream);
+
+/* Device pointer to the per-block sums (NULL until scan_zonemap_build). */
+scan_status scan_column_blocksums(const scan_column *col, const uint64_t **dev_blocksums);
 
 /* ---------------------------------------------------------------- scans */
 

@@ -58,14 +58,14 @@ bool width_ok(uint32_t b, uint32_t base)
 uint64_t n_blocks(uint64_t n) { return (n + 1023u) >> 10; }
 
 // Device workspace of one column, one allocation:
-//   result[4] (32 B) | status (4 B) | done (4 B) | pad | qctl[4] | partials[2*kMaxGrid]
+//   result[4] (32 B) | status (4 B) | done (4 B) | pad | qctl[8] (64 B) | partials[2*kMaxGrid]
 struct Workspace {
     long long* result;
     unsigned int* status;
     unsigned int* done;
     unsigned long long* qctl;
     unsigned long long* partials;
-    static constexpr size_t kBytes = 64 + 32 + 16 * kMaxGrid;
+    static constexpr size_t kBytes = 128 + 16 * kMaxGrid;
 };
 
 struct DeviceInfo {
@@ -99,16 +99,26 @@ namespace gb {
 // misses [lo, hi) holds no match).  Each CTA compacts 2048 consecutive
 // blocks in order in shared memory and reserves its output range with one
 // atomic, so runs of consecutive candidates survive for merged copies.
+// With kFlagAgg a block whose [min, max] lies inside [lo, hi) matches
+// entirely: it is not kept, and its count and code sum (the metadata sum
+// minus base * 1024) go to qctl[3], qctl[4] with one atomic pair per CTA.
 __global__ void __launch_bounds__(kFilterThreads) k_zone_filter(const ScanParams p)
 {
     __shared__ uint32_t list[kFilterPerCta];
     __shared__ uint32_t wcnt[kFilterThreads / 32];
     __shared__ uint32_t total;
     __shared__ unsigned long long out_base;
+    __shared__ unsigned long long in_cnt, in_sum;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint64_t full_blocks = p.n >> 10;
     const uint64_t first = static_cast<uint64_t>(blockIdx.x) * kFilterPerCta;
-    if (threadIdx.x == 0) total = 0u;
+    const bool agg = (p.flags & kFlagAgg) != 0u;
+    unsigned long long my_cnt = 0, my_sum = 0;
+    if (threadIdx.x == 0) {
+        total = 0u;
+        in_cnt = 0ull;
+        in_sum = 0ull;
+    }
     __syncthreads();
     for (int pass = 0; pass < kFilterPerCta / kFilterThreads; ++pass) {
         const uint64_t k = first + pass * kFilterThreads + threadIdx.x;
@@ -116,6 +126,11 @@ __global__ void __launch_bounds__(kFilterThreads) k_zone_filter(const ScanParams
         if (k < full_blocks) {
             const uint2 z = p.zonemap[k];
             keep = static_cast<uint64_t>(z.y) >= p.zlo && static_cast<uint64_t>(z.x) < p.zhi;
+            if (agg && keep && static_cast<uint64_t>(z.x) >= p.zlo && static_cast<uint64_t>(z.y) < p.zhi) {
+                keep = false;
+                my_cnt += 1024ull;
+                my_sum += p.blocksum[k] - 1024ull * p.base;
+            }
         }
         const uint32_t bal = __ballot_sync(kFull, keep);
         if (lane == 0) wcnt[warp] = __popc(bal);
@@ -128,8 +143,23 @@ __global__ void __launch_bounds__(kFilterThreads) k_zone_filter(const ScanParams
             for (int w = 0; w < kFilterThreads / 32; ++w) total += wcnt[w];
         __syncthreads();
     }
+    if (agg) {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            my_cnt += __shfl_xor_sync(kFull, my_cnt, o);
+            my_sum += __shfl_xor_sync(kFull, my_sum, o);
+        }
+        if (lane == 0 && my_cnt) {
+            atomicAdd(&in_cnt, my_cnt);
+            atomicAdd(&in_sum, my_sum);
+        }
+    }
     if (threadIdx.x == 0 && total) out_base = atomicAdd(&p.qctl[0], static_cast<unsigned long long>(total));
     __syncthreads();
+    if (threadIdx.x == 0 && in_cnt) {
+        atomicAdd(&p.qctl[3], in_cnt);
+        atomicAdd(&p.qctl[4], in_sum);
+    }
     for (uint32_t i = threadIdx.x; i < total; i += kFilterThreads) p.cand[out_base + i] = list[i];
 }
 
@@ -143,6 +173,7 @@ struct scan_column {
     uint32_t* packed = nullptr;
     bool owns_packed = false;
     uint2* zonemap = nullptr;
+    unsigned long long* blocksum = nullptr;  // per-block sums, built with the zone map
     bool zonemap_valid = false;
     unsigned int* cand = nullptr;
     void* ws_raw = nullptr;
@@ -386,7 +417,7 @@ scan_status new_column(uint64_t n, uint32_t b, uint32_t base, scan_column** out)
     c->ws.status = reinterpret_cast<unsigned int*>(base_ptr + 32);
     c->ws.done = reinterpret_cast<unsigned int*>(base_ptr + 36);
     c->ws.qctl = reinterpret_cast<unsigned long long*>(base_ptr + 64);
-    c->ws.partials = reinterpret_cast<unsigned long long*>(base_ptr + 96);
+    c->ws.partials = reinterpret_cast<unsigned long long*>(base_ptr + 128);
     *out = c;
     return SCAN_OK;
 }
@@ -398,6 +429,7 @@ gb::ScanParams base_params(const scan_column* c)
     p.n = c->n;
     p.base = c->base;
     p.zonemap = c->zonemap;
+    p.blocksum = c->blocksum;
     p.partials = c->ws.partials;
     p.done = c->ws.done;
     p.status = c->ws.status;
@@ -446,6 +478,14 @@ scan_status enqueue_scan(scan_column* c, scan_pred pred, scan_strategy strategy,
     case SCAN_BRANCHY: op = gb::kOpFullBR; break;
     case SCAN_ZONE_SKIP_BF: op = gb::kOpQueueBF; break;
     case SCAN_ZONE_SKIP_BR: op = gb::kOpQueueBR; break;
+    case SCAN_ZONE_AGG_BF:
+        op = gb::kOpQueueBF;
+        p.flags |= gb::kFlagAgg;
+        break;
+    case SCAN_ZONE_AGG_BR:
+        op = gb::kOpQueueBR;
+        p.flags |= gb::kFlagAgg;
+        break;
     default: return fail(SCAN_EINVAL, "unknown strategy %d", static_cast<int>(strategy));
     }
     // at b = 32 every layout is the plain array, which the lane kernels read
@@ -684,6 +724,14 @@ scan_status scan_column_create_packed_layout(const uint32_t* dev_packed, uint64_
     return SCAN_OK;
 }
 
+scan_status scan_column_blocksums(const scan_column* col, const uint64_t** dev_blocksums)
+{
+    g_err.clear();
+    if (!col || !dev_blocksums) return fail(SCAN_EINVAL, "null pointer");
+    *dev_blocksums = col->zonemap_valid ? reinterpret_cast<const uint64_t*>(col->blocksum) : nullptr;
+    return SCAN_OK;
+}
+
 scan_status scan_column_get_layout(const scan_column* col, scan_layout* layout)
 {
     g_err.clear();
@@ -711,6 +759,7 @@ scan_status scan_column_destroy(scan_column* col)
     cudaDeviceSynchronize();
     if (col->owns_packed && col->packed) cudaFree(col->packed);
     if (col->zonemap) cudaFree(col->zonemap);
+    if (col->blocksum) cudaFree(col->blocksum);
     if (col->cand) cudaFree(col->cand);
     if (col->ws_raw) cudaFree(col->ws_raw);
     if (col->host_result) cudaFreeHost(col->host_result);
@@ -742,11 +791,13 @@ scan_status scan_zonemap_build(scan_column* col, void* stream)
     const uint64_t nb = n_blocks(col->n);
     if (!col->zonemap) {
         GB_CUDA(cudaMalloc(&col->zonemap, std::max<uint64_t>(nb, 1) * sizeof(uint2)));
+        GB_CUDA(cudaMalloc(&col->blocksum, std::max<uint64_t>(nb, 1) * sizeof(unsigned long long)));
         GB_CUDA(cudaMalloc(&col->cand, std::max<uint64_t>(nb, 1) * sizeof(unsigned int)));
     }
     if (nb) {
         gb::ScanParams p = base_params(col);
         p.zonemap_out = col->zonemap;
+        p.blocksum = col->blocksum;
         const cudaError_t e = launch(static_cast<int>(col->b), gb::kOpZoneBuild, p, persistent_grid(),
                                      as_stream(stream));
         if (e != cudaSuccess) return cuda_fail(e, "zone-map build launch");

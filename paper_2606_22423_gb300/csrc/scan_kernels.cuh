@@ -25,6 +25,7 @@
 namespace gb {
 
 enum : uint32_t { kErrTimeout = 1u, kErrRange = 2u };
+enum : uint32_t { kFlagAgg = 1u };
 
 struct ScanParams {
     const uint32_t* packed;       // lane-interleaved words, 16-byte aligned
@@ -32,15 +33,17 @@ struct ScanParams {
     uint32_t base;                // frame-of-reference base
     uint32_t lo;                  // predicate lower bound in code space
     uint32_t wm1;                 // predicate width minus one (width >= 1)
-    uint32_t pad0;
+    uint32_t flags;               // kFlagAgg: answer wholly-inside blocks from their metadata
     uint64_t zlo, zhi;            // predicate [zlo, zhi) on decoded values, for zone tests
     const uint2* zonemap;         // (min, max) of decoded values per block
     uint2* zonemap_out;           // zone-map build output
+    unsigned long long* blocksum; // sum of decoded values per block (written by the build)
     unsigned long long* partials; // 2 words per CTA
     unsigned int* done;           // grid-finish ticket, reset by the last CTA
     unsigned int* status;         // error bits (kErr*)
     unsigned int* cand;           // zone-skip candidate block ids
-    unsigned long long* qctl;     // [0] candidates, [1] queue head, [2] tail kept
+    unsigned long long* qctl;     // [0] candidates, [1] queue head, [2] tail kept,
+                                  // [3] count and [4] code sum of wholly-inside blocks
     long long* result;            // count, sum, blocks_scanned, reserved
 };
 
@@ -361,10 +364,10 @@ __device__ __forceinline__ void agg_block_masked(const typename Geo<B>::Vec* row
     sum += s;
 }
 
-// (min, max) of codes of one block over valid positions.
+// (min, max) and sum of the codes of one block over valid positions.
 template <int B>
 __device__ __forceinline__ void minmax_block(const typename Geo<B>::Vec* rows, uint32_t limit, int q,
-                                             uint32_t& mn, uint32_t& mx)
+                                             uint32_t& mn, uint32_t& mx, uint64_t& sm)
 {
     constexpr int kLpt = Geo<B>::kLpt;
     typename Geo<B>::Vec W[B];
@@ -378,6 +381,7 @@ __device__ __forceinline__ void minmax_block(const typename Geo<B>::Vec* rows, u
             if (j < limit) {
                 mn = min(mn, u);
                 mx = max(mx, u);
+                sm += u;
             }
         }
     }
@@ -637,9 +641,13 @@ __device__ __forceinline__ void grid_finish(const ScanParams& p, uint64_t cnt, u
         unsigned long long blocks = full_blocks_scanned;
         if (queue_mode) {
             blocks = __ldcg(&p.qctl[0]) + __ldcg(&p.qctl[2]);
+            tc += __ldcg(&p.qctl[3]);  // wholly-inside blocks answered from metadata
+            ts += __ldcg(&p.qctl[4]);
             p.qctl[0] = 0ull;
             p.qctl[1] = 0ull;
             p.qctl[2] = 0ull;
+            p.qctl[3] = 0ull;
+            p.qctl[4] = 0ull;
         }
         p.result[0] = static_cast<long long>(tc);
         p.result[1] = static_cast<long long>(ts + static_cast<unsigned long long>(p.base) * tc);
@@ -780,13 +788,17 @@ __global__ void __launch_bounds__(Shape<B>::kWarps * 32, 1) k_zonemap_build(cons
             if (t < ntiles) issue(t, s);
         }
     }
-    auto emit = [&](uint64_t blk, bool ok, uint32_t mn, uint32_t mx) {
+    auto emit = [&](uint64_t blk, bool ok, uint32_t mn, uint32_t mx, uint64_t sm, uint32_t valid) {
 #pragma unroll
         for (int o = 1; o < Geo<B>::kTpb; o <<= 1) {
             mn = min(mn, __shfl_xor_sync(kFull, mn, o));
             mx = max(mx, __shfl_xor_sync(kFull, mx, o));
+            sm += __shfl_xor_sync(kFull, sm, o);
         }
-        if (ok && q == 0) p.zonemap_out[blk] = make_uint2(mn + p.base, mx + p.base);
+        if (ok && q == 0) {
+            p.zonemap_out[blk] = make_uint2(mn + p.base, mx + p.base);
+            p.blocksum[blk] = sm + static_cast<unsigned long long>(p.base) * valid;
+        }
     };
     uint32_t it = 0;
     bool failed = false;
@@ -807,8 +819,9 @@ __global__ void __launch_bounds__(Shape<B>::kWarps * 32, 1) k_zonemap_build(cons
         for (uint32_t g = 0; g < nb; g += static_cast<uint32_t>(Geo<B>::kLpt)) {
             const bool ok = g + sub < nb;
             uint32_t mn = 0xffffffffu, mx = 0u;
-            minmax_block<B>(block_rows<B>(tile + (ok ? g + sub : g) * (128u * B), q), 1024u, q, mn, mx);
-            emit(fb + g + sub, ok, mn, mx);
+            uint64_t sm = 0u;
+            minmax_block<B>(block_rows<B>(tile + (ok ? g + sub : g) * (128u * B), q), 1024u, q, mn, mx, sm);
+            emit(fb + g + sub, ok, mn, mx, sm, 1024u);
         }
         __syncwarp();
         const uint64_t tn = t + static_cast<uint64_t>(S::kStages) * GW;
@@ -831,8 +844,9 @@ __global__ void __launch_bounds__(Shape<B>::kWarps * 32, 1) k_zonemap_build(cons
         const auto* rows =
             block_rows<B>(reinterpret_cast<const unsigned char*>(p.packed + full_blocks * 32u * B), q);
         uint32_t mn = 0xffffffffu, mx = 0u;
-        minmax_block<B>(rows, sub == 0 ? rem : 0u, q, mn, mx);
-        emit(full_blocks, sub == 0, mn, mx);
+        uint64_t sm = 0u;
+        minmax_block<B>(rows, sub == 0 ? rem : 0u, q, mn, mx, sm);
+        emit(full_blocks, sub == 0, mn, mx, sm, rem);
     }
 }
 
@@ -939,8 +953,17 @@ __global__ void __launch_bounds__(Shape<B>::kWarps * 32, 1) k_scan_queue(const S
     if ((p.n & 1023u) && blockIdx.x == 0 && warp == 0) {
         const uint2 z = p.zonemap[p.n >> 10];
         if (static_cast<uint64_t>(z.y) >= p.zlo && static_cast<uint64_t>(z.x) < p.zhi) {
-            scan_tail<B>(p, lane, cnt, sum);
-            if (lane == 0) p.qctl[2] = 1ull;
+            if ((p.flags & kFlagAgg) && static_cast<uint64_t>(z.x) >= p.zlo && static_cast<uint64_t>(z.y) < p.zhi) {
+                // every value of the tail matches: count and (code) sum from the metadata
+                if (lane == 0) {
+                    const uint64_t rem = p.n & 1023u;
+                    cnt += rem;
+                    sum += p.blocksum[p.n >> 10] - static_cast<uint64_t>(p.base) * rem;
+                }
+            } else {
+                scan_tail<B>(p, lane, cnt, sum);
+                if (lane == 0) p.qctl[2] = 1ull;
+            }
         }
     }
     grid_finish<S::kWarps>(p, cnt, sum, true, 0);

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libgbscan.so")
 
 SCAN_OK, SCAN_EINVAL, SCAN_ENOMEM, SCAN_ECUDA, SCAN_ETIMEOUT, SCAN_EBUSY, SCAN_ENOTSUP = range(7)
-SCAN_AUTO, SCAN_BRANCHFREE, SCAN_BRANCHY, SCAN_ZONE_SKIP_BF, SCAN_ZONE_SKIP_BR = range(5)
+SCAN_AUTO, SCAN_BRANCHFREE, SCAN_BRANCHY, SCAN_ZONE_SKIP_BF, SCAN_ZONE_SKIP_BR, SCAN_ZONE_AGG_BF, SCAN_ZONE_AGG_BR = range(7)
 SCAN_LAYOUT_LANES, SCAN_LAYOUT_ROWMAJOR, SCAN_LAYOUT_BYTES = range(3)
 LAYOUTS = {"lanes": SCAN_LAYOUT_LANES, "rowmajor": SCAN_LAYOUT_ROWMAJOR, "bytes": SCAN_LAYOUT_BYTES}
 STRATEGIES = {
@@ -24,6 +24,8 @@ STRATEGIES = {
     "branchy": SCAN_BRANCHY,
     "zone_bf": SCAN_ZONE_SKIP_BF,
     "zone_br": SCAN_ZONE_SKIP_BR,
+    "zone_agg_bf": SCAN_ZONE_AGG_BF,
+    "zone_agg_br": SCAN_ZONE_AGG_BR,
 }
 
 
@@ -75,6 +77,7 @@ SIGNATURES = {
     "scan_column_create_device_layout": (_st, [_vp, _u64, _u32, _u32, ctypes.c_int, _vp, ctypes.POINTER(_vp)]),
     "scan_column_create_packed_layout": (_st, [_vp, _u64, _u32, _u32, ctypes.c_int, _vp, ctypes.POINTER(_vp)]),
     "scan_column_get_layout": (_st, [_vp, ctypes.POINTER(ctypes.c_int)]),
+    "scan_column_blocksums": (_st, [_vp, ctypes.POINTER(_vp)]),
     "scan_select": (_st, [_vp, scan_pred, _st, _vp, _u64, _vp, ctypes.POINTER(_u64)]),
     "scan_select_async": (_st, [_vp, scan_pred, _st, _vp, _u64, _vp, _vp]),
     "scan_probe_read": (_st, [_vp, _u64, _vp, _vp]),
@@ -285,6 +288,13 @@ class Column:
         cap = (0 if positions is None else positions.numel()) if capacity is None else int(capacity)
         _check(load().scan_select_async(self._h, scan_pred(lo, hi), st, _ptr(positions), cap, _stream(stream),
                                         _ptr(dev_count)))
+
+    @property
+    def dev_blocksums(self) -> int:
+        """Device address of the per-block sums (0 before zonemap_build)."""
+        p = _vp()
+        _check(load().scan_column_blocksums(self._h, ctypes.byref(p)))
+        return p.value or 0
 
     def status(self, stream=None):
         _check(load().scan_column_status(self._h, _stream(stream)))
