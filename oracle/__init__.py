@@ -74,6 +74,10 @@ def _load():
             lib.oracle_scan_zoneskip.argtypes = [
                 _u32p, _u32p, _u32p, _u64, _u32, _u32, _i64, _i64,
                 ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_u64)]
+            lib.oracle_scan_conj.restype = ctypes.c_int
+            lib.oracle_scan_conj.argtypes = [
+                ctypes.POINTER(ctypes.c_void_p), _u32p, _u32p, ctypes.POINTER(_i64), ctypes.POINTER(_i64), _u32,
+                _u64, ctypes.c_void_p, _u32, _u32, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]
             lib.oracle_blocksums.restype = ctypes.c_int
             lib.oracle_blocksums.argtypes = [_u32p, _u64, _u32, _u32, _u64p]
             lib.oracle_scan_zoneagg.restype = ctypes.c_int
@@ -287,3 +291,22 @@ def scan_zoneagg(words, zmin, zmax, sums, n: int, b: int, base: int, lo: int, hi
     if rc != OK:
         raise ValueError("oracle_scan_zoneagg rejected the input")
     return c.value, s.value, t.value
+
+
+def scan_conj(columns, n: int, agg=None):
+    """Conjunctive scan: columns = [(words, b, base, lo, hi), ...] of n rows each;
+    agg = (words, b, base) or None.  Returns (count, sum of agg over matching rows)."""
+    k = len(columns)
+    ws = [_u32arr(c[0]) for c in columns]
+    ptrs = (ctypes.c_void_p * max(k, 1))(*[w.ctypes.data for w in ws])
+    bs = np.array([c[1] for c in columns] or [1], np.uint32)
+    bases = np.array([c[2] for c in columns] or [0], np.uint32)
+    los = (_i64 * max(k, 1))(*[c[3] for c in columns])
+    his = (_i64 * max(k, 1))(*[c[4] for c in columns])
+    aw = _u32arr(agg[0]) if agg is not None else None
+    cnt, sm = _i64(), _i64()
+    rc = _load().oracle_scan_conj(ptrs, bs, bases, los, his, k, n, aw.ctypes.data if aw is not None else None,
+                                  agg[1] if agg else 0, agg[2] if agg else 0, ctypes.byref(cnt), ctypes.byref(sm))
+    if rc != OK:
+        raise ValueError("oracle_scan_conj rejected the input")
+    return cnt.value, sm.value

@@ -205,6 +205,38 @@ int oracle_scan_zoneskip(const uint32_t *words, const uint32_t *zmin, const uint
 }
 
 /*
+ * Conjunctive predicate over k columns of one table (the problem statement
+ * of paper §2 extended to several columns of equal length; rows are shared
+ * positions): COUNT = #{ i : lo_c <= v_c,i < hi_c for every c }, and SUM =
+ * the sum of the aggregate column's values over those rows (exact int64;
+ * 0 when agg_words is NULL).  All columns in the transposed layout.
+ */
+int oracle_scan_conj(const uint32_t *const *words, const uint32_t *b, const uint32_t *base, const int64_t *lo,
+                     const int64_t *hi, uint32_t k, uint64_t n, const uint32_t *agg_words, uint32_t agg_b,
+                     uint32_t agg_base, int64_t *count, int64_t *sum)
+{
+    uint64_t i;
+    uint32_t c;
+    int64_t cnt = 0, sm = 0;
+    for (c = 0; c < k; ++c)
+        if (!width_ok(b[c], base[c])) return ORACLE_EINVAL;
+    if (agg_words && !width_ok(agg_b, agg_base)) return ORACLE_EINVAL;
+    for (i = 0; i < n; ++i) {
+        int all = 1;
+        for (c = 0; c < k && all; ++c) {
+            int64_t v = (int64_t)code_at(words[c], i, b[c]) + (int64_t)base[c];
+            all = lo[c] <= v && v < hi[c];
+        }
+        if (!all) continue;
+        cnt += 1;
+        if (agg_words) sm += (int64_t)code_at(agg_words, i, agg_b) + (int64_t)agg_base;
+    }
+    *count = cnt;
+    *sum = sm;
+    return ORACLE_OK;
+}
+
+/*
  * Per-block aggregate metadata (an extension of the zone maps, not in the
  * paper): the sum of the block's decoded values over its valid positions.
  * With (min, max, sum) a block whose values all satisfy the predicate

@@ -408,3 +408,28 @@ def test_zoneagg_is_exact_and_sorted_data_scans_at_most_two_blocks(p):
         if p == 0.0:
             assert t <= 2
 
+
+# ------------------------------------------------ conjunctive predicates
+def test_conjunction_matches_numpy_masks():
+    """COUNT of rows meeting every predicate and SUM of the aggregate column over
+    them, fixed by numpy boolean masks over the raw values."""
+    n = 9 * 1024 + 77
+    specs = [(5, 0), (12, 300), (23, 7), (32, 0)]
+    vals, cols = [], []
+    for i, (b, base) in enumerate(specs):
+        v = synth.uniform_values(synth.seed_for(73, i), n, b, base)
+        vals.append(v)
+        lo, hi = synth.pick_range(synth.seed_for(74, i), b, 0.6, base)
+        cols.append((oracle.pack(v, b, base), b, base, lo, hi))
+    agg_v = synth.uniform_values(75, n, 20, 9)
+    agg = (oracle.pack(agg_v, 20, 9), 20, 9)
+    for k in (1, 2, 4):
+        m = np.ones(n, bool)
+        for v, (_, b, base, lo, hi) in zip(vals[:k], cols[:k]):
+            m &= (v.astype(np.int64) >= lo) & (v.astype(np.int64) < hi)
+        assert oracle.scan_conj(cols[:k], n, agg) == (int(m.sum()), int(agg_v[m].astype(np.int64).sum()))
+        assert oracle.scan_conj(cols[:k], n, None) == (int(m.sum()), 0)
+    # one column with itself as the aggregate is the plain scan
+    w, b, base, lo, hi = cols[1]
+    assert oracle.scan_conj([cols[1]], n, (w, b, base)) == oracle.scan_packed(w, n, b, base, lo, hi)
+

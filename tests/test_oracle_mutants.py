@@ -33,6 +33,8 @@ MUTANTS = {
                                         "if (lo <= (int64_t)zmin[k] && (int64_t)zmax[k] <= hi) {")],
     "inside tail block counted whole": [("            c += (int64_t)(last - first);\n            s += (int64_t)sums[k];",
                                          "            c += (int64_t)BLOCK_VALUES;\n            s += (int64_t)sums[k];")],
+    "conjunction checks only the first column": [("for (c = 0; c < k && all; ++c) {",
+                                                  "for (c = 0; c < 1 && all; ++c) {")],
     "select inclusive upper bound": [("(int64_t)base;\n        if (lo <= v && v < hi) {\n            if (k < capacity)",
                                       "(int64_t)base;\n        if (lo <= v && v <= hi) {\n            if (k < capacity)")],
     "select position off by one": [("if (k < capacity) pos[k] = (uint32_t)i;\n            k += 1;\n        }\n    }\n"
@@ -81,6 +83,9 @@ class Lib:
         self.l.oracle_blocksums.argtypes = [u32p, u64, u32, u32, u64p]
         self.l.oracle_scan_zoneagg.argtypes = [u32p, u32p, u32p, u64p, u64, u32, u32, i64, i64,
                                                ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(u64)]
+        self.l.oracle_scan_conj.argtypes = [ctypes.POINTER(ctypes.c_void_p), u32p, u32p, ctypes.POINTER(i64),
+                                            ctypes.POINTER(i64), u32, u64, ctypes.c_void_p, u32, u32,
+                                            ctypes.POINTER(i64), ctypes.POINTER(i64)]
         self.l.oracle_pack_rowmajor.argtypes = [u32p, u64, u32, u32, u32p]
         self.l.oracle_scan_rowmajor.argtypes = [u32p, u64, u32, u32, i64, i64, ctypes.POINTER(i64),
                                                 ctypes.POINTER(i64)]
@@ -113,6 +118,17 @@ class Lib:
         self.l.oracle_scan_zoneagg(w, mn, mx, sums, n, b, base, lo, hi, ctypes.byref(c), ctypes.byref(s),
                                    ctypes.byref(t))
         return c.value, s.value, t.value
+
+    def conj(self, cols, n):
+        k = len(cols)
+        ptrs = (ctypes.c_void_p * k)(*[c[0].ctypes.data for c in cols])
+        bs = np.array([c[1] for c in cols], np.uint32)
+        bases = np.array([c[2] for c in cols], np.uint32)
+        los = (ctypes.c_int64 * k)(*[c[3] for c in cols])
+        his = (ctypes.c_int64 * k)(*[c[4] for c in cols])
+        c_, s_ = ctypes.c_int64(), ctypes.c_int64()
+        self.l.oracle_scan_conj(ptrs, bs, bases, los, his, k, n, None, 0, 0, ctypes.byref(c_), ctypes.byref(s_))
+        return c_.value
 
     def pack_rowmajor(self, v, b, base=0):
         out = np.zeros(((v.size + 1023) // 1024) * 32 * b, np.uint32)
@@ -178,6 +194,13 @@ def pins(o):
         m = (v.astype(np.int64) >= lo) & (v.astype(np.int64) < hi)
         c, s_, t = o.zoneagg(w, mn, mx, n, b, 0, lo, hi)
         assert (c, s_) == (int(m.sum()), int(v[m].astype(np.int64).sum()))
+    # conjunction of two columns: COUNT fixed by numpy masks
+    n = 3000
+    va, vb = synth.uniform_values(10, n, 6), synth.uniform_values(11, n, 9)
+    ca = (o.pack(va, 6), 6, 0, 10, 50)
+    cb = (o.pack(vb, 9), 9, 0, 100, 400)
+    m = (va >= 10) & (va < 50) & (vb >= 100) & (vb < 400)
+    assert o.conj([ca, cb], n) == int(m.sum())
     # row-major layout: bit-level stream and brute-force scans
     for b in (3, 13, 24):
         v = synth.uniform_values(synth.seed_for(78, b), 2100, b)
