@@ -470,6 +470,7 @@ def run_ours(args, world, rank, local):
     plain = None if args.no_extra else run_plain(args, dev, stream, gbscan, beta_read)
     select = None if args.no_extra else run_select(args, dev, stream, gbscan, peaks().get("hbm_gbs", 6800.0))
     layouts = None if args.no_extra else run_layouts(args, dev, stream, gbscan, beta_read)
+    conj = None if args.no_extra else run_conj(args, dev, stream, gbscan, peaks().get("hbm_gbs", 6800.0))
     zone = None if args.no_extra else run_zone_sweep(args, dev, stream, gbscan)
     tdec = [law["branchfree"]["t_dec_gvals"], law["branchy"]["t_dec_gvals"],
             law["branchfree"]["t_dec_gvals"], law["branchy"]["t_dec_gvals"]]
@@ -494,6 +495,7 @@ def run_ours(args, world, rank, local):
         "zone_sweep": zone,
         "select": select,
         "layouts": layouts,
+        "conjunctive": conj,
         "batched": batched,
         "serving": serving,
         "realised_sigma": realised,
@@ -632,6 +634,58 @@ def run_layouts(args, dev, stream, gbscan, beta_read):
             "t_dec_below_ridge_gvals": round(float(np.median([rows[b]["gvals_per_s"] for b in rows
                                                                if rows[b]["f"] < 0.7] or [float("nan")])), 1),
         }
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_conj(args, dev, stream, gbscan, hbm_gbs):
+    """Conjunctive predicates over k = 1..4 columns of one table (2^27 rows; b = 8, 12,
+    16, 24; uniform values; sigma = 0.5 per column, so 2^-k of the rows survive), SUM
+    of the b = 24 column over the selected rows; against one counting scan per column
+    (the serving loop's bag of independent scans).  Bytes = every column read once
+    plus the aggregate column."""
+    import torch
+
+    n = 1 << 27
+    widths = [8, 12, 16, 24]
+    out = {"workload": "conjunctive scan: 2^27-row table, b = 8/12/16/24 uniform, sigma 0.5 per column, "
+                       "k = 1..4 predicate columns, SUM of the b=24 column", "rows": []}
+    cols = []
+    with torch.cuda.stream(stream):
+        for i, b in enumerate(widths):
+            v = synth.uniform_values_device(synth.seed_for(13, i), n, b, device=dev)
+            cols.append(gbscan.Column.from_device(v, n, b, stream=stream))
+            del v
+    torch.cuda.synchronize()
+    preds = [synth.pick_range(synth.seed_for(13, i, 1), b, 0.5) for i, b in enumerate(widths)]
+    res = torch.zeros((4, 4), dtype=torch.int64, device=dev)
+
+    def timed(fn):
+        fn()
+        ts = []
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    for k in range(1, 5):
+        sel = cols[:k]
+        r = gbscan.scan_conj(sel, preds[:k], cols[3], stream=stream)
+        ms = timed(lambda: gbscan.scan_conj(sel, preds[:k], cols[3], stream=stream))
+        ms_sep = timed(lambda: [c.run_async(lo, hi, res[i], "branchfree", stream)
+                                for i, (c, (lo, hi)) in enumerate(zip(sel, preds[:k]))])
+        nbytes = sum(gbscan.scan_packed_words(n, b) * 4 for b in widths[:k]) + gbscan.scan_packed_words(n, 24) * 4
+        out["rows"].append({"k": k, "selected_fraction": round(r.count / n, 5), "ms_conj": round(ms, 4),
+                            "ms_separate_column_scans": round(ms_sep, 4),
+                            "gbs_conj": round(nbytes / (ms * 1e-3) / 1e9, 1),
+                            "frac_conj": round(nbytes / (ms * 1e-3) / 1e9 / hbm_gbs, 4),
+                            "blocks_aggregated": int(r.blocks_scanned)})
+    for c in cols:
+        c.close()
     torch.cuda.empty_cache()
     return out
 

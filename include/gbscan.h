@@ -241,6 +241,22 @@ scan_status scan_select(scan_column *col, scan_pred pred, scan_strategy strategy
 scan_status scan_select_async(scan_column *col, scan_pred pred, scan_strategy strategy,
                               uint32_t *dev_positions, uint64_t capacity, void *stream, uint64_t *dev_count);
 
+/* ---------------------------------------------- conjunctive predicates */
+
+/* Conjunctive scan over k >= 1 columns of one table (the problem of paper §2
+ * over rows shared by several columns): COUNT of the rows i with
+ * preds[c].lo <= v_c,i < preds[c].hi for every column c, and SUM of the
+ * aggregate column's values over those rows (0 when agg is NULL; agg may be
+ * one of cols).  All columns lane-interleaved and of equal length.  One pass
+ * per predicate column builds a selection vector (a 32-bit row mask per lane
+ * and block) in the given order -- later columns skip the decode of blocks
+ * whose selection is already empty, so the most selective column first is
+ * fastest -- and one pass aggregates over it.  blocks_scanned = blocks of
+ * the aggregate column decoded.  strategy: SCAN_AUTO or SCAN_BRANCHFREE.
+ * Calls sharing a column must be ordered on one stream; waits for the stream. */
+scan_status scan_conj(scan_column *const *cols, const scan_pred *preds, uint32_t k, scan_column *agg,
+                      scan_strategy strategy, void *stream, scan_result *host_out);
+
 /* -------------------------------------------------------------- batches */
 
 typedef struct scan_batch scan_batch; /* opaque: a planned batch of column scans */

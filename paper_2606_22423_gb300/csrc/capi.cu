@@ -198,6 +198,9 @@ bool gb_column_view(const scan_column* c, const uint32_t** packed, uint64_t* n, 
     return true;
 }
 
+// Scan parameters of a column (its data and workspace), for other units of the library.
+gb::ScanParams gb_column_params(const scan_column* c);
+
 cudaError_t gb_column_select_ws(scan_column* c, uint64_t words, cudaStream_t st, GbSelectWs* out)
 {
     cudaError_t e = cudaSuccess;
@@ -438,6 +441,12 @@ gb::ScanParams base_params(const scan_column* c)
     p.result = c->ws.result;
     return p;
 }
+
+}  // namespace
+
+gb::ScanParams gb_column_params(const scan_column* c) { return base_params(c); }
+
+namespace {
 
 int persistent_grid()
 {

@@ -26,3 +26,10 @@ struct GbSelectWs {
 // Grows the column's select workspace to at least `words` tagged words and
 // hands out a fresh tag (clearing the words when the tag wraps).
 cudaError_t gb_column_select_ws(scan_column* c, uint64_t words, cudaStream_t st, GbSelectWs* out);
+
+namespace gb {
+struct ScanParams;
+}
+// Scan parameters of a column: its packed data, n, base, zone map and device
+// workspace (result, status, grid-finish ticket, queue counters, partials).
+gb::ScanParams gb_column_params(const scan_column* c);

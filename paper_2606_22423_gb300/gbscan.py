@@ -79,6 +79,7 @@ SIGNATURES = {
     "scan_column_get_layout": (_st, [_vp, ctypes.POINTER(ctypes.c_int)]),
     "scan_column_blocksums": (_st, [_vp, ctypes.POINTER(_vp)]),
     "scan_select": (_st, [_vp, scan_pred, _st, _vp, _u64, _vp, ctypes.POINTER(_u64)]),
+    "scan_conj": (_st, [_vp, _vp, _u32, _vp, _st, _vp, ctypes.POINTER(scan_result)]),
     "scan_select_async": (_st, [_vp, scan_pred, _st, _vp, _u64, _vp, _vp]),
     "scan_probe_read": (_st, [_vp, _u64, _vp, _vp]),
     "scan_launch_shape": (_st, [_u32] + [ctypes.POINTER(_u32)] * 5),
@@ -376,6 +377,18 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def scan_conj(columns, preds, agg=None, stream=None) -> scan_result:
+    """Conjunctive scan: COUNT of rows meeting every (lo, hi) of `preds` on the
+    matching `columns`, and SUM of `agg` (a Column or None) over those rows."""
+    k = len(columns)
+    cols = (_vp * max(k, 1))(*[c.handle.value for c in columns])
+    pr = (scan_pred * max(k, 1))(*[scan_pred(lo, hi) for lo, hi in preds])
+    out = scan_result()
+    _check(load().scan_conj(cols, pr, k, agg.handle if agg is not None else None, SCAN_BRANCHFREE,
+                            _stream(stream), ctypes.byref(out)))
+    return out
 
 
 def scan_batch_run(columns, preds, strategies=None, stream=None):
