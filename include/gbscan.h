@@ -253,9 +253,17 @@ scan_status scan_select_async(scan_column *col, scan_pred pred, scan_strategy st
  * whose selection is already empty, so the most selective column first is
  * fastest -- and one pass aggregates over it.  blocks_scanned = blocks of
  * the aggregate column decoded.  strategy: SCAN_AUTO or SCAN_BRANCHFREE.
- * Calls sharing a column must be ordered on one stream; waits for the stream. */
+ * The selection vector (n/8 bytes) is kept with the result column (agg, else
+ * cols[0]) for later calls.  Calls sharing a column must be ordered on one
+ * stream; waits for the stream. */
 scan_status scan_conj(scan_column *const *cols, const scan_pred *preds, uint32_t k, scan_column *agg,
                       scan_strategy strategy, void *stream, scan_result *host_out);
+
+/* As scan_conj, but the 32-byte result goes to device memory and the call
+ * returns without waiting; check scan_column_status on the aggregate column
+ * (or cols[0] when agg is NULL) afterwards. */
+scan_status scan_conj_async(scan_column *const *cols, const scan_pred *preds, uint32_t k, scan_column *agg,
+                            scan_strategy strategy, void *stream, scan_result *dev_out);
 
 /* -------------------------------------------------------------- batches */
 
@@ -351,10 +359,12 @@ scan_status scan_planner_train_step(scan_planner *planner, const float *dev_x, c
 /* dev_choice[rows] = argmin over strategies of the predicted log time. */
 scan_status scan_planner_choose(scan_planner *planner, const float *dev_x, uint32_t rows,
                                 int32_t *dev_choice, void *stream);
-/* As scan_planner_choose, but strategy 0 (the default plan) is kept unless
- * another strategy's predicted log time is lower by more than `margin`
- * (>= 0; e.g. the network's RMS error in log time, so that a plan changes
- * only on a predicted gain larger than the model's own error). */
+/* As scan_planner_choose, but each row gets the first strategy in index
+ * order (branch-free, branchy, zone-skip branch-free, zone-skip branchy)
+ * whose predicted log time is within `margin` (>= 0) of the row's minimum --
+ * e.g. the network's RMS error in log time, so that the plan leaves a
+ * simpler strategy only for a predicted gain larger than the model's own
+ * error.  margin 0 is scan_planner_choose. */
 scan_status scan_planner_choose_margin(scan_planner *planner, const float *dev_x, uint32_t rows,
                                        float margin, int32_t *dev_choice, void *stream);
 /* Binary checkpoint: 16-byte header (magic, version 1, S, count) + floats. */

@@ -180,6 +180,8 @@ struct scan_column {
     Workspace ws{};
     scan_result* host_result = nullptr;  // pinned staging, 48 bytes (result + status)
     int layout = SCAN_LAYOUT_LANES;         // order of the codes inside each block
+    uint32_t* conj_mask = nullptr;          // conjunctive scans: selection vector (grown on demand)
+    uint64_t conj_words = 0;
     unsigned long long* sel_agg = nullptr;  // materializing select: tagged CTA totals
     uint64_t sel_words = 0;
     uint32_t sel_epoch = 0;
@@ -200,6 +202,20 @@ bool gb_column_view(const scan_column* c, const uint32_t** packed, uint64_t* n, 
 
 // Scan parameters of a column (its data and workspace), for other units of the library.
 gb::ScanParams gb_column_params(const scan_column* c);
+
+cudaError_t gb_column_conj_mask(scan_column* c, uint64_t words, uint32_t** out)
+{
+    if (words > c->conj_words) {
+        if (c->conj_mask) cudaFree(c->conj_mask);  // synchronises: no earlier scan still uses it
+        c->conj_mask = nullptr;
+        c->conj_words = 0;
+        const cudaError_t e = cudaMalloc(&c->conj_mask, words * sizeof(uint32_t));
+        if (e != cudaSuccess) return e;
+        c->conj_words = words;
+    }
+    *out = c->conj_mask;
+    return cudaSuccess;
+}
 
 cudaError_t gb_column_select_ws(scan_column* c, uint64_t words, cudaStream_t st, GbSelectWs* out)
 {
@@ -773,6 +789,7 @@ scan_status scan_column_destroy(scan_column* col)
     if (col->ws_raw) cudaFree(col->ws_raw);
     if (col->host_result) cudaFreeHost(col->host_result);
     if (col->sel_agg) cudaFree(col->sel_agg);
+    if (col->conj_mask) cudaFree(col->conj_mask);
     delete col;
     return SCAN_OK;
 }

@@ -56,60 +56,46 @@ bool set_smem(const void* fn, int bytes, std::atomic<unsigned long long>& done)
     return true;
 }
 
-template <int B, bool FIRST>
-cudaError_t launch_mask(const gb::ConjParams& p, int grid, cudaStream_t st)
+template <int B, int MODE>
+cudaError_t launch_pass(const gb::ConjParams& c, const gb::ScanParams& p, int grid, cudaStream_t st)
 {
     static std::atomic<unsigned long long> done{0ull};
-    auto k = gb::k_conj_mask<B, FIRST>;
-    if (!set_smem(reinterpret_cast<const void*>(k), gb::Shape<B>::kSmemBytes, done)) return cudaErrorInvalidValue;
-    k<<<grid, gb::Shape<B>::kWarps * 32, gb::Shape<B>::kSmemBytes, st>>>(p);
-    return cudaGetLastError();
-}
-
-template <int B>
-cudaError_t launch_agg(const gb::ScanParams& p, const uint32_t* mask, int grid, cudaStream_t st)
-{
-    static std::atomic<unsigned long long> done{0ull};
-    auto k = gb::k_conj_agg<B>;
-    if (!set_smem(reinterpret_cast<const void*>(k), gb::Shape<B>::kSmemBytes, done)) return cudaErrorInvalidValue;
-    k<<<grid, gb::Shape<B>::kWarps * 32, gb::Shape<B>::kSmemBytes, st>>>(p, mask);
+    using S = gb::ConjShape<B>;
+    auto k = gb::k_conj_pass<B, MODE>;
+    if (!set_smem(reinterpret_cast<const void*>(k), S::kSmemBytes, done)) return cudaErrorInvalidValue;
+    k<<<grid, S::kWarps * 32, S::kSmemBytes, st>>>(c, p);
     return cudaGetLastError();
 }
 
 template <int LO, int HI>
-cudaError_t mask_range(int b, bool first, const gb::ConjParams& p, int grid, cudaStream_t st)
+cudaError_t pass_range(int b, int mode, const gb::ConjParams& c, const gb::ScanParams& p, int grid,
+                       cudaStream_t st)
 {
     if constexpr (LO > HI) {
         return cudaErrorInvalidValue;
     } else {
-        if (b == LO) return first ? launch_mask<LO, true>(p, grid, st) : launch_mask<LO, false>(p, grid, st);
-        return mask_range<LO + 1, HI>(b, first, p, grid, st);
-    }
-}
-
-template <int LO, int HI>
-cudaError_t agg_range(int b, const gb::ScanParams& p, const uint32_t* mask, int grid, cudaStream_t st)
-{
-    if constexpr (LO > HI) {
-        return cudaErrorInvalidValue;
-    } else {
-        if (b == LO) return launch_agg<LO>(p, mask, grid, st);
-        return agg_range<LO + 1, HI>(b, p, mask, grid, st);
+        if (b == LO) {
+            if (mode == gb::kConjFirst) return launch_pass<LO, gb::kConjFirst>(c, p, grid, st);
+            if (mode == gb::kConjAnd) return launch_pass<LO, gb::kConjAnd>(c, p, grid, st);
+            return launch_pass<LO, gb::kConjAgg>(c, p, grid, st);
+        }
+        return pass_range<LO + 1, HI>(b, mode, c, p, grid, st);
     }
 }
 
 cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
 
-}  // namespace
-
-extern "C" scan_status scan_conj(scan_column* const* cols, const scan_pred* preds, uint32_t k, scan_column* agg,
-                                 scan_strategy strategy, void* stream, scan_result* host_out)
+// Enqueue the conjunctive scan; the result (count, sum, blocks decoded, 0)
+// goes to dev_result (device), or to the result column's workspace when NULL.
+// *empty: no launch was needed (the result is all zero).
+scan_status enqueue_conj(scan_column* const* cols, const scan_pred* preds, uint32_t k, scan_column* agg,
+                         scan_strategy strategy, cudaStream_t st, long long* dev_result, bool* empty_out,
+                         gb::ScanParams* rp_out)
 {
-    gb_set_last_error("");
-    if (!cols || !preds || !host_out || k == 0) return cfail(SCAN_EINVAL, "cols, preds and host_out are required, k >= 1");
+    *empty_out = false;
+    if (!cols || !preds || k == 0) return cfail(SCAN_EINVAL, "cols and preds are required, k >= 1");
     if (strategy != SCAN_AUTO && strategy != SCAN_BRANCHFREE)
         return cfail(SCAN_EINVAL, "the conjunctive scan takes SCAN_AUTO or SCAN_BRANCHFREE");
-    std::memset(host_out, 0, sizeof *host_out);
     struct Col {
         const uint32_t* packed;
         uint64_t n;
@@ -138,31 +124,51 @@ extern "C" scan_status scan_conj(scan_column* const* cols, const scan_pred* pred
             return cfail(SCAN_EINVAL, "the aggregate column is not lane-interleaved");
         if (ag.n != cs[0].n) return cfail(SCAN_EINVAL, "the aggregate column differs in length");
     }
-    const uint64_t n = cs[0].n;
-    if (n == 0 || empty) return SCAN_OK;
-    cudaStream_t st = as_stream(stream);
-    const uint64_t nblocks = (n + 1023u) >> 10;
-    uint32_t* mask = nullptr;
-    CJ_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&mask), nblocks * 32u * sizeof(uint32_t), st));
     gb::ScanParams rp = gb_column_params(agg ? agg : cols[0]);
+    if (dev_result) rp.result = dev_result;
+    if (rp_out) *rp_out = rp;
+    const uint64_t n = cs[0].n;
+    if (n == 0 || empty) {
+        *empty_out = true;
+        return SCAN_OK;
+    }
+    const uint64_t nblocks = (n + 1023u) >> 10;
+    uint32_t* mask = nullptr;  // the result column's selection vector, reused across calls
+    CJ_CUDA(gb_column_conj_mask(agg ? agg : cols[0], nblocks * 32u, &mask));
     const int grid = sm_count();
     cudaError_t e = cudaSuccess;
     for (uint32_t c = 0; c < k && e == cudaSuccess; ++c) {
         gb::ConjParams p{cs[c].packed, n, cs[c].lo, cs[c].wm1, mask, rp.status};
-        e = mask_range<1, 32>(static_cast<int>(cs[c].b), c == 0, p, grid, st);
+        e = pass_range<1, 32>(static_cast<int>(cs[c].b), c == 0 ? gb::kConjFirst : gb::kConjAnd, p, rp, grid, st);
     }
     if (e == cudaSuccess) {
         if (agg) {
-            e = agg_range<1, 32>(static_cast<int>(ag.b), rp, mask, grid, st);
+            gb::ConjParams p{ag.packed, n, 0u, 0u, mask, rp.status};
+            e = pass_range<1, 32>(static_cast<int>(ag.b), gb::kConjAgg, p, rp, grid, st);
         } else {
-            rp.base = 0;
-            gb::k_conj_count<<<grid, 256, 0, st>>>(rp, mask, nblocks * 32u);
+            gb::ScanParams cp = rp;
+            cp.base = 0;
+            gb::k_conj_count<<<grid, 256, 0, st>>>(cp, mask, nblocks * 32u);
             e = cudaGetLastError();
         }
     }
-    const cudaError_t ef = cudaFreeAsync(mask, st);
     if (e != cudaSuccess) return ccuda(e, "conjunctive scan launch");
-    if (ef != cudaSuccess) return ccuda(ef, "cudaFreeAsync(mask)");
+    return SCAN_OK;
+}
+
+}  // namespace
+
+extern "C" scan_status scan_conj(scan_column* const* cols, const scan_pred* preds, uint32_t k, scan_column* agg,
+                                 scan_strategy strategy, void* stream, scan_result* host_out)
+{
+    gb_set_last_error("");
+    if (!host_out) return cfail(SCAN_EINVAL, "host_out is NULL");
+    std::memset(host_out, 0, sizeof *host_out);
+    cudaStream_t st = as_stream(stream);
+    bool empty = false;
+    gb::ScanParams rp{};
+    const scan_status s = enqueue_conj(cols, preds, k, agg, strategy, st, nullptr, &empty, &rp);
+    if (s != SCAN_OK || empty) return s;
     long long res[4];
     unsigned int dev_status = 0;
     CJ_CUDA(cudaMemcpyAsync(res, rp.result, sizeof res, cudaMemcpyDeviceToHost, st));
@@ -175,5 +181,19 @@ extern "C" scan_status scan_conj(scan_column* const* cols, const scan_pred* pred
     host_out->count = res[0];
     host_out->sum = res[1];
     host_out->blocks_scanned = res[2];
+    return SCAN_OK;
+}
+
+extern "C" scan_status scan_conj_async(scan_column* const* cols, const scan_pred* preds, uint32_t k,
+                                       scan_column* agg, scan_strategy strategy, void* stream, scan_result* dev_out)
+{
+    gb_set_last_error("");
+    if (!dev_out) return cfail(SCAN_EINVAL, "dev_out is NULL");
+    cudaStream_t st = as_stream(stream);
+    bool empty = false;
+    const scan_status s =
+        enqueue_conj(cols, preds, k, agg, strategy, st, reinterpret_cast<long long*>(dev_out), &empty, nullptr);
+    if (s != SCAN_OK) return s;
+    if (empty) CJ_CUDA(cudaMemsetAsync(dev_out, 0, sizeof(scan_result), st));
     return SCAN_OK;
 }

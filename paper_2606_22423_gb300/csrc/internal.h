@@ -23,6 +23,10 @@ struct GbSelectWs {
     scan_result* host_result;  // pinned staging for result + status (36 bytes)
 };
 
+// The column's selection-vector buffer for conjunctive scans, grown to at
+// least `words` 32-bit words (kept for later calls; freed with the column).
+cudaError_t gb_column_conj_mask(scan_column* c, uint64_t words, uint32_t** out);
+
 // Grows the column's select workspace to at least `words` tagged words and
 // hands out a fresh tag (clearing the words when the tag wraps).
 cudaError_t gb_column_select_ws(scan_column* c, uint64_t words, cudaStream_t st, GbSelectWs* out);

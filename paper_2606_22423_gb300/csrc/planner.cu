@@ -126,20 +126,19 @@ __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float
     p[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
 }
 
-// Strategy 0 (the default plan) is kept unless another strategy's predicted
-// log time is lower by more than `margin`; among those, the lowest wins.
+// The first strategy (in index order) whose predicted log time is within
+// `margin` of the row's minimum: with margin 0 the argmin (ties to the lower
+// index); with margin > 0 predicted gains below the margin do not move the
+// plan off the earlier (simpler) strategies.
 __global__ void k_argmin_rows(const float* __restrict__ y, int rows, int S, float margin,
                               int32_t* __restrict__ out)
 {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= rows) return;
+    float lo = y[n * S];
+    for (int s = 1; s < S; ++s) lo = fminf(lo, y[n * S + s]);
     int best = 0;
-    float bestv = y[n * S] - margin;
-    for (int s = 1; s < S; ++s)
-        if (y[n * S + s] < bestv) {
-            best = s;
-            bestv = y[n * S + s];
-        }
+    while (best < S - 1 && y[n * S + best] > lo + margin) ++best;
     out[n] = best;
 }
 

@@ -80,6 +80,7 @@ SIGNATURES = {
     "scan_column_blocksums": (_st, [_vp, ctypes.POINTER(_vp)]),
     "scan_select": (_st, [_vp, scan_pred, _st, _vp, _u64, _vp, ctypes.POINTER(_u64)]),
     "scan_conj": (_st, [_vp, _vp, _u32, _vp, _st, _vp, ctypes.POINTER(scan_result)]),
+    "scan_conj_async": (_st, [_vp, _vp, _u32, _vp, _st, _vp, _vp]),
     "scan_select_async": (_st, [_vp, scan_pred, _st, _vp, _u64, _vp, _vp]),
     "scan_probe_read": (_st, [_vp, _u64, _vp, _vp]),
     "scan_launch_shape": (_st, [_u32] + [ctypes.POINTER(_u32)] * 5),
@@ -389,6 +390,22 @@ def scan_conj(columns, preds, agg=None, stream=None) -> scan_result:
     _check(load().scan_conj(cols, pr, k, agg.handle if agg is not None else None, SCAN_BRANCHFREE,
                             _stream(stream), ctypes.byref(out)))
     return out
+
+
+class Conj:
+    """A prepared conjunctive query (argument arrays marshalled once) for
+    repeated asynchronous runs with the result in device memory."""
+
+    def __init__(self, columns, preds, agg=None):
+        self.k = len(columns)
+        self._cols = (_vp * max(self.k, 1))(*[c.handle.value for c in columns])
+        self._preds = (scan_pred * max(self.k, 1))(*[scan_pred(lo, hi) for lo, hi in preds])
+        self._agg = agg.handle if agg is not None else None
+        self._keep = (list(columns), agg)
+
+    def run_async(self, dev_out, stream=None):
+        _check(load().scan_conj_async(self._cols, self._preds, self.k, self._agg, SCAN_BRANCHFREE, _stream(stream),
+                                      _ptr(dev_out)))
 
 
 def scan_batch_run(columns, preds, strategies=None, stream=None):

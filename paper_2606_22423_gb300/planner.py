@@ -93,8 +93,8 @@ def train(planner, X, T, steps=1500, lr=3e-3, stream=None):
 
 def choose(planner, X, stream=None, margin=0.0):
     """Strategy names per row of X from the network (argmin of predicted log time).
-    With margin > 0 the default (branch-free full scan) is kept unless another
-    strategy is predicted faster by more than `margin` in log time."""
+    With margin > 0: the first strategy, in STRATEGIES order, whose predicted log
+    time is within `margin` of the row's minimum."""
     torch = _torch()
     out = torch.zeros(X.shape[0], dtype=torch.int32, device="cuda")
     planner.choose(X, X.shape[0], out, stream, margin=margin)

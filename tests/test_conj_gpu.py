@@ -81,6 +81,16 @@ def test_conjunction_edge_cases():
     c, s, blocks = _expect(vals, specs, [(lo, lo + 1), (100, 100 + (1 << 13))], 1, n)
     assert (r.count, r.sum, r.blocks_scanned) == (c, s, blocks)
     assert blocks <= 3
+    # the asynchronous form writes the same result to device memory
+    dres = torch.zeros(4, dtype=torch.int64, device="cuda")
+    s_ = torch.cuda.Stream()
+    q = gbscan.Conj(cols, [(lo, lo + 1), (100, 100 + (1 << 13))], cols[1])
+    q.run_async(dres, s_)
+    cols[1].status(s_)
+    assert dres.cpu().tolist()[:3] == [c, s, blocks]
+    gbscan.Conj(cols, [(0, 1 << 9), (5, 5)], cols[0]).run_async(dres, s_)     # empty: zeros
+    torch.cuda.synchronize()
+    assert dres.cpu().tolist() == [0, 0, 0, 0]
     for c_ in cols:
         c_.close()
 
