@@ -55,7 +55,7 @@ struct SelectParams {
 
 constexpr int kSelWarps = 8;
 constexpr int kSelStages = 3;   // data ring per warp (a slot is refilled right after its count pass)
-constexpr int kSelLag = 2;      // a tile is written kSelLag iterations after it was counted
+constexpr int kSelLag = 3;      // a tile is written kSelLag iterations after it was counted
 constexpr int kSelRing = 8;     // CTA count ring; must be >= 2 * kSelLag + 2
 constexpr uint32_t kSelSelectErr = 1u;  // same bit as kErrTimeout
 static_assert(kSelRing >= 2 * kSelLag + 2, "a CTA count slot is reused before every warp has read it");
