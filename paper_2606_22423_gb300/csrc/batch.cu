@@ -16,10 +16,7 @@
 #include "../../include/gbscan.h"
 #include "batch_kernels.cuh"
 
-void gb_set_last_error(const char* msg);
-// column internals shared with capi.cu
-bool gb_column_view(const scan_column* c, const uint32_t** packed, uint64_t* n, uint32_t* b,
-                    uint32_t* base, const uint2** zonemap);
+#include "internal.h"
 
 namespace {
 
@@ -43,16 +40,7 @@ scan_status bcuda(cudaError_t e, const char* what)
         if (e_ != cudaSuccess) return bcuda(e_, #call); \
     } while (0)
 
-int batch_grid()
-{
-    static int sms = [] {
-        int dev = 0, n = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        return n > 0 ? n : 1;
-    }();
-    return sms;
-}
+int batch_grid() { return gb_device_sms(); }
 
 uint32_t tile_blocks_for(uint32_t b) { return static_cast<uint32_t>(gb::shape_of(static_cast<int>(b)).tile_blocks); }
 

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -92,6 +93,44 @@ cudaError_t launch(int b, int op, const gb::ScanParams& p, int grid, cudaStream_
 
 // Lets other units of the library set the message scan_last_error() returns.
 void gb_set_last_error(const char* msg) { g_err = msg ? msg : ""; }
+
+// SM count and cooperative-launch support of the current device, read once
+// per device.
+namespace {
+constexpr int kMaxDevices = 64;
+std::atomic<int> g_dev_sms[kMaxDevices];
+std::atomic<int> g_dev_coop[kMaxDevices];
+int current_device()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) dev = 0;
+    return dev;
+}
+}  // namespace
+
+int gb_device_sms()
+{
+    const int dev = current_device();
+    int n = g_dev_sms[dev].load(std::memory_order_relaxed);
+    if (n <= 0) {
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+        g_dev_sms[dev].store(n, std::memory_order_relaxed);
+    }
+    return n;
+}
+
+bool gb_device_coop()
+{
+    const int dev = current_device();
+    int v = g_dev_coop[dev].load(std::memory_order_relaxed);
+    if (v == 0) {
+        int c = 0;
+        if (cudaDeviceGetAttribute(&c, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess) c = 0;
+        v = c ? 1 : -1;
+        g_dev_coop[dev].store(v, std::memory_order_relaxed);
+    }
+    return v > 0;
+}
 
 namespace gb {
 // ----------------------------------------------------- zone-map filtering
@@ -464,11 +503,7 @@ gb::ScanParams gb_column_params(const scan_column* c) { return base_params(c); }
 
 namespace {
 
-int persistent_grid()
-{
-    static int sms = device_info().sms;
-    return std::max(1, std::min(sms, kMaxGrid));
-}
+int persistent_grid() { return std::max(1, std::min(gb_device_sms(), kMaxGrid)); }
 
 // Translate [lo, hi) on decoded values into code space; false if empty.
 bool translate(const scan_column* c, scan_pred pr, gb::ScanParams& p)

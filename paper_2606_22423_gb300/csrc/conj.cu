@@ -33,16 +33,7 @@ scan_status ccuda(cudaError_t e, const char* what)
         if (e_ != cudaSuccess) return ccuda(e_, #call); \
     } while (0)
 
-int sm_count()
-{
-    static int sms = [] {
-        int dev = 0, n = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        return n > 0 ? n : 1;
-    }();
-    return sms;
-}
+int sm_count() { return gb_device_sms(); }
 
 // cudaFuncSetAttribute once per (kernel, device).
 bool set_smem(const void* fn, int bytes, std::atomic<unsigned long long>& done)

@@ -10,6 +10,10 @@
 // Sets the message scan_last_error() returns on this thread.
 void gb_set_last_error(const char* msg);
 
+// SM count and cooperative-launch support of the current device (cached per device).
+int gb_device_sms();
+bool gb_device_coop();
+
 // Read-only view of a column.
 bool gb_column_view(const scan_column* c, const uint32_t** packed, uint64_t* n, uint32_t* b,
                     uint32_t* base, const uint2** zonemap);

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 
@@ -32,32 +33,20 @@ scan_status scuda(cudaError_t e, const char* what)
         if (e_ != cudaSuccess) return scuda(e_, #call); \
     } while (0)
 
-struct Device {
-    int id = -1, sms = 0, coop = 0;
-};
-
-Device device()
-{
-    Device d;
-    if (cudaGetDevice(&d.id) != cudaSuccess) return d;
-    cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, d.id);
-    cudaDeviceGetAttribute(&d.coop, cudaDevAttrCooperativeLaunch, d.id);
-    return d;
-}
-
 template <int B, bool BRANCHY>
 cudaError_t launch_one(const gb::SelectParams& p, int grid, cudaStream_t st)
 {
     using S = gb::SelShape<B>;
     auto kernel = gb::k_select<B, BRANCHY>;
-    static int configured_for = -1;  // device whose attribute is set
+    static std::atomic<unsigned long long> configured{0ull};  // one bit per device
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (configured_for != dev) {
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (!(configured.load(std::memory_order_acquire) & bit)) {
         e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kSmemBytes);
         if (e != cudaSuccess) return e;
-        configured_for = dev;
+        configured.fetch_or(bit, std::memory_order_acq_rel);
     }
     gb::SelectParams q = p;
     void* args[] = {&q};
@@ -117,9 +106,8 @@ scan_status enqueue_select(scan_column* col, scan_pred pred, scan_strategy strat
         *empty = true;
         return SCAN_OK;
     }
-    static const Device dev = device();
-    if (!dev.coop) return sfail(SCAN_ENOTSUP, "the device cannot launch cooperative kernels");
-    const int grid = std::min(dev.sms, 256);  // the kernel polls up to 256 CTA totals per iteration
+    if (!gb_device_coop()) return sfail(SCAN_ENOTSUP, "the device cannot launch cooperative kernels");
+    const int grid = std::min(gb_device_sms(), 256);  // the kernel polls up to 256 CTA totals per iteration
     const uint64_t nblocks = (n + 1023u) >> 10;
     const uint64_t tb = static_cast<uint64_t>(tile_blocks_range<1, 32>(static_cast<int>(b)));
     const uint64_t ntiles = (nblocks + tb - 1) / tb;
