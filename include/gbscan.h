@@ -452,6 +452,15 @@ scan_status scan_probe_read(const void *dev_buf, uint64_t bytes, void *stream, u
  * broken. */
 scan_status scan_selftest_wait_timeout(uint64_t limit_ns, void *stream);
 
+/* Failure-path check of the select's waits on other CTAs (no paper
+ * counterpart; a test hook): runs the select over `col` with a wait bound of
+ * limit_ns (at most 1 s) while CTA 0 never publishes its totals, so every
+ * other CTA's bounded wait must give up, set the status, let its copies land
+ * and return.  Returns SCAN_ETIMEOUT when that happened (the status is
+ * cleared and the context stays usable); any other status means the path is
+ * broken.  Nothing is written. */
+scan_status scan_selftest_select_timeout(scan_column *col, uint64_t limit_ns, void *stream);
+
 /* Number of SMs and the persistent grid size the scan kernels use for width b. */
 scan_status scan_launch_shape(uint32_t b, uint32_t *sms, uint32_t *ctas, uint32_t *warps_per_cta,
                               uint32_t *blocks_per_tile, uint32_t *stages);

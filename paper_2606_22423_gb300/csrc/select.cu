@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdint>
 #include <atomic>
 #include <cstdio>
 #include <cstring>
@@ -79,7 +80,7 @@ int tile_blocks_range(int b)
 // Enqueue the select; *empty = true when no value can match (nothing launched).
 scan_status enqueue_select(scan_column* col, scan_pred pred, scan_strategy strategy, uint32_t* dev_positions,
                            uint64_t capacity, cudaStream_t st, unsigned long long* dev_count, bool* empty,
-                           GbSelectWs* ws_out)
+                           GbSelectWs* ws_out, uint64_t wait_limit_ns = gb::kWaitLimitNs, int32_t silent_cta = -1)
 {
     *empty = false;
     if (!col) return sfail(SCAN_EINVAL, "col is NULL");
@@ -127,6 +128,8 @@ scan_status enqueue_select(scan_column* col, scan_pred pred, scan_strategy strat
     p.niter = static_cast<uint32_t>(niter);
     p.count = dev_count ? dev_count : reinterpret_cast<unsigned long long*>(ws.result);
     p.status = ws.status;
+    p.wait_limit_ns = wait_limit_ns;
+    p.silent_cta = silent_cta;
     const cudaError_t e = branchy ? launch_range<true, 1, 32>(static_cast<int>(b), p, grid, st)
                                   : launch_range<false, 1, 32>(static_cast<int>(b), p, grid, st);
     if (e != cudaSuccess) return scuda(e, "select kernel launch");
@@ -178,6 +181,29 @@ scan_status scan_select(scan_column* col, scan_pred pred, scan_strategy strategy
     }
     *host_count = static_cast<uint64_t>(ws.host_result->count);
     return SCAN_OK;
+}
+
+scan_status scan_selftest_select_timeout(scan_column* col, uint64_t limit_ns, void* stream)
+{
+    gb_set_last_error("");
+    if (!col) return sfail(SCAN_EINVAL, "col is NULL");
+    if (limit_ns == 0 || limit_ns > 1000000000ull) return sfail(SCAN_EINVAL, "limit_ns must be in (0, 1e9]");
+    cudaStream_t st = as_stream(stream);
+    bool empty = false;
+    GbSelectWs ws{};
+    // every value matches, nothing is written (capacity 0), and CTA 0 never publishes
+    const scan_status s = enqueue_select(col, scan_pred{INT64_MIN / 2, INT64_MAX / 2}, SCAN_BRANCHFREE, nullptr, 0,
+                                         st, nullptr, &empty, &ws, limit_ns, 0);
+    if (s != SCAN_OK) return s;
+    if (empty) return sfail(SCAN_EINVAL, "the column is empty");
+    unsigned int dev_status = 0;
+    SL_CUDA(cudaMemcpyAsync(&dev_status, ws.status, sizeof dev_status, cudaMemcpyDeviceToHost, st));
+    SL_CUDA(cudaStreamSynchronize(st));
+    if (dev_status & gb::kSelSelectErr) {
+        SL_CUDA(cudaMemset(ws.status, 0, sizeof(unsigned int)));
+        return sfail(SCAN_ETIMEOUT, "the waits on the silent CTA gave up as designed");
+    }
+    return sfail(SCAN_ECUDA, "the select finished although one CTA never published");
 }
 
 }  // extern "C"

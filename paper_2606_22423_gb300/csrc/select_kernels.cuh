@@ -51,6 +51,8 @@ struct SelectParams {
     uint32_t niter;               // ceil(tiles / warps in the grid)
     unsigned long long* count;    // total number of matches
     unsigned int* status;         // kErrTimeout on an expired wait
+    uint64_t wait_limit_ns;       // bound of every wait (kWaitLimitNs in normal use)
+    int32_t silent_cta;           // -1; a self-test names a CTA that never publishes
 };
 
 constexpr int kSelWarps = 8;
@@ -327,7 +329,7 @@ __global__ void __launch_bounds__(kSelWarps * 32, 1) k_select(const SelectParams
             if (t < ntiles) {
                 const int s = static_cast<int>(consumed % kSelStages);
                 const uint32_t parity = (consumed / kSelStages) & 1u;
-                const bool ok = mbar_wait(&bars[s], parity, kWaitLimitNs);
+                const bool ok = mbar_wait(&bars[s], parity, p.wait_limit_ns);
                 if (!__all_sync(kFull, ok)) {
                     failed = true;
                     break;
@@ -362,8 +364,9 @@ __global__ void __launch_bounds__(kSelWarps * 32, 1) k_select(const SelectParams
                     __threadfence_block();
                     uint32_t sum = 0;
                     for (int w = 0; w < kSelWarps; ++w) sum += cc[w];
-                    st_relaxed(&p.agg[static_cast<uint64_t>(i) * gridDim.x + blockIdx.x],
-                               (static_cast<unsigned long long>(p.epoch) << 32) | sum);
+                    if (static_cast<int32_t>(blockIdx.x) != p.silent_cta)
+                        st_relaxed(&p.agg[static_cast<uint64_t>(i) * gridDim.x + blockIdx.x],
+                                   (static_cast<unsigned long long>(p.epoch) << 32) | sum);
                 }
             }
             __syncwarp();
@@ -384,7 +387,7 @@ __global__ void __launch_bounds__(kSelWarps * 32, 1) k_select(const SelectParams
                         const uint64_t t0 = global_ns();
                         uint32_t nap = 64;
                         do {
-                            if (global_ns() - t0 > kWaitLimitNs) {
+                            if (global_ns() - t0 > p.wait_limit_ns) {
                                 ok = false;
                                 break;
                             }
@@ -427,7 +430,7 @@ __global__ void __launch_bounds__(kSelWarps * 32, 1) k_select(const SelectParams
                 if (got != wi + 1u && got != ~0u) {
                     const uint64_t t0 = global_ns();
                     do {
-                        if (global_ns() - t0 > kWaitLimitNs) {
+                        if (global_ns() - t0 > p.wait_limit_ns) {
                             ok = false;
                             break;
                         }

@@ -80,6 +80,7 @@ SIGNATURES = {
     "scan_column_blocksums": (_st, [_vp, ctypes.POINTER(_vp)]),
     "scan_select": (_st, [_vp, scan_pred, _st, _vp, _u64, _vp, ctypes.POINTER(_u64)]),
     "scan_conj": (_st, [_vp, _vp, _u32, _vp, _st, _vp, ctypes.POINTER(scan_result)]),
+    "scan_selftest_select_timeout": (_st, [_vp, _u64, _vp]),
     "scan_conj_async": (_st, [_vp, _vp, _u32, _vp, _st, _vp, _vp]),
     "scan_select_async": (_st, [_vp, scan_pred, _st, _vp, _u64, _vp, _vp]),
     "scan_probe_read": (_st, [_vp, _u64, _vp, _vp]),

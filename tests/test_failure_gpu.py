@@ -29,6 +29,25 @@ def test_bounded_wait_times_out_and_context_survives():
     col.close()
 
 
+def test_select_waits_on_a_silent_cta_give_up_and_the_next_select_is_exact():
+    """The select's CTAs wait on each other's tagged totals; with one CTA that
+    never publishes, every bounded wait must run out (SCAN_ETIMEOUT), and a
+    normal select on the same column afterwards must still be exact."""
+    n, b = 3 * (1 << 20) + 77, 12
+    v = synth.uniform_values(5, n, b)
+    col = gbscan.Column.from_host(v, b)
+    lib = gbscan.load()
+    for limit_ns in (2_000_000, 20_000_000):
+        st = lib.scan_selftest_select_timeout(col.handle, limit_ns, None)
+        assert st == gbscan.SCAN_ETIMEOUT, lib.scan_last_error()
+    assert lib.scan_selftest_select_timeout(col.handle, 0, None) == gbscan.SCAN_EINVAL
+    want, k = oracle.select_values(v, 100, 900)
+    pos = torch.empty(k, dtype=torch.int32, device="cuda")
+    assert col.select(100, 900, pos) == k
+    assert (pos.cpu().numpy().view("uint32") == want).all()
+    col.close()
+
+
 def test_bad_arguments_are_refused_before_any_launch():
     assert gbscan.load().scan_selftest_wait_timeout(0, None) == gbscan.SCAN_EINVAL
     with pytest.raises(gbscan.ScanError) as e:
