@@ -271,7 +271,7 @@ typedef struct scan_batch scan_batch; /* opaque: a planned batch of column scans
 
 /* Plan a batch over `ncols` columns (the paper has no batched form; this
  * runs thousands of column scans as one CUDA-graph launch).  Every column's
- * blocks are cut into tiles of at most 8 KB; columns are grouped by
+ * blocks are cut into tiles of at most 12 KB; columns are grouped by
  * (predicate flavour, width) and each group is served by one width-specialised
  * persistent kernel, the groups recorded as parallel branches of one graph with
  * grids sized to their work.  Warps pop `tiles_per_pop` consecutive tiles per

@@ -42,7 +42,7 @@ scan_status bcuda(cudaError_t e, const char* what)
 
 int batch_grid() { return gb_device_sms(); }
 
-uint32_t tile_blocks_for(uint32_t b) { return static_cast<uint32_t>(gb::shape_of(static_cast<int>(b)).tile_blocks); }
+uint32_t tile_blocks_for(uint32_t b) { return gb::batch_tile_blocks(b); }
 
 // Control words after the results: one pop counter per width group (u32),
 // then the status word at u32 index kMaxGroups.

@@ -45,10 +45,23 @@ struct BatchParams {
     unsigned int* status;
 };
 
+// 8 warps, each with 2 slots of 12 KB: per tile the batch kernel spends about a
+// third of its issue on bookkeeping (column lookup, keep mask, copy issue),
+// so tiles larger than the scans' 8 KB pay (3 x 8 KB slots: -12% time).
 constexpr int kBatchWarps = 8;
-constexpr int kBatchStages = 3;
-constexpr int kBatchSlot = 8 * 1024;
+constexpr int kBatchStages = 2;
+constexpr int kBatchSlot = 12 * 1024;
 constexpr int kBatchSmem = kBatchWarps * kBatchStages * (kBatchSlot + 8 + 16);
+
+// Blocks per batch tile at width b: as many as fill a slot, a multiple of
+// the warp step (4 blocks for b <= 16, else 2), at most 64 (the keep mask).
+__host__ __device__ constexpr uint32_t batch_tile_blocks(uint32_t b)
+{
+    const uint32_t step = b <= 16 ? 4u : 2u;
+    const uint32_t tb = (static_cast<uint32_t>(kBatchSlot) / (128u * b)) / step * step;
+    return tb < step ? step : (tb > 64u ? 64u : tb);
+}
+static_assert(batch_tile_blocks(32) * 128u * 32u <= static_cast<uint32_t>(kBatchSlot), "a tile fits its slot");
 
 struct SlotMeta {
     uint32_t col;   // column index

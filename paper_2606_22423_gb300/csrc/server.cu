@@ -97,7 +97,7 @@ struct scan_server {
 
 namespace {
 
-uint32_t tile_blocks_for(uint32_t b) { return static_cast<uint32_t>(gb::shape_of(static_cast<int>(b)).tile_blocks); }
+uint32_t tile_blocks_for(uint32_t b) { return gb::batch_tile_blocks(b); }
 
 void fill_entry(gb::BatchCol& d, const scan_column* col, scan_pred pr, uint32_t out, uint32_t& tiles)
 // tiles: running tile count of the entry's width group (numbering restarts per group)
