@@ -467,16 +467,18 @@ def run_ours(args, world, rank, local):
     for c in cols.values():
         c.close()
     torch.cuda.empty_cache()
-    plain = None if args.no_extra else run_plain(args, dev, stream, gbscan, beta_read)
-    select = None if args.no_extra else run_select(args, dev, stream, gbscan, peaks().get("hbm_gbs", 6800.0))
-    layouts = None if args.no_extra else run_layouts(args, dev, stream, gbscan, beta_read)
-    conj = None if args.no_extra else run_conj(args, dev, stream, gbscan, peaks().get("hbm_gbs", 6800.0))
-    zone = None if args.no_extra else run_zone_sweep(args, dev, stream, gbscan)
+    # the per-feature sections describe one GPU; a multi-GPU (replica) run reports the sweep only
+    extra = not args.no_extra and world == 1
+    plain = run_plain(args, dev, stream, gbscan, beta_read) if extra else None
+    select = run_select(args, dev, stream, gbscan, peaks().get("hbm_gbs", 6800.0)) if extra else None
+    layouts = run_layouts(args, dev, stream, gbscan, beta_read) if extra else None
+    conj = run_conj(args, dev, stream, gbscan, peaks().get("hbm_gbs", 6800.0)) if extra else None
+    zone = run_zone_sweep(args, dev, stream, gbscan) if extra else None
     tdec = [law["branchfree"]["t_dec_gvals"], law["branchy"]["t_dec_gvals"],
             law["branchfree"]["t_dec_gvals"], law["branchy"]["t_dec_gvals"]]
-    batched = None if args.no_batch else run_batched(args, dev, stream, gbscan, beta_read, tdec)
+    batched = run_batched(args, dev, stream, gbscan, beta_read, tdec) if not args.no_batch and world == 1 else None
     torch.cuda.empty_cache()
-    serving = None if args.no_serve else run_serving(args, dev, stream, gbscan)
+    serving = run_serving(args, dev, stream, gbscan) if not args.no_serve and world == 1 else None
 
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
