@@ -66,14 +66,15 @@ cudaError_t launch_range(int b, const gb::SelectParams& p, int grid, cudaStream_
     }
 }
 
+// Blocks a warp covers per iteration (tiles per iteration x blocks per tile).
 template <int LO, int HI>
-int tile_blocks_range(int b)
+int iter_blocks_range(int b)
 {
     if constexpr (LO > HI) {
         return 1;
     } else {
-        if (b == LO) return gb::SelShape<LO>::kTB;
-        return tile_blocks_range<LO + 1, HI>(b);
+        if (b == LO) return gb::SelShape<LO>::kIB;
+        return iter_blocks_range<LO + 1, HI>(b);
     }
 }
 
@@ -110,10 +111,11 @@ scan_status enqueue_select(scan_column* col, scan_pred pred, scan_strategy strat
     if (!gb_device_coop()) return sfail(SCAN_ENOTSUP, "the device cannot launch cooperative kernels");
     const int grid = std::min(gb_device_sms(), 256);  // the kernel polls up to 256 CTA totals per iteration
     const uint64_t nblocks = (n + 1023u) >> 10;
-    const uint64_t tb = static_cast<uint64_t>(tile_blocks_range<1, 32>(static_cast<int>(b)));
-    const uint64_t ntiles = (nblocks + tb - 1) / tb;
+    // iteration i covers blocks [i*warps*ib, (i+1)*warps*ib): ib per warp, tiles
+    // never straddling two warps (ib is a whole number of tiles)
+    const uint64_t ib = static_cast<uint64_t>(iter_blocks_range<1, 32>(static_cast<int>(b)));
     const uint64_t warps = static_cast<uint64_t>(grid) * gb::kSelWarps;
-    const uint64_t niter = (ntiles + warps - 1) / warps;
+    const uint64_t niter = (nblocks + warps * ib - 1) / (warps * ib);
     GbSelectWs ws{};
     SL_CUDA(gb_column_select_ws(col, niter * static_cast<uint64_t>(grid), st, &ws));
     gb::SelectParams p{};

@@ -6,9 +6,10 @@
 // One persistent, co-resident grid (one CTA of 8 warps per SM).  Each warp
 // streams its own tiles through a 3-stage ring of bulk copies.  The output
 // order needs every tile's offset, i.e. the number of matches in all earlier
-// tiles, so the work runs in iterations: in iteration i warp gw owns tile
-// gw + i*GW (GW = warps in the grid), which makes each iteration one
-// contiguous range of tiles.
+// tiles, so the work runs in iterations: in iteration i warp gw owns the M
+// consecutive tiles starting at tile (i*GW + gw)*M (GW = warps in the grid;
+// M tiles make about 8 blocks), which makes each iteration one contiguous
+// range of tiles.
 //   count pass : decode the tile from shared memory once and keep, per lane
 //                and block, a 32-bit column mask (bit r = value 32r + lane
 //                matches).  The data slot is refilled right away; only the
@@ -65,28 +66,44 @@ static_assert(kSelRing >= 2 * kSelLag + 2, "a CTA count slot is reused before ev
 // after every 32, so that the 32 rows' writes at 32r + j fall in distinct banks.
 constexpr int kSelStageHalfs = 1024 + 64;
 
-__host__ __device__ constexpr int sel_warp_bytes(int b, int tb)
+__host__ __device__ constexpr int sel_warp_bytes(int b, int tb, int m)
 {
-    return kSelStages * tb * 128 * b + (kSelLag + 1) * tb * 32 * 4 + kSelStageHalfs * 2 + kSelStages * 8;
+    return kSelStages * tb * 128 * b + (kSelLag + 1) * tb * m * 32 * 4 + kSelStageHalfs * 2 + kSelStages * 8;
 }
 
-// Blocks per warp tile: at most 8 KB of data and 8 blocks, shrunk until the
-// CTA's ring, masks and stages fit the 227 KB of shared memory.
+__host__ __device__ constexpr bool sel_fits(int b, int tb, int m) { return kSelWarps * sel_warp_bytes(b, tb, m) + 1024 <= 227 * 1024; }
+
+// Blocks per warp tile (one bulk copy): at most 8 KB of data and 8 blocks,
+// shrunk until the CTA's ring, masks and stages fit the 227 KB of shared memory.
 __host__ __device__ constexpr int sel_tile_blocks(int b)
 {
     int tb = 8192 / (128 * b);
     tb = tb < 1 ? 1 : (tb > 8 ? 8 : tb);
-    while (tb > 1 && kSelWarps * sel_warp_bytes(b, tb) + 1024 > 227 * 1024) --tb;
+    while (tb > 1 && !sel_fits(b, tb, 1)) --tb;
     return tb;
+}
+
+// Tiles per warp and iteration: up to 8 blocks in all, as many as the masks'
+// shared memory allows (wide widths have small tiles; taking several per
+// iteration divides the iterations, and their synchronisation, by as much).
+__host__ __device__ constexpr int sel_iter_tiles(int b)
+{
+    const int tb = sel_tile_blocks(b);
+    int m = 8 / tb;
+    m = m < 1 ? 1 : m;
+    while (m > 1 && !sel_fits(b, tb, m)) --m;
+    return m;
 }
 
 template <int B>
 struct SelShape {
     static constexpr int kBlockBytes = 128 * B;
     static constexpr int kTB = sel_tile_blocks(B);
+    static constexpr int kM = sel_iter_tiles(B);
+    static constexpr int kIB = kM * kTB;  // blocks per warp and iteration
     static constexpr int kTileBytes = kTB * kBlockBytes;
     static constexpr int kDataBytes = kSelWarps * kSelStages * kTileBytes;
-    static constexpr int kMaskBytes = kSelWarps * (kSelLag + 1) * kTB * 32 * 4;
+    static constexpr int kMaskBytes = kSelWarps * (kSelLag + 1) * kIB * 32 * 4;
     static constexpr int kStageBytes = kSelWarps * kSelStageHalfs * 2;
     static constexpr int kSmemBytes = kDataBytes + kMaskBytes + kStageBytes + kSelWarps * kSelStages * 8;
     static_assert(kSmemBytes + 1024 <= 227 * 1024, "shared-memory budget");
@@ -137,16 +154,19 @@ __device__ __forceinline__ uint32_t sel_block_mask(const uint32_t* words, int la
     uint32_t W[B];
 #pragma unroll
     for (int w = 0; w < B; ++w) W[w] = words[w * 32 + lane];
-    uint32_t pm = 0u;
+    // four interleaved OR chains (rows r = c mod 4), merged at the end, so
+    // that no chain of 32 dependent ORs sets the pace
+    uint32_t acc[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
     for (int r = 0; r < 32; ++r) {
         const uint32_t u = sel_code<B>(W, r);
         asm("{\n\t.reg .pred p;\n\t"
             "setp.le.u32 p, %1, %2;\n\t"
             "@p or.b32 %0, %0, %3;\n\t}"
-            : "+r"(pm)
+            : "+r"(acc[r & 3])
             : "r"(u - lo), "r"(wm1), "r"(1u << r));
     }
+    uint32_t pm = (acc[0] | acc[1]) | (acc[2] | acc[3]);
     if (limit < 1024u) {  // zero-padded tail block: rows at or past `limit` do not exist
         const uint32_t l = static_cast<uint32_t>(lane);
         const uint32_t rows = limit > l ? (limit - l + 31u) >> 5 : 0u;
@@ -233,11 +253,21 @@ __device__ __forceinline__ uint32_t sel_write_tile(const uint32_t* mk, uint32_t 
                 ++at;
             }
         } else {
+            // four independent chains over the row's bytes, each starting
+            // where the matches of the bytes below it end
+            const uint32_t r = rm[k];
+            uint32_t a[4] = {at, at + static_cast<uint32_t>(__popc(r & 0xffu)),
+                             at + static_cast<uint32_t>(__popc(r & 0xffffu)),
+                             at + static_cast<uint32_t>(__popc(r & 0xffffffu))};
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                if ((rm[k] >> j) & 1u) {  // predicated, no branch
-                    stage[at + ((at >> 5) << 1)] = static_cast<uint16_t>(row0 + static_cast<uint32_t>(j));
-                    ++at;
+            for (int j = 0; j < 8; ++j) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int bit = 8 * c + j;
+                    if ((r >> bit) & 1u) {  // predicated, no branch
+                        stage[a[c] + ((a[c] >> 5) << 1)] = static_cast<uint16_t>(row0 + static_cast<uint32_t>(bit));
+                        ++a[c];
+                    }
                 }
             }
         }
@@ -245,8 +275,20 @@ __device__ __forceinline__ uint32_t sel_write_tile(const uint32_t* mk, uint32_t 
         const uint64_t room = capacity > off ? capacity - off : 0u;
         const uint32_t lim = room < total ? static_cast<uint32_t>(room) : total;
         const uint32_t first = (blk0 + static_cast<uint32_t>(k)) * 1024u;
-        for (uint32_t q = static_cast<uint32_t>(lane); q < lim; q += 32u)
-            pos[off + q] = first + stage[q + ((q >> 5) << 1)];
+        // copy out 128 positions per step: the four stage loads first, then the stores
+        for (uint32_t q0 = 0; q0 < lim; q0 += 128u) {
+            uint32_t v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint32_t q = q0 + 32u * u + static_cast<uint32_t>(lane);
+                v[u] = q < lim ? stage[q + ((q >> 5) << 1)] : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint32_t q = q0 + 32u * u + static_cast<uint32_t>(lane);
+                if (q < lim) pos[off + q] = first + v[u];
+            }
+        }
         __syncwarp();
         off += total;
     }
@@ -263,7 +305,7 @@ __global__ void __launch_bounds__(kSelWarps * 32, 1) k_select(const SelectParams
     __shared__ uint32_t grid_tot[kSelRing], grid_before[kSelRing], grid_seq[kSelRing];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char* slots = smem + static_cast<size_t>(warp) * kSelStages * S::kTileBytes;
-    uint32_t* masks = reinterpret_cast<uint32_t*>(smem + S::kDataBytes) + warp * (kSelLag + 1) * S::kTB * 32;
+    uint32_t* masks = reinterpret_cast<uint32_t*>(smem + S::kDataBytes) + warp * (kSelLag + 1) * S::kIB * 32;
     uint16_t* stage = reinterpret_cast<uint16_t*>(smem + S::kDataBytes + S::kMaskBytes) + warp * kSelStageHalfs;
     uint64_t* bars =
         reinterpret_cast<uint64_t*>(smem + S::kDataBytes + S::kMaskBytes + S::kStageBytes) + warp * kSelStages;
@@ -289,6 +331,11 @@ __global__ void __launch_bounds__(kSelWarps * 32, 1) k_select(const SelectParams
         const uint64_t left = nblocks - static_cast<uint64_t>(t) * S::kTB;
         return left < S::kTB ? static_cast<uint32_t>(left) : static_cast<uint32_t>(S::kTB);
     };
+    // q-th tile of this warp: iteration q / M, tile q % M of the warp's run
+    // (increasing in q, so once past the last tile every later q is too)
+    auto tile_of = [&](uint32_t q) -> uint64_t {
+        return (static_cast<uint64_t>(q / S::kM) * GW + gw) * S::kM + q % S::kM;
+    };
     auto issue = [&](uint32_t t, int s) {
         const uint32_t bytes = tile_blocks(t) * S::kBlockBytes;
         mbar_arrive_expect_tx(&bars[s], bytes);
@@ -297,7 +344,7 @@ __global__ void __launch_bounds__(kSelWarps * 32, 1) k_select(const SelectParams
     };
     if (lane == 0) {
         for (int s = 0; s < kSelStages; ++s) {
-            const uint64_t t = gw + static_cast<uint64_t>(s) * GW;
+            const uint64_t t = tile_of(static_cast<uint32_t>(s));
             if (t < ntiles) issue(static_cast<uint32_t>(t), s);
         }
     }
@@ -324,9 +371,12 @@ __global__ void __launch_bounds__(kSelWarps * 32, 1) k_select(const SelectParams
         }
         // ---------------------------------------------------- count pass (i)
         if (i < p.niter) {
-            const uint32_t t = gw + i * GW;
             uint32_t cnt = 0;
-            if (t < ntiles) {
+            uint32_t* mk = masks + (i % (kSelLag + 1)) * S::kIB * 32;
+#pragma unroll 1
+            for (uint32_t m = 0; m < static_cast<uint32_t>(S::kM); ++m) {
+                const uint64_t t = tile_of(i * S::kM + m);
+                if (t >= ntiles) break;
                 const int s = static_cast<int>(consumed % kSelStages);
                 const uint32_t parity = (consumed / kSelStages) & 1u;
                 const bool ok = mbar_wait(&bars[s], parity, p.wait_limit_ns);
@@ -334,25 +384,25 @@ __global__ void __launch_bounds__(kSelWarps * 32, 1) k_select(const SelectParams
                     failed = true;
                     break;
                 }
-                const uint32_t nb = tile_blocks(t);
+                const uint32_t nb = tile_blocks(static_cast<uint32_t>(t));
                 const uint32_t* tw = reinterpret_cast<const uint32_t*>(slots + s * S::kTileBytes);
-                uint32_t* mk = masks + (i % (kSelLag + 1)) * S::kTB * 32;
 #pragma unroll 1
                 for (uint32_t k = 0; k < nb; ++k) {
-                    const uint64_t blk = static_cast<uint64_t>(t) * S::kTB + k;
+                    const uint64_t blk = t * S::kTB + k;
                     const uint32_t limit = (tail && blk == nblocks - 1) ? tail : 1024u;
                     const uint32_t pm = sel_block_mask<B>(tw + k * 32u * B, lane, p.lo, p.wm1, limit);
-                    mk[k * 32 + lane] = pm;
+                    mk[(m * S::kTB + k) * 32 + lane] = pm;
                     cnt += static_cast<uint32_t>(__popc(pm));
                 }
                 __syncwarp();
+                const uint64_t tn = tile_of(consumed + kSelStages);
                 ++consumed;
-                const uint64_t tn = t + static_cast<uint64_t>(kSelStages) * GW;
                 if (lane == 0 && tn < ntiles) {
                     fence_proxy_async_smem();
                     issue(static_cast<uint32_t>(tn), s);
                 }
             }
+            if (failed) break;
 #pragma unroll
             for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(kFull, cnt, o);
             if (lane == 0) {
@@ -452,11 +502,13 @@ __global__ void __launch_bounds__(kSelWarps * 32, 1) k_select(const SelectParams
             const volatile uint32_t* cc = cta_cnt[wi % kSelRing];
             uint32_t off = base + before;
             for (int w = 0; w < warp; ++w) off += cc[w];
-            const uint32_t t = gw + wi * GW;
-            if (t < ntiles && off < p.capacity) {
-                const uint32_t* mk = masks + (wi % (kSelLag + 1)) * S::kTB * 32;
-                sel_write_tile<S::kTB, BRANCHY>(mk, tile_blocks(t), t * static_cast<uint32_t>(S::kTB), lane, off,
-                                                p.pos, p.capacity, stage, T);
+            const uint64_t blk0 = tile_of(wi * S::kM) * S::kTB;  // the iteration's blocks are consecutive
+            if (blk0 < nblocks && off < p.capacity) {
+                const uint32_t* mk = masks + (wi % (kSelLag + 1)) * S::kIB * 32;
+                const uint64_t left = nblocks - blk0;
+                const uint32_t nb = left < S::kIB ? static_cast<uint32_t>(left) : static_cast<uint32_t>(S::kIB);
+                sel_write_tile<S::kIB, BRANCHY>(mk, nb, static_cast<uint32_t>(blk0), lane, off, p.pos, p.capacity,
+                                                stage, T);
             }
             base += tot;
         }
@@ -465,10 +517,9 @@ __global__ void __launch_bounds__(kSelWarps * 32, 1) k_select(const SelectParams
         if (lane == 0) atomicOr(p.status, kSelSelectErr);
         // Let this warp's copies still in flight land before shared memory
         // goes away: ring positions consumed .. consumed + stages - 1 that name a tile.
-        const uint32_t mine = gw < ntiles ? (ntiles - 1u - gw) / GW + 1u : 0u;
         for (uint32_t j = 0; j < static_cast<uint32_t>(kSelStages); ++j) {
             const uint32_t jt = consumed + j;
-            if (jt >= mine) break;
+            if (tile_of(jt) >= ntiles) break;
             mbar_wait(&bars[jt % kSelStages], (jt / kSelStages) & 1u, kDrainLimitNs);
         }
         return;
