@@ -3,8 +3,8 @@
 // (paper §3 lists "a materializing select" beside the count aggregates; §4
 // "Branch" is where its branchy and predicated forms part ways).
 //
-// One persistent, co-resident grid (one CTA of 8 warps per SM).  Each warp
-// streams its own tiles through a 3-stage ring of bulk copies.  The output
+// One persistent, co-resident grid (one CTA of 16 warps per SM).  Each warp
+// streams its own tiles through a ring of two or three bulk copies.  The output
 // order needs every tile's offset, i.e. the number of matches in all earlier
 // tiles, so the work runs in iterations: in iteration i warp gw owns the M
 // consecutive tiles starting at tile (i*GW + gw)*M (GW = warps in the grid;
@@ -56,8 +56,11 @@ struct SelectParams {
     int32_t silent_cta;           // -1; a self-test names a CTA that never publishes
 };
 
-constexpr int kSelWarps = 8;
-constexpr int kSelStages = 3;   // data ring per warp (a slot is refilled right after its count pass)
+// 16 warps per CTA (four per scheduler): the count and write passes are
+// chains of dependent ALU and shuffle steps, and more resident warps hide
+// their latency.  That leaves ~14 KB of shared memory per warp.
+constexpr int kSelWarps = 16;
+constexpr int kSelTileBytes = 4096;  // data of one bulk copy, at most
 constexpr int kSelLag = 3;      // a tile is written kSelLag iterations after it was counted
 constexpr int kSelRing = 8;     // CTA count ring; must be >= 2 * kSelLag + 2
 constexpr uint32_t kSelSelectErr = 1u;  // same bit as kErrTimeout
@@ -66,46 +69,63 @@ static_assert(kSelRing >= 2 * kSelLag + 2, "a CTA count slot is reused before ev
 // after every 32, so that the 32 rows' writes at 32r + j fall in distinct banks.
 constexpr int kSelStageHalfs = 1024 + 64;
 
-__host__ __device__ constexpr int sel_warp_bytes(int b, int tb, int m)
+// Shared memory of one warp: a ring of `st` tiles of tb blocks, the column
+// masks of kSelLag + 1 iterations of m tiles, the index stage, the barriers.
+__host__ __device__ constexpr int sel_warp_bytes(int b, int st, int tb, int m)
 {
-    return kSelStages * tb * 128 * b + (kSelLag + 1) * tb * m * 32 * 4 + kSelStageHalfs * 2 + kSelStages * 8;
+    return st * tb * 128 * b + (kSelLag + 1) * tb * m * 32 * 4 + kSelStageHalfs * 2 + st * 8;
 }
 
-__host__ __device__ constexpr bool sel_fits(int b, int tb, int m) { return kSelWarps * sel_warp_bytes(b, tb, m) + 1024 <= 227 * 1024; }
-
-// Blocks per warp tile (one bulk copy): at most 8 KB of data and 8 blocks,
-// shrunk until the CTA's ring, masks and stages fit the 227 KB of shared memory.
-__host__ __device__ constexpr int sel_tile_blocks(int b)
+__host__ __device__ constexpr bool sel_fits(int b, int st, int tb, int m)
 {
-    int tb = 8192 / (128 * b);
+    return kSelWarps * sel_warp_bytes(b, st, tb, m) + 1024 <= 227 * 1024;
+}
+
+// Blocks per tile for a ring of `st` slots: at most kSelTileBytes of data and
+// 8 blocks, shrunk until the CTA's rings, masks and stages fit 227 KB.
+__host__ __device__ constexpr int sel_tile_blocks_for(int b, int st)
+{
+    int tb = kSelTileBytes / (128 * b);
     tb = tb < 1 ? 1 : (tb > 8 ? 8 : tb);
-    while (tb > 1 && !sel_fits(b, tb, 1)) --tb;
+    while (tb > 1 && !sel_fits(b, st, tb, 1)) --tb;
     return tb;
 }
+
+// Ring depth per warp: three slots where they fit without shrinking the tile
+// (a slot is refilled right after its count pass), else two -- larger copies
+// measured faster than a deeper ring of smaller ones.
+__host__ __device__ constexpr int sel_stages(int b)
+{
+    return sel_fits(b, 3, 1, 1) && sel_tile_blocks_for(b, 3) >= sel_tile_blocks_for(b, 2) ? 3 : 2;
+}
+
+__host__ __device__ constexpr int sel_tile_blocks(int b) { return sel_tile_blocks_for(b, sel_stages(b)); }
 
 // Tiles per warp and iteration: up to 8 blocks in all, as many as the masks'
 // shared memory allows (wide widths have small tiles; taking several per
 // iteration divides the iterations, and their synchronisation, by as much).
 __host__ __device__ constexpr int sel_iter_tiles(int b)
 {
+    const int st = sel_stages(b);
     const int tb = sel_tile_blocks(b);
     int m = 8 / tb;
     m = m < 1 ? 1 : m;
-    while (m > 1 && !sel_fits(b, tb, m)) --m;
+    while (m > 1 && !sel_fits(b, st, tb, m)) --m;
     return m;
 }
 
 template <int B>
 struct SelShape {
     static constexpr int kBlockBytes = 128 * B;
+    static constexpr int kStages = sel_stages(B);
     static constexpr int kTB = sel_tile_blocks(B);
     static constexpr int kM = sel_iter_tiles(B);
     static constexpr int kIB = kM * kTB;  // blocks per warp and iteration
     static constexpr int kTileBytes = kTB * kBlockBytes;
-    static constexpr int kDataBytes = kSelWarps * kSelStages * kTileBytes;
+    static constexpr int kDataBytes = kSelWarps * kStages * kTileBytes;
     static constexpr int kMaskBytes = kSelWarps * (kSelLag + 1) * kIB * 32 * 4;
     static constexpr int kStageBytes = kSelWarps * kSelStageHalfs * 2;
-    static constexpr int kSmemBytes = kDataBytes + kMaskBytes + kStageBytes + kSelWarps * kSelStages * 8;
+    static constexpr int kSmemBytes = kDataBytes + kMaskBytes + kStageBytes + kSelWarps * kStages * 8;
     static_assert(kSmemBytes + 1024 <= 227 * 1024, "shared-memory budget");
     static_assert(kTileBytes % 16 == 0, "bulk copies move multiples of 16 bytes");
 };
@@ -304,11 +324,11 @@ __global__ void __launch_bounds__(kSelWarps * 32, 1) k_select(const SelectParams
     __shared__ uint32_t cta_arrive[kSelRing];
     __shared__ uint32_t grid_tot[kSelRing], grid_before[kSelRing], grid_seq[kSelRing];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    unsigned char* slots = smem + static_cast<size_t>(warp) * kSelStages * S::kTileBytes;
+    unsigned char* slots = smem + static_cast<size_t>(warp) * S::kStages * S::kTileBytes;
     uint32_t* masks = reinterpret_cast<uint32_t*>(smem + S::kDataBytes) + warp * (kSelLag + 1) * S::kIB * 32;
     uint16_t* stage = reinterpret_cast<uint16_t*>(smem + S::kDataBytes + S::kMaskBytes) + warp * kSelStageHalfs;
     uint64_t* bars =
-        reinterpret_cast<uint64_t*>(smem + S::kDataBytes + S::kMaskBytes + S::kStageBytes) + warp * kSelStages;
+        reinterpret_cast<uint64_t*>(smem + S::kDataBytes + S::kMaskBytes + S::kStageBytes) + warp * S::kStages;
 
     const uint64_t nblocks = (p.n + 1023u) >> 10;
     const uint32_t ntiles = static_cast<uint32_t>((nblocks + S::kTB - 1) / S::kTB);
@@ -322,7 +342,7 @@ __global__ void __launch_bounds__(kSelWarps * 32, 1) k_select(const SelectParams
         grid_seq[threadIdx.x] = 0u;
     }
     if (lane == 0) {
-        for (int s = 0; s < kSelStages; ++s) mbar_init(&bars[s], 1);
+        for (int s = 0; s < S::kStages; ++s) mbar_init(&bars[s], 1);
         fence_mbar_init();
     }
     __syncthreads();
@@ -343,7 +363,7 @@ __global__ void __launch_bounds__(kSelWarps * 32, 1) k_select(const SelectParams
                  &bars[s]);
     };
     if (lane == 0) {
-        for (int s = 0; s < kSelStages; ++s) {
+        for (int s = 0; s < S::kStages; ++s) {
             const uint64_t t = tile_of(static_cast<uint32_t>(s));
             if (t < ntiles) issue(static_cast<uint32_t>(t), s);
         }
@@ -377,8 +397,8 @@ __global__ void __launch_bounds__(kSelWarps * 32, 1) k_select(const SelectParams
             for (uint32_t m = 0; m < static_cast<uint32_t>(S::kM); ++m) {
                 const uint64_t t = tile_of(i * S::kM + m);
                 if (t >= ntiles) break;
-                const int s = static_cast<int>(consumed % kSelStages);
-                const uint32_t parity = (consumed / kSelStages) & 1u;
+                const int s = static_cast<int>(consumed % S::kStages);
+                const uint32_t parity = (consumed / S::kStages) & 1u;
                 const bool ok = mbar_wait(&bars[s], parity, p.wait_limit_ns);
                 if (!__all_sync(kFull, ok)) {
                     failed = true;
@@ -395,7 +415,7 @@ __global__ void __launch_bounds__(kSelWarps * 32, 1) k_select(const SelectParams
                     cnt += static_cast<uint32_t>(__popc(pm));
                 }
                 __syncwarp();
-                const uint64_t tn = tile_of(consumed + kSelStages);
+                const uint64_t tn = tile_of(consumed + S::kStages);
                 ++consumed;
                 if (lane == 0 && tn < ntiles) {
                     fence_proxy_async_smem();
@@ -517,10 +537,10 @@ __global__ void __launch_bounds__(kSelWarps * 32, 1) k_select(const SelectParams
         if (lane == 0) atomicOr(p.status, kSelSelectErr);
         // Let this warp's copies still in flight land before shared memory
         // goes away: ring positions consumed .. consumed + stages - 1 that name a tile.
-        for (uint32_t j = 0; j < static_cast<uint32_t>(kSelStages); ++j) {
+        for (uint32_t j = 0; j < static_cast<uint32_t>(S::kStages); ++j) {
             const uint32_t jt = consumed + j;
             if (tile_of(jt) >= ntiles) break;
-            mbar_wait(&bars[jt % kSelStages], (jt / kSelStages) & 1u, kDrainLimitNs);
+            mbar_wait(&bars[jt % S::kStages], (jt / S::kStages) & 1u, kDrainLimitNs);
         }
         return;
     }
