@@ -1,7 +1,7 @@
 // Batched scan: thousands of columns in one CUDA-graph launch.
 //
-// The host cuts every column's 1024-value blocks into tiles (the same
-// per-width tile size as the single-column scan, at most 8 KB), groups the
+// The host cuts every column's 1024-value blocks into tiles (per width, the
+// most blocks that fill a 12 KB slot in whole warp steps), groups the
 // columns by width and numbers each group's tiles consecutively.  One
 // persistent kernel serves a group: warps pop chunks of consecutive tile
 // numbers from the group's atomic counter (a host-built table gives each
@@ -74,9 +74,16 @@ struct CountSum {
     uint64_t cnt, sum;
 };
 
+// The consumer's copy of its column's descriptor (what decoding a slot needs).
+struct ConsCol {
+    uint32_t lo, wm1;  // predicate in code space
+    uint32_t tail;     // values in the column's last block (0: whole)
+    uint32_t b;
+};
+
 template <int B, bool BRANCHY>
 __device__ __forceinline__ CountSum batch_consume_body(const unsigned char* slot, const SlotMeta m,
-                                                       const BatchCol& c, int lane)
+                                                       const ConsCol& c, int lane)
 {
     uint64_t cnt = 0, sum = 0;
     const Lanes L = make_lanes<B>(c.lo, c.wm1);
@@ -85,21 +92,21 @@ __device__ __forceinline__ CountSum batch_consume_body(const unsigned char* slot
     if (m.tail) {
         const int q = lane % Geo<B>::kTpb;
         agg_block_masked<B>(block_rows<B>(slot + nfull * (128u * B), q), c.lo, c.wm1, cnt, sum,
-                            lane < Geo<B>::kTpb, static_cast<uint32_t>(c.n & 1023u), q);
+                            lane < Geo<B>::kTpb, c.tail, q);
     }
     return CountSum{cnt, sum};
 }
 
 template <int B, bool BRANCHY>
 __device__ __noinline__ CountSum batch_consume_b(const unsigned char* slot, const SlotMeta m,
-                                                 const BatchCol& c, int lane)
+                                                 const ConsCol& c, int lane)
 {
     return batch_consume_body<B, BRANCHY>(slot, m, c, lane);
 }
 
 template <bool BRANCHY, int LO, int HI>
 __device__ __forceinline__ CountSum batch_consume_range(int b, const unsigned char* slot,
-                                                        const SlotMeta m, const BatchCol& c, int lane)
+                                                        const SlotMeta m, const ConsCol& c, int lane)
 {
     if constexpr (LO > HI) {
         return CountSum{0, 0};
@@ -128,10 +135,31 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 1) k_scan_batch(const BatchP
     }
     __syncwarp();
 
-    // producer cursor (warp-uniform)
+    // producer cursor (warp-uniform) and the descriptor of its column, kept in
+    // registers: a warp's tiles come in runs of one column, so the descriptor
+    // and the next column's first tile are loaded once per run, not per tile
     uint32_t t_next = 0, t_end = 0, col = 0;
     bool exhausted = false;
     uint32_t phase = 0;  // bit s: parity of slot s's next completion
+    uint32_t pc_id = ~0u, next_begin = 0;
+    const uint32_t* pc_packed = nullptr;
+    const uint2* pc_zm = nullptr;
+    uint64_t pc_n = 0, pc_zlo = 0, pc_zhi = 0;
+    uint32_t pc_b = 0, pc_begin = 0, pc_tb = 0, pc_flags = 0;
+    auto load_col = [&](uint32_t c) {
+        const BatchCol* d = P.cols + c;
+        pc_packed = d->packed;
+        pc_zm = d->zonemap;
+        pc_n = d->n;
+        pc_b = BFIX > 0 ? static_cast<uint32_t>(BFIX) : d->b;
+        pc_begin = d->tile_begin;
+        pc_tb = d->tile_blocks;
+        pc_flags = d->flags;
+        pc_zlo = d->zlo;
+        pc_zhi = d->zhi;
+        next_begin = c + 1 < P.ncols ? __ldg(&P.cols[c + 1].tile_begin) : 0xffffffffu;
+        pc_id = c;
+    };
 
     // Next tile number, or false when the launch has no more work.
     auto next_tile = [&](uint32_t& t) -> bool {
@@ -157,9 +185,10 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 1) k_scan_batch(const BatchP
                 }
                 col = lo;
             }
+            if (col != pc_id) load_col(col);
         }
         t = t_next++;
-        while (col + 1 < P.ncols && __ldg(&P.cols[col + 1].tile_begin) <= t) ++col;
+        while (next_begin <= t) load_col(++col);  // the last column's next_begin is past every tile
         return true;
     };
 
@@ -167,24 +196,23 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 1) k_scan_batch(const BatchP
     auto produce = [&](int s) -> bool {
         uint32_t t;
         if (!next_tile(t)) return false;
-        const BatchCol& c = P.cols[col];
-        const uint32_t bb = 128u * c.b;
-        const uint64_t nblocks = (c.n + 1023u) >> 10;
-        const uint64_t k0 = static_cast<uint64_t>(t - c.tile_begin) * c.tile_blocks;
+        const uint32_t bb = 128u * pc_b;
+        const uint64_t nblocks = (pc_n + 1023u) >> 10;
+        const uint64_t k0 = static_cast<uint64_t>(t - pc_begin) * pc_tb;
         const uint64_t left = nblocks - k0;
-        const uint32_t nb = left < c.tile_blocks ? static_cast<uint32_t>(left) : c.tile_blocks;
-        const bool has_tail = (c.n & 1023u) && (k0 + nb == nblocks);
+        const uint32_t nb = left < pc_tb ? static_cast<uint32_t>(left) : pc_tb;
+        const bool has_tail = (pc_n & 1023u) && (k0 + nb == nblocks);
         uint64_t keep = (nb >= 64) ? ~0ull : ((1ull << nb) - 1ull);
-        if (c.flags & kColEmpty) {
+        if (pc_flags & kColEmpty) {
             keep = 0;
-        } else if (c.flags & kColZone) {
+        } else if (pc_flags & kColZone) {
             uint64_t km = 0;
             for (uint32_t base_i = 0; base_i < nb; base_i += 32u) {
                 const uint32_t i = base_i + lane;
                 bool k = false;
                 if (i < nb) {
-                    const uint2 z = __ldg(&c.zonemap[k0 + i]);
-                    k = static_cast<uint64_t>(z.y) >= c.zlo && static_cast<uint64_t>(z.x) < c.zhi;
+                    const uint2 z = __ldg(&pc_zm[k0 + i]);
+                    k = static_cast<uint64_t>(z.y) >= pc_zlo && static_cast<uint64_t>(z.x) < pc_zhi;
                 }
                 km |= static_cast<uint64_t>(__ballot_sync(kFull, k)) << base_i;
             }
@@ -209,7 +237,7 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 1) k_scan_batch(const BatchP
                     const uint64_t from = rem >> first;
                     const uint32_t len = (~from == 0ull) ? (64u - first)
                                                           : static_cast<uint32_t>(__ffsll(static_cast<long long>(~from)) - 1);
-                    bulk_g2s(dst + placed * bb, c.packed + (k0 + first) * 32u * c.b, len * bb, &bars[s]);
+                    bulk_g2s(dst + placed * bb, pc_packed + (k0 + first) * 32u * pc_b, len * bb, &bars[s]);
                     placed += len;
                     rem &= (len + first >= 64u) ? 0ull : (~0ull << (first + len));
                 }
@@ -227,6 +255,8 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 1) k_scan_batch(const BatchP
 
     uint64_t cnt = 0, sum = 0, blocks = 0;
     int cur = -1;
+    ConsCol cc{0u, 0u, 0u, 0u};   // the consumer's column (loaded when it changes)
+    uint32_t cur_out = 0, cur_base = 0;
     auto flush = [&]() {
         uint64_t c2 = cnt, s2 = sum;
 #pragma unroll
@@ -235,10 +265,9 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 1) k_scan_batch(const BatchP
             s2 += __shfl_xor_sync(kFull, s2, o);
         }
         if (lane == 0 && cur >= 0) {
-            const BatchCol& c = P.cols[cur];
-            unsigned long long* r = P.results + 4u * c.out;
+            unsigned long long* r = P.results + 4u * cur_out;
             if (c2) atomicAdd(&r[0], static_cast<unsigned long long>(c2));
-            if (c2) atomicAdd(&r[1], static_cast<unsigned long long>(s2 + static_cast<uint64_t>(c.base) * c2));
+            if (c2) atomicAdd(&r[1], static_cast<unsigned long long>(s2 + static_cast<uint64_t>(cur_base) * c2));
             if (blocks) atomicAdd(&r[2], static_cast<unsigned long long>(blocks));
         }
         cnt = 0;
@@ -255,6 +284,13 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 1) k_scan_batch(const BatchP
         if (static_cast<int>(m.col) != cur) {
             flush();
             cur = static_cast<int>(m.col);
+            const BatchCol* d = P.cols + m.col;
+            cc.lo = d->lo;
+            cc.wm1 = d->wm1;
+            cc.tail = static_cast<uint32_t>(d->n & 1023u);
+            cc.b = BFIX > 0 ? static_cast<uint32_t>(BFIX) : d->b;
+            cur_out = d->out;
+            cur_base = d->base;
         }
         if (m.nk) {
             const bool ok = mbar_wait(&bars[s], (phase >> s) & 1u, kWaitLimitNs);
@@ -263,12 +299,11 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 1) k_scan_batch(const BatchP
                 break;
             }
             phase ^= 1u << s;
-            const BatchCol& c = P.cols[m.col];
             CountSum r;
             if constexpr (BFIX > 0)
-                r = batch_consume_body<BFIX, BRANCHY>(slots + s * kBatchSlot, m, c, lane);
+                r = batch_consume_body<BFIX, BRANCHY>(slots + s * kBatchSlot, m, cc, lane);
             else
-                r = batch_consume_range<BRANCHY, 1, 32>(static_cast<int>(c.b), slots + s * kBatchSlot, m, c,
+                r = batch_consume_range<BRANCHY, 1, 32>(static_cast<int>(cc.b), slots + s * kBatchSlot, m, cc,
                                                         lane);
             cnt += r.cnt;
             sum += r.sum;

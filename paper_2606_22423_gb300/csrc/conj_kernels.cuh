@@ -31,13 +31,14 @@ enum ConjMode : int { kConjFirst = 0, kConjAnd = 1, kConjAgg = 2 };
 
 // Staging shape: a tile is kTB blocks of data (128*B bytes each) followed by
 // their selection words (128 bytes each), both brought in by bulk copies on
-// one transaction barrier, at most ~8 KB per slot.
+// one transaction barrier, at most ~4 KB per slot; 16 warps per CTA, so that
+// four warps per scheduler hide the latency of the decode's dependent steps.
 template <int B>
 struct ConjShape {
-    static constexpr int kWarps = 8;
+    static constexpr int kWarps = 16;
     static constexpr int kStages = 3;
     static constexpr int kBlockBytes = 128 * B;
-    static constexpr int kRaw = 8192 / (kBlockBytes + 128);
+    static constexpr int kRaw = 4096 / (kBlockBytes + 128);
     static constexpr int kTB = kRaw < 1 ? 1 : (kRaw > 64 ? 64 : kRaw);
     static constexpr int kDataBytes = kTB * kBlockBytes;
     static constexpr int kTileBytes = kDataBytes + kTB * 128;
