@@ -470,6 +470,7 @@ def run_ours(args, world, rank, local):
     # the per-feature sections describe one GPU; a multi-GPU (replica) run reports the sweep only
     extra = not args.no_extra and world == 1
     plain = run_plain(args, dev, stream, gbscan, beta_read) if extra else None
+    probes = run_probes(args, dev, stream, gbscan, beta_read, law) if extra else None
     select = run_select(args, dev, stream, gbscan, peaks().get("hbm_gbs", 6800.0)) if extra else None
     layouts = run_layouts(args, dev, stream, gbscan, beta_read) if extra else None
     conj = run_conj(args, dev, stream, gbscan, peaks().get("hbm_gbs", 6800.0)) if extra else None
@@ -494,6 +495,7 @@ def run_ours(args, world, rank, local):
         "per_b": per_b,
         "branch_crossover": branch,
         "plain_scan": plain,
+        "probes": probes,
         "zone_sweep": zone,
         "select": select,
         "layouts": layouts,
@@ -782,6 +784,73 @@ def run_select(args, dev, stream, gbscan, hbm_gbs):
     torch.cuda.empty_cache()
     out["exact"] = all(r["exact"] for r in out["rows"])
     return out
+
+
+def run_probes(args, dev, stream, gbscan, beta_read, law):
+    """The two other probes of the paper's setup (§3): STREAM triad, and the
+    decode rate with the column resident in L2, i.e. T_dec measured directly
+    rather than fitted from the sweep.
+      triad : a = b + s*c over three 1 GiB float32 arrays, 12 bytes per element,
+              best of 10 after 3 warm-ups (CUDA events on the launching stream).
+      decode: per width b, a column of N values (64 MiB packed: in L2 after the
+              first launch, and ~6.7 of the scan's 8 KB tiles per warp) and its
+              first N/2 values are each scanned warm, branch-free, sigma = 0.1, as
+              a CUDA graph of 20 launches; T_dec,resident(b) = (N/2) / (t(N) -
+              t(N/2)): the slope, so the fixed cost of a launch cancels."""
+    import torch
+
+    n = 1 << 28
+    ta = torch.empty(n, dtype=torch.float32, device=dev)
+    tb = torch.full((n,), 1.0, dtype=torch.float32, device=dev)
+    tc = torch.full((n,), 2.0, dtype=torch.float32, device=dev)
+    torch.cuda.synchronize()
+    best = 0.0
+    with torch.cuda.stream(stream):
+        for i in range(13):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            gbscan.scan_probe_triad(ta, tb, tc, 3.0, n, stream)
+            e1.record(stream)
+            e1.synchronize()
+            if i >= 3:
+                best = max(best, 12 * n / (e0.elapsed_time(e1) * 1e-3) / 1e9)
+    triad_ok = bool((ta[:: 1 << 16] == 7.0).all().item()) and float(ta[-1].item()) == 7.0
+    del ta, tb, tc
+    torch.cuda.empty_cache()
+
+    res = torch.zeros(4, dtype=torch.int64, device=dev)
+    per_b = {}
+    for b in WIDTHS:
+        n2 = ((64 << 23) // b) // 2048 * 2048
+        n1 = n2 // 2
+        with torch.cuda.stream(stream):
+            v = synth.uniform_values_device(synth.seed_for(20, b), n2, b, device=dev)
+            col = gbscan.Column.from_device(v, n2, b, stream=stream)
+            del v
+        torch.cuda.synchronize()
+        part = gbscan.Column.from_packed(col.dev_packed, n1, b, stream=stream)
+        lo, hi = synth.pick_range(synth.seed_for(20, b, 1), b, 0.1)
+        t2 = _graph_time(lambda: col.run_async(lo, hi, res, "branchfree", stream), stream)
+        t1 = _graph_time(lambda: part.run_async(lo, hi, res, "branchfree", stream), stream)
+        col.status(stream)
+        part.close()
+        col.close()
+        dt = max(t2 - t1, 1e-9)
+        per_b[b] = {"n": n2, "us_n": round(t2 * 1e3, 2), "us_half": round(t1 * 1e3, 2),
+                    "gvals_per_s": round((n2 - n1) / (dt * 1e-3) / 1e9, 1),
+                    "l2_gbs": round((n2 - n1) * b / 8 / (dt * 1e-3) / 1e9, 1)}
+    torch.cuda.empty_cache()
+    fitted = law["branchfree"]["t_dec_gvals"]
+    ridge = law["branchfree"]["b_star"]
+    below = [per_b[b]["gvals_per_s"] for b in WIDTHS if b < ridge]
+    med = statistics.median(below) if below else None
+    return {"triad": {"workload": "STREAM triad a = b + 3c over 2^28 float32 (3 GiB), best of 10",
+                      "gbs": round(best, 1), "beta_read_gbs": round(beta_read, 1), "exact": triad_ok},
+            "decode_resident": {"workload": "branch-free scan of an L2-resident column per b (64 MiB packed), "
+                                            "sigma = 0.1, slope between N and N/2 values, CUDA graphs of 20 launches",
+                                "per_b": per_b, "t_dec_median_below_ridge_gvals": med,
+                                "t_dec_fitted_gvals": fitted, "b_star_fitted": ridge,
+                                "resident_over_fitted": round(med / fitted, 3) if med and fitted else None}}
 
 
 def run_plain(args, dev, stream, gbscan, beta_read):

@@ -445,6 +445,17 @@ scan_status scan_run_packed_noalloc(const uint32_t *dev_packed, uint64_t n, uint
  * is read once and folded into a checksum written to *dev_out (8 bytes). */
 scan_status scan_probe_read(const void *dev_buf, uint64_t bytes, void *stream, uint64_t *dev_out);
 
+/* STREAM triad (paper §3 measures beta per machine as STREAM-Triad as well as
+ * the read maximum): dev_a[i] = dev_b[i] + s * dev_c[i] for i < n, each
+ * element computed as one fused multiply-add.  All three arrays are caller-
+ * owned device memory, 16-byte aligned; n is a multiple of 4 (n = 0 does
+ * nothing and accepts NULL arrays).  12 bytes move per element.
+ * Asynchronous on `stream`.
+ * Errors: SCAN_EINVAL for NULL or misaligned arrays or n not a multiple of 4;
+ * SCAN_ECUDA if the launch fails. */
+scan_status scan_probe_triad(float *dev_a, const float *dev_b, const float *dev_c, float s, uint64_t n,
+                             void *stream);
+
 /* Failure-path check: one warp waits, with the same bounded wait every
  * pipeline uses, on a transaction barrier nothing ever completes.  The wait
  * gives up after limit_ns (at most 1 s) and the call returns SCAN_ETIMEOUT;

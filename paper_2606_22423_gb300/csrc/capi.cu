@@ -364,6 +364,31 @@ __global__ void k_selftest_wait(unsigned long long limit_ns, unsigned int* statu
     if (!__all_sync(gb::kFull, ok) && threadIdx.x == 0) atomicOr(status, gb::kErrTimeout);
 }
 
+// STREAM triad a = b + s*c over float4 vectors (streaming loads and stores,
+// four vectors per thread in flight).
+__global__ void k_triad_probe(float4* __restrict__ a, const float4* __restrict__ b, const float4* __restrict__ c,
+                              float s, uint64_t n4)
+{
+    const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+    uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    for (; i + 3 * stride < n4; i += 4 * stride) {
+        float4 x[4], y[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            x[u] = __ldcs(b + i + u * stride);
+            y[u] = __ldcs(c + i + u * stride);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            __stcs(a + i + u * stride, make_float4(fmaf(s, y[u].x, x[u].x), fmaf(s, y[u].y, x[u].y),
+                                                   fmaf(s, y[u].z, x[u].z), fmaf(s, y[u].w, x[u].w)));
+    }
+    for (; i < n4; i += stride) {
+        const float4 x = __ldcs(b + i), y = __ldcs(c + i);
+        __stcs(a + i, make_float4(fmaf(s, y.x, x.x), fmaf(s, y.y, x.y), fmaf(s, y.z, x.z), fmaf(s, y.w, x.w)));
+    }
+}
+
 __global__ void k_read_probe(const uint4* __restrict__ p, uint64_t n16, unsigned long long* out)
 {
     const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
@@ -932,6 +957,23 @@ scan_status scan_probe_read(const void* dev_buf, uint64_t bytes, void* stream, u
     const int grid = persistent_grid() * 4;
     k_read_probe<<<grid, 512, 0, st>>>(static_cast<const uint4*>(dev_buf), bytes / 16,
                                        reinterpret_cast<unsigned long long*>(dev_out));
+    GB_CUDA(cudaGetLastError());
+    return SCAN_OK;
+}
+
+scan_status scan_probe_triad(float* dev_a, const float* dev_b, const float* dev_c, float s, uint64_t n,
+                             void* stream)
+{
+    g_err.clear();
+    if (n == 0) return SCAN_OK;  // nothing to touch (empty arrays may be NULL)
+    if (!dev_a || !dev_b || !dev_c) return fail(SCAN_EINVAL, "null pointer");
+    if (((reinterpret_cast<uintptr_t>(dev_a) | reinterpret_cast<uintptr_t>(dev_b) |
+          reinterpret_cast<uintptr_t>(dev_c)) & 15u) || (n & 3u))
+        return fail(SCAN_EINVAL, "arrays must be 16-byte aligned and n a multiple of 4");
+    cudaStream_t st = as_stream(stream);
+    const int grid = persistent_grid() * 4;
+    k_triad_probe<<<grid, 512, 0, st>>>(reinterpret_cast<float4*>(dev_a), reinterpret_cast<const float4*>(dev_b),
+                                        reinterpret_cast<const float4*>(dev_c), s, n / 4);
     GB_CUDA(cudaGetLastError());
     return SCAN_OK;
 }

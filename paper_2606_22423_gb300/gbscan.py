@@ -84,6 +84,7 @@ SIGNATURES = {
     "scan_conj_async": (_st, [_vp, _vp, _u32, _vp, _st, _vp, _vp]),
     "scan_select_async": (_st, [_vp, scan_pred, _st, _vp, _u64, _vp, _vp]),
     "scan_probe_read": (_st, [_vp, _u64, _vp, _vp]),
+    "scan_probe_triad": (_st, [_vp, _vp, _vp, ctypes.c_float, _u64, _vp]),
     "scan_launch_shape": (_st, [_u32] + [ctypes.POINTER(_u32)] * 5),
     "scan_selftest_wait_timeout": (_st, [_u64, _vp]),
     "scan_run_packed_noalloc": (_st, [_vp, _u64, _u32, _u32, scan_pred, _st, _vp, _vp, _vp]),
@@ -189,6 +190,11 @@ def scan_encode_device(dev_values, n: int, b: int, base: int, dev_out, stream=No
 
 def scan_probe_read(dev_buf, nbytes: int, dev_out, stream=None):
     _check(load().scan_probe_read(_ptr(dev_buf), nbytes, _stream(stream), _ptr(dev_out)))
+
+
+def scan_probe_triad(dev_a, dev_b, dev_c, s: float, n: int, stream=None):
+    """STREAM triad a = b + s*c over n float32 elements (device arrays)."""
+    _check(load().scan_probe_triad(_ptr(dev_a), _ptr(dev_b), _ptr(dev_c), float(s), n, _stream(stream)))
 
 
 def scan_run_packed_noalloc(dev_packed, n: int, b: int, base: int, lo: int, hi: int, dev_out,

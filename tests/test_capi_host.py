@@ -101,3 +101,14 @@ def test_launch_shapes_fit_shared_memory(lib):
         assert tb % step == 0 and tb >= step
         assert tb * 128 * b <= 8 * 1024      # a tile fits one 8 KB slot
         assert warps * stages * tb * 128 * b <= 227 * 1024
+
+
+def test_triad_probe_rejects_bad_arguments(lib):
+    """Argument checks run before any CUDA call: misaligned arrays, n not a
+    multiple of 4 and NULL arrays are refused (the pointers are never touched)."""
+    for a, b, c, n, why in [(0x1000, 0x2000, 0x3000, 6, "multiple of 4"), (0x1004, 0x2000, 0x3000, 8, "aligned"),
+                            (0x1000, 0x2008, 0x3000, 8, "aligned"), (None, 0x2000, 0x3000, 8, "null")]:
+        with pytest.raises(gbscan.ScanError) as e:
+            gbscan.scan_probe_triad(a, b, c, 3.0, n)
+        assert e.value.status == gbscan.SCAN_EINVAL
+        assert why in str(e.value)
