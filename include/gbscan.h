@@ -412,10 +412,10 @@ scan_status scan_server_destroy(scan_server *server);
 /* The paper has no counterpart to this call; it is an integration aid.
  * The same fused full scan as scan_run_async on a caller-owned packed buffer
  * (scan_packed_words(n, b) words, 16-byte aligned), for callers that cannot
- * allocate device memory when they scan: code running inside CUDA graph
- * capture (cudaMalloc cannot be captured), latency-bound loops that must not
- * take the allocator's implicit synchronisation, and engines that manage a
- * fixed memory budget themselves.  It calls no cudaMalloc/cudaFree and no
+ * allocate device memory when they scan: latency-bound loops that must not
+ * take the allocator's implicit synchronisation, engines that manage a fixed
+ * memory budget through their own sub-allocator, and plug-ins whose host
+ * process owns the device memory.  It calls no cudaMalloc/cudaFree and no
  * allocating library routine.  Its grid-reduction scratch is a statically
  * sized device array of 16 KiB + 64 bytes inside this library (room for 1024
  * CTAs, one per SM), held by every GPU that loads the library until exit; a

@@ -1,12 +1,13 @@
 // Allocation-free scan entry point.
 //
-// Some callers cannot call cudaMalloc at scan time: code that runs while a
-// CUDA graph is being captured (allocation calls are not capturable), latency
-// critical serving loops that must not take the allocator's implicit device
-// synchronisation, and engines that own a fixed memory budget with their own
-// sub-allocator.  For them this file keeps the full scan's grid-reduction
-// scratch (one (count, sum) pair per CTA plus the last-CTA ticket) in a
-// statically sized device array instead of a per-column workspace.
+// Some callers cannot call cudaMalloc at scan time: latency-critical serving
+// loops that must not take the allocator's implicit device synchronisation,
+// engines that own a fixed memory budget and hand out memory only through
+// their own sub-allocator, and plug-ins hosted by a process whose device
+// memory belongs to another runtime.  For them this file keeps the full
+// scan's grid-reduction scratch (one (count, sum) pair per CTA plus the
+// last-CTA ticket) in a statically sized device array instead of a per-column
+// workspace.
 //
 // The array lives at file scope, so every GPU that loads the library holds it
 // until the process exits.  Host code cannot use its name as a device

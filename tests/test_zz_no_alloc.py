@@ -1,7 +1,8 @@
 """The allocation-free scan entry point (scan_run_packed_noalloc).
 
-It serves callers that cannot allocate device memory while they scan (graph
-capture, allocator-free serving loops, fixed-budget engines).  Its result
+It serves callers that cannot allocate device memory while they scan
+(allocator-free serving loops, fixed-budget engines, plug-ins whose host owns
+the device memory).  Its result
 must equal the regular entry point's, exactly, on consecutive calls that
 reuse the shared static scratch.  This file is collected last on purpose.
 """
