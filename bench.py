@@ -158,22 +158,55 @@ def traffic_from_profile(b_lo=16):
 
 
 # ============================================================ CPU / oracle
-def cpu_sample_gbs(columns_host, threads, budget_s=12.0):
-    """Oracle (threaded) on prefixes of the sweep columns at sigma = 0.1."""
+def cpu_model() -> str:
+    """The host CPU as /proc/cpuinfo names it (Arm hosts give implementer/part codes)."""
+    try:
+        txt = open("/proc/cpuinfo").read()
+    except OSError:
+        return "unknown"
+    for line in txt.splitlines():
+        if line.lower().startswith(("model name", "hardware")):
+            return line.split(":", 1)[1].strip()
+    impl = part = None
+    for line in txt.splitlines():
+        if line.startswith("CPU implementer") and impl is None:
+            impl = line.split(":", 1)[1].strip()
+        if line.startswith("CPU part") and part is None:
+            part = line.split(":", 1)[1].strip()
+    names = {("0x41", "0xd4f"): "Arm Neoverse V2", ("0x41", "0xd40"): "Arm Neoverse V1"}
+    return names.get((impl, part), f"Arm implementer {impl} part {part}")
+
+
+def cpu_sample(columns_host, threads, budget_s, passes_max=3):
+    """The oracle over prefixes of the sweep columns: sigma-outer, b-inner passes over
+    SIGMAS (the sweep's order) until the time budget is spent (at least one pass).
+    Returns GB/s of packed bytes, values/s, scans, seconds and per-width values/s."""
     import oracle
 
-    total_bytes, t_used, scans = 0, 0.0, 0
-    for b, words in columns_host:
-        lo, hi = pred_for(b, 0.1)
-        n = words.size // b * 32  # values covered by these whole blocks
-        t0 = time.perf_counter()
-        oracle.scan_packed_threads(words, n, b, 0, lo, hi, threads)
-        t_used += time.perf_counter() - t0
-        total_bytes += n * b / 8
-        scans += 1
+    total_bytes, total_vals, t_used, scans = 0, 0, 0.0, 0
+    per_b = {}
+    for _ in range(passes_max):
+        for s in SIGMAS:
+            for b, words in columns_host:
+                lo, hi = pred_for(b, s)
+                n = words.size // b * 32  # values covered by these whole blocks
+                t0 = time.perf_counter()
+                if threads == 1:
+                    oracle.scan_packed(words, n, b, 0, lo, hi)
+                else:
+                    oracle.scan_packed_threads(words, n, b, 0, lo, hi, threads)
+                dt = time.perf_counter() - t0
+                t_used += dt
+                total_bytes += n * b / 8
+                total_vals += n
+                scans += 1
+                acc = per_b.setdefault(b, [0, 0.0])
+                acc[0] += n
+                acc[1] += dt
         if t_used > budget_s:
             break
-    return total_bytes / t_used / 1e9, scans, t_used
+    vps = {b: n / t for b, (n, t) in per_b.items() if t > 0}
+    return total_bytes / t_used / 1e9, total_vals / t_used, scans, t_used, vps
 
 
 def run_reference(args, world, rank):
@@ -445,24 +478,41 @@ def run_ours(args, world, rank, local):
                        "previous width's 12 scan_run_async calls; one result copy and one host sync per step"}
         del host
 
-    # ---- CPU baseline: the oracle on a bounded sample, all host cores
+    # ---- CPU baseline: the oracle on a bounded sample, all host cores and one thread
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         import oracle
 
         oracle.build()
         threads = os.cpu_count() or 1
-        sample_n = 1 << 24
-        host_cols = []
-        for b in WIDTHS:
-            words = sample_n // 1024 * 32 * b
-            t = torch.empty(words, dtype=torch.int32, device=dev)
-            cudart_copy(t, cols[b].dev_packed, words * 4)
-            host_cols.append((b, t.cpu().numpy().view(np.uint32)))
-        gbs, scans, used = cpu_sample_gbs(host_cols, threads)
+
+        def prefixes(sample_n):
+            out = []
+            for b in WIDTHS:
+                words = sample_n // 1024 * 32 * b
+                t = torch.empty(words, dtype=torch.int32, device=dev)
+                cudart_copy(t, cols[b].dev_packed, words * 4)
+                out.append((b, t.cpu().numpy().view(np.uint32)))
+            return out
+
+        host_cols = prefixes(1 << 27)
+        gbs, vps, scans, used, _ = cpu_sample(host_cols, threads, budget_s=10.0)
+        del host_cols
+        host_cols = prefixes(1 << 21)
+        gbs1, vps1, scans1, used1, per_b1 = cpu_sample(host_cols, 1, budget_s=2.0, passes_max=1)
+        del host_cols
+        low = [v for b, v in per_b1.items() if b <= 16]
         cpu = {"value": round(gbs, 3), "unit": "GB/s", "cores": threads, "kind": "oracle",
-               "sample": f"{scans} scans at sigma=0.1 over the first 2^24 values of the b=1..{host_cols[scans-1][0]} "
-                         f"columns ({used:.1f} s); oracle.scan_packed_threads"}
+               "sample": f"{scans} scans (the sweep's sigma-outer, b-inner order) over the first 2^27 values of "
+                         f"each b=1..32 column ({used:.1f} s); oracle.scan_packed_threads",
+               "cpu_model": cpu_model(),
+               "values_per_s": round(vps, 1),
+               "single_thread": {"gbs": round(gbs1, 3), "values_per_s": round(vps1, 1),
+                                 "t_dec_gvals": round(statistics.median(low) / 1e9, 3) if low else None,
+                                 "sample": f"{scans1} scans over the first 2^21 values of each b=1..32 column "
+                                           f"({used1:.1f} s); oracle.scan_packed on one thread"},
+               "t_dec_note": "the oracle decodes one value at a time and stays compute-bound at every b on "
+                             "the host, so its T_dec is its values/s (median over b <= 16, one thread)"}
 
     for c in cols.values():
         c.close()
@@ -792,11 +842,13 @@ def run_probes(args, dev, stream, gbscan, beta_read, law):
     rather than fitted from the sweep.
       triad : a = b + s*c over three 1 GiB float32 arrays, 12 bytes per element,
               best of 10 after 3 warm-ups (CUDA events on the launching stream).
-      decode: per width b, a column of N values (64 MiB packed: in L2 after the
-              first launch, and ~6.7 of the scan's 8 KB tiles per warp) and its
-              first N/2 values are each scanned warm, branch-free, sigma = 0.1, as
-              a CUDA graph of 20 launches; T_dec,resident(b) = (N/2) / (t(N) -
-              t(N/2)): the slope, so the fixed cost of a launch cancels."""
+      decode: per width b, a column of N values and its first N/2 values are
+              each scanned warm, branch-free, sigma = 0.1, as a CUDA graph of 20
+              launches; T_dec,resident(b) = (N/2) / (t(N) - t(N/2)): the slope,
+              so the fixed cost of a launch cancels.  N is six rounds of the
+              scan's tiles over all its warps (N/2 three), so both sizes give
+              every warp the same work (<= 60 MB packed: in L2 after the first
+              launch)."""
     import torch
 
     n = 1 << 28
@@ -821,7 +873,8 @@ def run_probes(args, dev, stream, gbscan, beta_read, law):
     res = torch.zeros(4, dtype=torch.int64, device=dev)
     per_b = {}
     for b in WIDTHS:
-        n2 = ((64 << 23) // b) // 2048 * 2048
+        shape = gbscan.scan_launch_shape(b)
+        n2 = 6 * shape["ctas"] * shape["warps_per_cta"] * shape["blocks_per_tile"] * 1024
         n1 = n2 // 2
         with torch.cuda.stream(stream):
             v = synth.uniform_values_device(synth.seed_for(20, b), n2, b, device=dev)
@@ -846,8 +899,9 @@ def run_probes(args, dev, stream, gbscan, beta_read, law):
     med = statistics.median(below) if below else None
     return {"triad": {"workload": "STREAM triad a = b + 3c over 2^28 float32 (3 GiB), best of 10",
                       "gbs": round(best, 1), "beta_read_gbs": round(beta_read, 1), "exact": triad_ok},
-            "decode_resident": {"workload": "branch-free scan of an L2-resident column per b (64 MiB packed), "
-                                            "sigma = 0.1, slope between N and N/2 values, CUDA graphs of 20 launches",
+            "decode_resident": {"workload": "branch-free scan of an L2-resident column per b (N = six rounds of "
+                                            "tiles over all warps, <= 60 MB packed), sigma = 0.1, slope between N "
+                                            "and N/2 values, CUDA graphs of 20 launches",
                                 "per_b": per_b, "t_dec_median_below_ridge_gvals": med,
                                 "t_dec_fitted_gvals": fitted, "b_star_fitted": ridge,
                                 "resident_over_fitted": round(med / fitted, 3) if med and fitted else None}}

@@ -64,7 +64,9 @@ struct Geo {
 
 // Launch shape for width B: 8 warps per CTA, each with kStages slots of up
 // to 8 KB; a tile is the largest multiple of the warp step (kLpt blocks) that
-// fits a slot.
+// fits a slot, and at most 16 blocks: below b = 4 a full slot would hold
+// 32-64 K values (~10-20 us of decode per warp), too coarse to share a
+// column's work evenly among the warps.
 template <int B>
 struct Shape {
     static constexpr int kWarps = 8;
@@ -73,7 +75,7 @@ struct Shape {
     static constexpr int kSlotMax = 8 * 1024;
     static constexpr int kStep = Geo<B>::kLpt;
     static constexpr int kTbRaw = (kSlotMax / kBlockBytes) / kStep * kStep;
-    static constexpr int kTB = kTbRaw < kStep ? kStep : (kTbRaw > 128 ? 128 : kTbRaw);
+    static constexpr int kTB = kTbRaw < kStep ? kStep : (kTbRaw > 16 ? 16 : kTbRaw);
     static constexpr int kTileBytes = kTB * kBlockBytes;
     static constexpr int kSlotBytes = kWarps * kStages * kTileBytes;
     static constexpr int kSmemBytes = kSlotBytes + kWarps * kStages * 8 + kWarps * kStages * 4;
@@ -114,14 +116,14 @@ __device__ __forceinline__ void load_rows(typename Geo<B>::Vec (&W)[B], const ty
 }
 
 // -------------------------------------------------------------- aggregate
-// Per value the decode needs an extraction, two compares and one add.  On
-// this SM the integer ALU pipe retires 16 lanes per cycle and IMAD (FMA-heavy
-// pipe) half that, so the work is split about 3:1: extraction (shift, funnel
-// shift, LOP3 mask) and both compares stay on the ALU, and each value costs
-// exactly one IMAD -- the accumulation (IMAD by an opaque 1, %nctaid.z, which
-// the compiler cannot fold) or, for a field at the top of its word, the
-// extraction itself (IMAD.HI by 2^B with the added constant folded in), in
-// which case the accumulation is an ALU add.
+// Per value the decode needs an extraction, a range test and one add.  The
+// integer ALU pipe and the FMA-heavy pipe (IMAD) each retire 16 lanes per
+// cycle on this SM (the ncu pipe counters of the b = 8 scan: 2 cycles per warp
+// instruction on both), so the decode spreads its work over both: extraction
+// (shift, funnel shift, LOP3 mask) and one ISETP per value stay on the ALU;
+// the subtract of the range test and the accumulation are IMADs by an opaque
+// 1 (%nctaid.z, which the compiler cannot fold), and a field at the top of its
+// word is extracted by IMAD.HI by 2^B with the added constant folded in.
 struct Lanes {
     uint32_t one;     // 1, opaque to the compiler
     uint32_t pow2b;   // 2^B (B < 32)
@@ -199,10 +201,10 @@ __device__ __forceinline__ uint32_t field_add(const typename Geo<B>::Vec (&W)[B]
     }
 }
 
-// For a field in the middle of its word or straddling two words the
-// extraction already costs two ALU operations; every other such value moves
-// its subtraction to the FMA pipe (one compare left on the ALU) so both pipes
-// stay busy: about 3.5 ALU and 1.5 IMAD per value.
+// Mode 1 (32-bit sums plus a count): for a field in the middle of its word
+// or straddling two words the extraction already costs two ALU operations;
+// every other such value moves its subtraction to the FMA pipe (one compare
+// left on the ALU).
 template <int B>
 __device__ __forceinline__ bool sub_on_fma(int r, int k)
 {
@@ -236,6 +238,16 @@ __device__ __forceinline__ void acc0_imad(uint32_t& a, uint32_t ui, const Lanes&
         "setp.lt.and.u32 p, %1, %3, p;\n\t"
         "@p mad.lo.u32 %0, %1, %4, %0;\n\t}"
         : "+r"(a) : "r"(ui), "r"(L.loi), "r"(L.hii), "r"(L.one));
+}
+// subtract on the FMA pipe, compare and add on the ALU (a top-of-word field,
+// whose extraction was already an IMAD)
+__device__ __forceinline__ void acc0_fsub(uint32_t& a, uint32_t ui, const Lanes& L)
+{
+    asm("{\n\t.reg .pred p;\n\t.reg .b32 t;\n\t"
+        "mad.lo.u32 t, %1, %4, %2;\n\t"
+        "setp.le.u32 p, t, %3;\n\t"
+        "@p add.u32 %0, %0, %1;\n\t}"
+        : "+r"(a) : "r"(ui), "r"(L.negloi), "r"(L.wm1), "r"(L.one));
 }
 __device__ __forceinline__ void acc0_alu(uint32_t& a, uint32_t ui, const Lanes& L)
 {
@@ -301,9 +313,12 @@ __device__ __forceinline__ void agg_block(const typename Geo<B>::Vec* rows, cons
                     }
                 }
             } else if constexpr (kMode == 0) {
-                if (top_field<B>(r)) acc0_alu(a[k], ui, L);
-                else if (sub_on_fma<B>(r, k)) acc0_fma(a[k], ui, L);
-                else acc0_imad(a[k], ui, L);
+                // Every compare keeps one ISETP on the ALU; the subtract and the
+                // add go to the FMA pipe, except that half the top-of-word
+                // fields (already extracted by IMAD.HI) add on the ALU: about
+                // 2.9 ALU and 2.0 IMAD per value (2.4 / 2.1 at b = 8).
+                if (top_field<B>(r) && ((r + k) & 1) == 0) acc0_fsub(a[k], ui, L);
+                else acc0_fma(a[k], ui, L);
             } else if constexpr (kMode == 1) {
                 if (top_field<B>(r)) acc1_alu(c, a[k], ui, L);
                 else if (sub_on_fma<B>(r, k)) acc1_fma(c, a[k], ui, L);
