@@ -965,6 +965,9 @@ BATCH_WORKLOAD = ("batched: 4096 columns, lengths log-uniform in [2^10, 2^26] sc
                   "log-uniform in [1e-4, 1]")
 
 
+TRAIN_COLS = 200
+
+
 def run_batched(args, dev, stream, gbscan, beta_gbs, t_dec_gvals):
     """4096-column batch: one planned graph launch vs one plain launch per column.
 
@@ -1027,7 +1030,8 @@ def run_batched(args, dev, stream, gbscan, beta_gbs, t_dec_gvals):
     out = {}
     # planner: trained on harness timings of separate training columns, on the GPU
     t0 = time.perf_counter()
-    tcols, tpreds = plmod.training_columns(seed=11, count=120, stream=stream)
+    # training lengths span the batch's own (89 .. 5.8 M values after scaling), not 2^22..2^27
+    tcols, tpreds = plmod.training_columns(seed=11, count=TRAIN_COLS, n_lo=1 << 12, n_hi=1 << 23, stream=stream)
     X, T = plmod.collect(tcols, tpreds, stream, reps=3)
     for c in tcols:
         c.close()
@@ -1067,7 +1071,8 @@ def run_batched(args, dev, stream, gbscan, beta_gbs, t_dec_gvals):
     return {"workload": BATCH_WORKLOAD, "ncols": ncols, "values": total_values, "packed_bytes": total_bytes,
             "ms_per_column_graph": round(ms_graph, 4), "ms_per_column_loop": round(ms_loop, 4),
             "per_column_launches": ncols, "plans": out,
-            "planner": {"training_columns": 120, "labels": "log of each strategy's marginal device time as a one-entry batch",
+            "planner": {"training_columns": TRAIN_COLS, "training_lengths": "log-uniform in [2^12, 2^23] values",
+                        "labels": "log of each strategy's marginal device time as a one-entry batch",
                         "steps": 1500, "loss_first": round(hist[0], 4), "loss_last": round(hist[-1], 4),
                         "decision_margin_log_time": round(margin, 4),
                         "train_and_label_s": round(train_s, 1)}}
