@@ -965,7 +965,7 @@ BATCH_WORKLOAD = ("batched: 4096 columns, lengths log-uniform in [2^10, 2^26] sc
                   "log-uniform in [1e-4, 1]")
 
 
-TRAIN_COLS = 200
+TRAIN_COLS = 120
 
 
 def run_batched(args, dev, stream, gbscan, beta_gbs, t_dec_gvals):
@@ -1030,13 +1030,20 @@ def run_batched(args, dev, stream, gbscan, beta_gbs, t_dec_gvals):
     out = {}
     # planner: trained on harness timings of separate training columns, on the GPU
     t0 = time.perf_counter()
-    # training lengths span the batch's own (89 .. 5.8 M values after scaling), not 2^22..2^27
-    tcols, tpreds = plmod.training_columns(seed=11, count=TRAIN_COLS, n_lo=1 << 12, n_hi=1 << 23, stream=stream)
-    X, T = plmod.collect(tcols, tpreds, stream, reps=3)
+    # training lengths 2^22..2^27: the columns that carry the batch's time (training on the batch's
+    # whole length range, 2^12..2^23, fitted label noise of tiny columns and planned worse)
+    tcols, tpreds = plmod.training_columns(seed=11, count=TRAIN_COLS, stream=stream)
+    X, T = plmod.collect(tcols, tpreds, stream, reps=5)
+    L_train = plmod.law_log_times(tcols, X, beta_gbs, t_dec_gvals, stream)
+    calib = plmod.calibrate_law(L_train, T)
+    P_train = plmod.law_prior(L_train, calib)
     for c in tcols:
         c.close()
     net = gbscan.Planner(4, seed=5)
     hist = plmod.train(net, X, T, steps=1500, lr=3e-3, stream=stream)
+    # the same network shape trained on the law's residual: it corrects the law's log times
+    net_r = gbscan.Planner(4, seed=5)
+    hist_r = plmod.train(net_r, X, (T - P_train).contiguous(), steps=1500, lr=3e-3, stream=stream)
     train_s = time.perf_counter() - t0
     probe = gbscan.Batch(cols)
     feats = torch.zeros((ncols, 4), dtype=torch.float32, device=dev)
@@ -1044,12 +1051,18 @@ def run_batched(args, dev, stream, gbscan, beta_gbs, t_dec_gvals):
     torch.cuda.synchronize()
     law_plan = plmod.choose_law(probe, feats, beta_gbs, t_dec_gvals, stream)
     probe.close()
+    P_batch = plmod.law_prior(plmod.law_log_times(cols, feats, beta_gbs, t_dec_gvals, stream), calib)
+    calib_plan = plmod.choose_prior_only(P_batch)
     # switch away from the default plan only on a predicted gain above the
     # network's own RMS error in log time (the final training loss is an MSE)
     margin = float(np.sqrt(max(hist[-1], 0.0)))
     mlp_plan = plmod.choose(net, feats, stream, margin=margin)
+    margin_r = float(np.sqrt(max(hist_r[-1], 0.0)))
+    mlp_law_plan = plmod.choose(net_r, feats, stream, margin=margin_r, prior=P_batch)
     net.close()
-    plans = {"branchfree": ["branchfree"] * ncols, "law": law_plan, "planned_mlp": mlp_plan}
+    net_r.close()
+    plans = {"branchfree": ["branchfree"] * ncols, "law": law_plan, "planned_mlp": mlp_plan,
+             "law_calibrated": calib_plan, "planned_mlp_law_prior": mlp_law_plan}
     res_b = torch.zeros((ncols, 4), dtype=torch.int64, device=dev)
     parr = gbscan.Batch.pred_array(preds)      # marshalled once, outside the timed region
     for name, strategies in plans.items():
@@ -1071,10 +1084,13 @@ def run_batched(args, dev, stream, gbscan, beta_gbs, t_dec_gvals):
     return {"workload": BATCH_WORKLOAD, "ncols": ncols, "values": total_values, "packed_bytes": total_bytes,
             "ms_per_column_graph": round(ms_graph, 4), "ms_per_column_loop": round(ms_loop, 4),
             "per_column_launches": ncols, "plans": out,
-            "planner": {"training_columns": TRAIN_COLS, "training_lengths": "log-uniform in [2^12, 2^23] values",
+            "planner": {"training_columns": TRAIN_COLS, "training_lengths": "log-uniform in [2^22, 2^27] values",
                         "labels": "log of each strategy's marginal device time as a one-entry batch",
                         "steps": 1500, "loss_first": round(hist[0], 4), "loss_last": round(hist[-1], 4),
                         "decision_margin_log_time": round(margin, 4),
+                        "law_prior_net": {"target": "label minus the calibrated law's log time (per strategy a + b * law)", "loss_first": round(hist_r[0], 4),
+                                          "loss_last": round(hist_r[-1], 4),
+                                          "decision_margin_log_time": round(margin_r, 4)},
                         "train_and_label_s": round(train_s, 1)}}
 
 

@@ -319,6 +319,14 @@ scan_status scan_batch_features(scan_batch *batch, const scan_pred *preds, void 
 scan_status scan_batch_law_choose(scan_batch *batch, const float *dev_features,
                                   float beta_bytes_per_s, const float *t_dec_values_per_s,
                                   void *stream, int32_t *dev_choice);
+/* The same law's predicted times, as natural-log milliseconds: dev_log_ms
+ * (ncols x 4 float32, device, row = the column's position in the batch) gets
+ * log(1e3 * max(bytes_s/beta, values_s/T_dec[s])) per strategy, and 30 for a
+ * zone strategy of a column without a zone map.  The prior of
+ * scan_planner_choose_prior.  Errors as scan_batch_law_choose. */
+scan_status scan_batch_law_times(scan_batch *batch, const float *dev_features,
+                                 float beta_bytes_per_s, const float *t_dec_values_per_s,
+                                 void *stream, float *dev_log_ms);
 
 /* One-shot batch: plan, run once with host results, free. */
 scan_status scan_batch_run(const scan_column *const *cols, const scan_pred *preds, uint32_t ncols,
@@ -367,6 +375,17 @@ scan_status scan_planner_choose(scan_planner *planner, const float *dev_x, uint3
  * error.  margin 0 is scan_planner_choose. */
 scan_status scan_planner_choose_margin(scan_planner *planner, const float *dev_x, uint32_t rows,
                                        float margin, int32_t *dev_choice, void *stream);
+/* As scan_planner_choose_margin, on the network's output plus a prior:
+ * row n's predicted log time of strategy s is y[n][s] + dev_prior[n*S + s].
+ * With the law's log times as the prior (scan_batch_law_times) and a network
+ * trained on the labels minus those log times, the network learns a
+ * correction to the bandwidth law of paper §2 (Eq. 2) instead of the whole
+ * time, and an untrained correction leaves the law's plan.  dev_prior:
+ * rows x S float32, device, row-major.  Errors: SCAN_EINVAL for NULL
+ * pointers or a negative margin. */
+scan_status scan_planner_choose_prior(scan_planner *planner, const float *dev_x, uint32_t rows,
+                                      float margin, const float *dev_prior, int32_t *dev_choice,
+                                      void *stream);
 /* Binary checkpoint: 16-byte header (magic, version 1, S, count) + floats. */
 scan_status scan_planner_save(const scan_planner *planner, const char *path);
 scan_status scan_planner_load(scan_planner *planner, const char *path);

@@ -334,6 +334,24 @@ __global__ void __launch_bounds__(256) k_batch_features(const gb::BatchCol* __re
 //   max(bytes_s / beta, values_s / T_dec[s]); a zone skip reads the zone map
 //   plus a fraction phi = min(1, sigma_hat + (1 - c) + 2 / blocks) of the blocks.
 //   Strategies: 0 branch-free, 1 branchy, 2 zone-skip branch-free, 3 zone-skip branchy.
+//   A zone strategy of a column without a zone map gets a negative time (unavailable).
+__device__ void law_seconds(const float* f, const gb::BatchCol& c, float beta, const double (&tdec)[4],
+                            double (&t)[4])
+{
+    const double n = static_cast<double>(c.n), nb = static_cast<double>((c.n + 1023u) >> 10);
+    const double bytes = nb * 128.0 * c.b;
+    const double sigma = pow(10.0, 5.0 * f[2] - 5.0);
+    double phi = sigma + (1.0 - f[3]) + (nb > 0 ? 2.0 / nb : 1.0);
+    phi = phi > 1.0 ? 1.0 : phi;
+    const bool has_zone = c.zonemap != nullptr;
+    for (int s = 0; s < 4; ++s) {
+        const bool zone = s >= 2;
+        const double rd = zone ? phi * bytes + 8.0 * nb : bytes;
+        const double vals = zone ? phi * n : n;
+        t[s] = (zone && !has_zone) ? -1.0 : fmax(rd / beta, vals / tdec[s]);
+    }
+}
+
 __global__ void k_law_choose(const float* __restrict__ feats, const gb::BatchCol* __restrict__ cols,
                              uint32_t ncols, float beta, float t0, float t1, float t2, float t3,
                              int32_t* __restrict__ out)
@@ -341,28 +359,36 @@ __global__ void k_law_choose(const float* __restrict__ feats, const gb::BatchCol
     const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= ncols) return;
     const gb::BatchCol c = cols[j];
-    const float* f = feats + 4ull * c.out;
-    const double n = static_cast<double>(c.n), nb = static_cast<double>((c.n + 1023u) >> 10);
-    const double bytes = nb * 128.0 * c.b;
-    const double sigma = pow(10.0, 5.0 * f[2] - 5.0);
-    double phi = sigma + (1.0 - f[3]) + (nb > 0 ? 2.0 / nb : 1.0);
-    phi = phi > 1.0 ? 1.0 : phi;
     const double tdec[4] = {t0, t1, t2, t3};
-    const bool has_zone = c.zonemap != nullptr;
+    double t[4];
+    law_seconds(feats + 4ull * c.out, c, beta, tdec, t);
     int best = 0;
     double bt = 1e300;
     for (int s = 0; s < 4; ++s) {
-        const bool zone = s >= 2;
-        if (zone && !has_zone) continue;
-        const double rd = zone ? phi * bytes + 8.0 * nb : bytes;
-        const double vals = zone ? phi * n : n;
-        const double t = fmax(rd / beta, vals / tdec[s]);
-        if (t < bt) {
-            bt = t;
+        if (t[s] < 0.0) continue;
+        if (t[s] < bt) {
+            bt = t[s];
             best = s;
         }
     }
     out[c.out] = best;
+}
+
+// The same law times as natural-log milliseconds, ncols x 4 (row = the
+// column's position in the batch); an unavailable strategy gets kLawNoLogMs.
+constexpr float kLawNoLogMs = 30.0f;
+__global__ void k_law_times(const float* __restrict__ feats, const gb::BatchCol* __restrict__ cols,
+                            uint32_t ncols, float beta, float t0, float t1, float t2, float t3,
+                            float* __restrict__ out)
+{
+    const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= ncols) return;
+    const gb::BatchCol c = cols[j];
+    const double tdec[4] = {t0, t1, t2, t3};
+    double t[4];
+    law_seconds(feats + 4ull * c.out, c, beta, tdec, t);
+    for (int s = 0; s < 4; ++s)
+        out[4ull * c.out + s] = t[s] < 0.0 ? kLawNoLogMs : static_cast<float>(log(t[s] * 1e3 + 1e-9));
 }
 
 }  // namespace
@@ -484,6 +510,23 @@ scan_status scan_batch_law_choose(scan_batch* bt, const float* dev_features, flo
     k_law_choose<<<(bt->ncols + 255) / 256, 256, 0, st>>>(dev_features, bt->d_table, bt->ncols, beta_bytes_per_s,
                                                           t_dec_values_per_s[0], t_dec_values_per_s[1],
                                                           t_dec_values_per_s[2], t_dec_values_per_s[3], dev_choice);
+    BT_CUDA(cudaGetLastError());
+    return SCAN_OK;
+}
+
+scan_status scan_batch_law_times(scan_batch* bt, const float* dev_features, float beta_bytes_per_s,
+                                 const float* t_dec_values_per_s, void* stream, float* dev_log_ms)
+{
+    gb_set_last_error("");
+    if (!bt || !dev_features || !dev_log_ms || !t_dec_values_per_s) return bfail(SCAN_EINVAL, "null pointer");
+    if (!bt->ncols) return SCAN_OK;
+    if (!(beta_bytes_per_s > 0.f)) return bfail(SCAN_EINVAL, "beta must be positive");
+    for (int s = 0; s < 4; ++s)
+        if (!(t_dec_values_per_s[s] > 0.f)) return bfail(SCAN_EINVAL, "every T_dec must be positive");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    k_law_times<<<(bt->ncols + 255) / 256, 256, 0, st>>>(dev_features, bt->d_table, bt->ncols, beta_bytes_per_s,
+                                                         t_dec_values_per_s[0], t_dec_values_per_s[1],
+                                                         t_dec_values_per_s[2], t_dec_values_per_s[3], dev_log_ms);
     BT_CUDA(cudaGetLastError());
     return SCAN_OK;
 }

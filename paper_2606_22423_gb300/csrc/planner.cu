@@ -142,6 +142,20 @@ __global__ void k_argmin_rows(const float* __restrict__ y, int rows, int S, floa
     out[n] = best;
 }
 
+// Same rule on y + prior: the network predicts a correction to a prior
+// estimate of each strategy's log time (the law's), row-major rows x S.
+__global__ void k_argmin_rows_prior(const float* __restrict__ y, const float* __restrict__ prior, int rows,
+                                    int S, float margin, int32_t* __restrict__ out)
+{
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= rows) return;
+    float lo = y[n * S] + prior[n * S];
+    for (int s = 1; s < S; ++s) lo = fminf(lo, y[n * S + s] + prior[n * S + s]);
+    int best = 0;
+    while (best < S - 1 && y[n * S + best] + prior[n * S + best] > lo + margin) ++best;
+    out[n] = best;
+}
+
 inline unsigned blocks_for(long long n, int t = 256) { return static_cast<unsigned>((n + t - 1) / t); }
 
 // splitmix64 (Steele, Lea, Flood 2014) for the deterministic initial weights
@@ -375,6 +389,22 @@ scan_status scan_planner_choose_margin(scan_planner* pl, const float* dev_x, uin
     if (s != SCAN_OK || !rows) return s;
     k_argmin_rows<<<blocks_for(rows), 256, 0, static_cast<cudaStream_t>(stream)>>>(a.y, static_cast<int>(rows),
                                                                                   pl->S, margin, dev_choice);
+    PL_CUDA(cudaGetLastError());
+    return SCAN_OK;
+}
+
+scan_status scan_planner_choose_prior(scan_planner* pl, const float* dev_x, uint32_t rows, float margin,
+                                      const float* dev_prior, int32_t* dev_choice, void* stream)
+{
+    if (!pl || (rows && (!dev_x || !dev_prior || !dev_choice))) return pfail(SCAN_EINVAL, "null pointer");
+    if (!(margin >= 0.0f)) return pfail(SCAN_EINVAL, "margin must be >= 0");
+    scan_status s = ensure_ws(pl, rows ? rows : 1);
+    if (s != SCAN_OK) return s;
+    const Acts a = acts(pl);
+    s = scan_planner_forward(pl, dev_x, rows, a.y, stream);
+    if (s != SCAN_OK || !rows) return s;
+    k_argmin_rows_prior<<<blocks_for(rows), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        a.y, dev_prior, static_cast<int>(rows), pl->S, margin, dev_choice);
     PL_CUDA(cudaGetLastError());
     return SCAN_OK;
 }

@@ -95,6 +95,7 @@ SIGNATURES = {
     "scan_batch_set_strategies": (_st, [_vp, _vp]),
     "scan_batch_features": (_st, [_vp, _vp, _vp, _vp]),
     "scan_batch_law_choose": (_st, [_vp, _vp, ctypes.c_float, _vp, _vp, _vp]),
+    "scan_batch_law_times": (_st, [_vp, _vp, ctypes.c_float, _vp, _vp, _vp]),
     "scan_planner_create": (_st, [_u32, _u64, ctypes.POINTER(_vp)]),
     "scan_planner_destroy": (_st, [_vp]),
     "scan_planner_param_count": (_u64, [_vp]),
@@ -105,6 +106,7 @@ SIGNATURES = {
     "scan_planner_train_step": (_st, [_vp, _vp, _vp, _u32, ctypes.c_float, _vp, _vp]),
     "scan_planner_choose": (_st, [_vp, _vp, _u32, _vp, _vp]),
     "scan_planner_choose_margin": (_st, [_vp, _vp, _u32, ctypes.c_float, _vp, _vp]),
+    "scan_planner_choose_prior": (_st, [_vp, _vp, _u32, ctypes.c_float, _vp, _vp, _vp]),
     "scan_planner_save": (_st, [_vp, ctypes.c_char_p]),
     "scan_planner_load": (_st, [_vp, ctypes.c_char_p]),
     "scan_server_create": (_st, [_vp, _u32, _u32, _u64, _u32, ctypes.POINTER(_vp)]),
@@ -363,6 +365,12 @@ class Batch:
         _check(load().scan_batch_law_choose(self._h, _ptr(dev_features), float(beta_bytes_per_s), td,
                                             _stream(stream), _ptr(dev_choice)))
 
+    def law_times(self, dev_features, beta_bytes_per_s, t_dec_values_per_s, dev_log_ms, stream=None):
+        """The law's predicted log milliseconds per (column, strategy) (float32, device, ncols x 4)."""
+        td = (ctypes.c_float * 4)(*[float(x) for x in t_dec_values_per_s])
+        _check(load().scan_batch_law_times(self._h, _ptr(dev_features), float(beta_bytes_per_s), td,
+                                           _stream(stream), _ptr(dev_log_ms)))
+
     @staticmethod
     def pred_array(preds):
         """Marshal predicates once (reusable across runs)."""
@@ -467,8 +475,11 @@ class Planner:
                                               _stream(stream), ctypes.byref(loss) if want_loss else None))
         return float(loss.value) if want_loss else None
 
-    def choose(self, dev_x, rows, dev_choice, stream=None, margin=0.0):
-        if margin:
+    def choose(self, dev_x, rows, dev_choice, stream=None, margin=0.0, dev_prior=None):
+        if dev_prior is not None:
+            _check(load().scan_planner_choose_prior(self._h, _ptr(dev_x), rows, float(margin), _ptr(dev_prior),
+                                                    _ptr(dev_choice), _stream(stream)))
+        elif margin:
             _check(load().scan_planner_choose_margin(self._h, _ptr(dev_x), rows, float(margin), _ptr(dev_choice),
                                                      _stream(stream)))
         else:

@@ -91,15 +91,27 @@ def train(planner, X, T, steps=1500, lr=3e-3, stream=None):
     return hist
 
 
-def choose(planner, X, stream=None, margin=0.0):
+def choose(planner, X, stream=None, margin=0.0, prior=None):
     """Strategy names per row of X from the network (argmin of predicted log time).
     With margin > 0: the first strategy, in STRATEGIES order, whose predicted log
-    time is within `margin` of the row's minimum."""
+    time is within `margin` of the row's minimum.  With a prior (rows x 4 log
+    times on the GPU, e.g. law_log_times): the prediction is network + prior."""
     torch = _torch()
     out = torch.zeros(X.shape[0], dtype=torch.int32, device="cuda")
-    planner.choose(X, X.shape[0], out, stream, margin=margin)
+    planner.choose(X, X.shape[0], out, stream, margin=margin, dev_prior=prior)
     torch.cuda.synchronize()
     return [STRATEGIES[i] for i in out.cpu().tolist()]
+
+
+def law_log_times(columns, X, beta_gbs, t_dec_gvals, stream=None):
+    """The bandwidth law's predicted log milliseconds per (column, strategy), on the GPU."""
+    torch = _torch()
+    bt = gbscan.Batch(columns)
+    out = torch.zeros((len(columns), len(STRATEGIES)), dtype=torch.float32, device="cuda")
+    bt.law_times(X, beta_gbs * 1e9, [t * 1e9 for t in t_dec_gvals], out, stream)
+    torch.cuda.synchronize()
+    bt.close()
+    return out
 
 
 def choose_law(batch, X, beta_gbs, t_dec_gvals, stream=None):
@@ -109,6 +121,45 @@ def choose_law(batch, X, beta_gbs, t_dec_gvals, stream=None):
     batch.law_choose(X, beta_gbs * 1e9, [t * 1e9 for t in t_dec_gvals], out, stream)
     torch.cuda.synchronize()
     return [STRATEGIES[i] for i in out.cpu().tolist()]
+
+
+def calibrate_law(L, T):
+    """Per strategy, the least-squares affine map a_s + b_s * L_s from the law's log
+    times L to the measured log-time labels T (both rows x S, on the GPU): the law's
+    shape with its scale and fixed costs fitted to this machine.  Returns (a, b)."""
+    torch = _torch()
+    a = torch.zeros(L.shape[1], dtype=torch.float32, device=L.device)
+    b = torch.ones(L.shape[1], dtype=torch.float32, device=L.device)
+    for s in range(L.shape[1]):
+        x, y = L[:, s].double(), T[:, s].double()
+        keep = x < 29.0                      # strategies the law marks unavailable stay out
+        if int(keep.sum()) < 2:
+            continue
+        x, y = x[keep], y[keep]
+        vx = float(((x - x.mean()) ** 2).sum())
+        bs = float(((x - x.mean()) * (y - y.mean())).sum()) / vx if vx > 0 else 0.0
+        b[s] = bs
+        a[s] = float(y.mean() - bs * x.mean())
+    return a, b
+
+
+def law_prior(L, calib):
+    """Calibrated law log times a_s + b_s * L_s (rows x S): the prior the network corrects."""
+    a, b = calib
+    return (a[None, :] + b[None, :] * L).contiguous()
+
+
+def choose_prior_only(prior, stream=None):
+    """The plan of the prior alone (argmin per row, first on ties): the choice of a
+    correction network that predicts no correction, run through the same kernel."""
+    torch = _torch()
+    rows = prior.shape[0]
+    pl = gbscan.Planner(prior.shape[1], seed=1)
+    pl.set_params(np.zeros(pl.nparams, dtype=np.float32))
+    X = torch.zeros((rows, 4), dtype=torch.float32, device=prior.device)
+    plan = choose(pl, X, stream, margin=0.0, prior=prior)
+    pl.close()
+    return plan
 
 
 def training_columns(seed, count=160, n_lo=1 << 22, n_hi=1 << 27, stream=None):

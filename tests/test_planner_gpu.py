@@ -140,6 +140,57 @@ def test_features_match_oracle_computation():
         c.close()
 
 
+def test_law_times_and_the_prior_corrected_choice():
+    from paper_2606_22423_gb300 import planner as plmod
+
+    specs = [(60_000, 7, None, 0.1, True), (400_000, 16, 0.0, 1e-3, True), (33_000, 32, 1.0, 0.5, True),
+             (200_000, 3, 0.01, 1e-3, False), (1500, 12, None, 1.0, True), (1 << 20, 24, 0.0, 0.01, True)]
+    cols, preds = [], []
+    for i, (n, b, p, sigma, zoned) in enumerate(specs):
+        v = synth.uniform_values(300 + i, n, b) if p is None else synth.clustered_values(300 + i, n, b, p)
+        c = gbscan.Column.from_host(v, b)
+        if zoned:
+            c.zonemap_build()
+        cols.append(c)
+        preds.append(synth.pick_range(400 + i, b, sigma))
+    X = plmod.features(cols, preds)
+    beta_gbs, tdec = 7000.0, [3.9, 2.5, 3.9, 2.5]
+    L = plmod.law_log_times(cols, X, beta_gbs, tdec)
+    bt = gbscan.Batch(cols)
+    law = plmod.choose_law(bt, X, beta_gbs, tdec)
+    bt.close()
+    Lh = L.cpu().numpy()
+    # the law's plan is the argmin of its own times; no zone strategy without a zone map
+    assert [plmod.STRATEGIES[i] for i in Lh.argmin(axis=1)] == law
+    assert (Lh[3, 2:] == 30.0).all() and law[3] in ("branchfree", "branchy")
+    # full scans in closed form: log(1e3 * max(bytes / beta, values / T_dec)) milliseconds
+    for j, (n, b, *_rest) in enumerate(specs):
+        nbytes = -(-n // 1024) * 128 * b
+        for s in (0, 1):
+            want = math.log(1e3 * max(nbytes / (beta_gbs * 1e9), n / (tdec[s] * 1e9)) + 1e-9)
+            assert abs(Lh[j, s] - want) <= 1e-5 * abs(want) + 1e-6
+    # prior-corrected choice: network output + prior, first strategy within the margin
+    rows = len(cols)
+    pl = gbscan.Planner(4, seed=7)
+    y = torch.zeros((rows, 4), dtype=torch.float32, device="cuda")
+    pl.forward(X, rows, y)
+    ch = torch.zeros(rows, dtype=torch.int32, device="cuda")
+    for margin in (0.0, 0.2, 1e9):
+        pl.choose(X, rows, ch, margin=margin, dev_prior=L)
+        torch.cuda.synchronize()
+        tot = y.cpu().numpy() + Lh                                    # float32, as the kernel
+        want = (tot <= tot.min(axis=1, keepdims=True) + np.float32(margin)).argmax(axis=1)
+        assert (ch.cpu().numpy() == want).all(), margin
+    # a network that predicts no correction leaves the law's plan
+    pl.set_params(np.zeros(pl.nparams, dtype=np.float32))
+    pl.choose(X, rows, ch, dev_prior=L)
+    torch.cuda.synchronize()
+    assert [plmod.STRATEGIES[i] for i in ch.cpu().tolist()] == law
+    pl.close()
+    for c in cols:
+        c.close()
+
+
 def test_trained_planner_beats_the_fixed_full_scan_on_clustered_low_selectivity_columns():
     from paper_2606_22423_gb300 import planner as plmod
 
