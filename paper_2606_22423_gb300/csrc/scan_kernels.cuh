@@ -435,7 +435,7 @@ __device__ __forceinline__ void acc_one(uint32_t ui, const Lanes& L, uint32_t& a
             }
         }
     } else if constexpr (kMode == 0) {
-        acc0_imad(a, ui, L);
+        acc0_fma(a, ui, L);  // subtract and add on the FMA pipe, one ISETP on the ALU
     } else if constexpr (kMode == 1) {
         acc1_imad(c, a, ui, L);
     } else {
