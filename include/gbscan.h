@@ -377,12 +377,12 @@ scan_status scan_planner_choose_margin(scan_planner *planner, const float *dev_x
                                        float margin, int32_t *dev_choice, void *stream);
 /* As scan_planner_choose_margin, on the network's output plus a prior:
  * row n's predicted log time of strategy s is y[n][s] + dev_prior[n*S + s].
- * With the law's log times as the prior (scan_batch_law_times) and a network
- * trained on the labels minus those log times, the network learns a
- * correction to the bandwidth law of paper §2 (Eq. 2) instead of the whole
- * time, and an untrained correction leaves the law's plan.  dev_prior:
- * rows x S float32, device, row-major.  Errors: SCAN_EINVAL for NULL
- * pointers or a negative margin. */
+ * With the law's log times as the prior (scan_batch_law_times, or an affine
+ * calibration of them per strategy) and a network trained on the labels
+ * minus that prior, the network learns a correction to the bandwidth law of
+ * paper §2 (Eq. 2) instead of the whole time; a network whose output is zero
+ * gives the prior's own plan.  dev_prior: rows x S float32, device,
+ * row-major.  Errors: SCAN_EINVAL for NULL pointers or a negative margin. */
 scan_status scan_planner_choose_prior(scan_planner *planner, const float *dev_x, uint32_t rows,
                                       float margin, const float *dev_prior, int32_t *dev_choice,
                                       void *stream);
