@@ -698,7 +698,11 @@ __global__ void __launch_bounds__(Shape<B>::kWarps * 32, 1) k_scan_full(const Sc
 
     const uint64_t full_blocks = p.n >> 10;
     const uint64_t ntiles = (full_blocks + S::kTB - 1) / S::kTB;
-    const uint64_t gw = static_cast<uint64_t>(blockIdx.x) * S::kWarps + warp;
+    // Warp-major numbering: a round's last, partial stretch of tiles goes to
+    // warp slot w of every CTA before slot w + 1 of any, so the CTAs (SMs) of
+    // a small column get equal shares (CTA-major numbering gave the first
+    // CTAs two tiles per warp and the rest one at 2^24 values, b = 8).
+    const uint64_t gw = static_cast<uint64_t>(warp) * gridDim.x + blockIdx.x;
     const uint64_t GW = static_cast<uint64_t>(gridDim.x) * S::kWarps;
 
     if (lane == 0) {
