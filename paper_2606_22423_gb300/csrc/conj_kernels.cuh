@@ -69,7 +69,8 @@ k_conj_pass(const ConjParams c, const ScanParams p)
     const uint64_t nblocks = (c.n + 1023u) >> 10;
     const uint64_t ntiles = (nblocks + S::kTB - 1) / S::kTB;
     const uint32_t tail = static_cast<uint32_t>(c.n & 1023u);
-    const uint64_t gw = static_cast<uint64_t>(blockIdx.x) * S::kWarps + warp;
+    // warp-major numbering, as the full scan: a partial last round is spread over all SMs
+    const uint64_t gw = static_cast<uint64_t>(warp) * gridDim.x + blockIdx.x;
     const uint64_t GW = static_cast<uint64_t>(gridDim.x) * S::kWarps;
 
     if (threadIdx.x == 0) decoded = 0u;
