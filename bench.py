@@ -177,62 +177,65 @@ def cpu_model() -> str:
     return names.get((impl, part), f"Arm implementer {impl} part {part}")
 
 
-def cpu_sample(columns_host, threads, budget_s, passes_max=3):
+def cpu_sample(columns_host, threads, budget_s, passes_max=3, strategies=1, sigmas=None):
     """The oracle over prefixes of the sweep columns: sigma-outer, b-inner passes over
-    SIGMAS (the sweep's order) until the time budget is spent (at least one pass).
-    Returns GB/s of packed bytes, values/s, scans, seconds and per-width values/s."""
+    the sweep's sigmas (each pass `strategies` times: the oracle has one scan loop,
+    so the sweep's two GPU strategies are the same CPU work), repeated until the
+    time budget is spent (at least one pass).  Returns GB/s of packed bytes,
+    values/s, scans, seconds and per-width values/s."""
     import oracle
 
     total_bytes, total_vals, t_used, scans = 0, 0, 0.0, 0
     per_b = {}
     for _ in range(passes_max):
-        for s in SIGMAS:
-            for b, words in columns_host:
-                lo, hi = pred_for(b, s)
-                n = words.size // b * 32  # values covered by these whole blocks
-                t0 = time.perf_counter()
-                if threads == 1:
-                    oracle.scan_packed(words, n, b, 0, lo, hi)
-                else:
-                    oracle.scan_packed_threads(words, n, b, 0, lo, hi, threads)
-                dt = time.perf_counter() - t0
-                t_used += dt
-                total_bytes += n * b / 8
-                total_vals += n
-                scans += 1
-                acc = per_b.setdefault(b, [0, 0.0])
-                acc[0] += n
-                acc[1] += dt
+        for _ in range(strategies):
+            for s in (sigmas or SIGMAS):
+                for b, words in columns_host:
+                    lo, hi = pred_for(b, s)
+                    n = words.size // b * 32  # values covered by these whole blocks
+                    t0 = time.perf_counter()
+                    if threads == 1:
+                        oracle.scan_packed(words, n, b, 0, lo, hi)
+                    else:
+                        oracle.scan_packed_threads(words, n, b, 0, lo, hi, threads)
+                    dt = time.perf_counter() - t0
+                    t_used += dt
+                    total_bytes += n * b / 8
+                    total_vals += n
+                    scans += 1
+                    acc = per_b.setdefault(b, [0, 0.0])
+                    acc[0] += n
+                    acc[1] += dt
         if t_used > budget_s:
             break
     vps = {b: n / t for b, (n, t) in per_b.items() if t > 0}
     return total_bytes / t_used / 1e9, total_vals / t_used, scans, t_used, vps
 
 
+CPU_SAMPLE_LOG2 = 25   # both oracle legs (the reference arm, cpu_baseline) scan 2^25-value columns
+
+
 def run_reference(args, world, rank):
-    """The oracle as it stands, timed on the host cores, on a sample of the sweep."""
+    """The oracle as it stands, timed on the host cores, on a sample of the sweep:
+    each step is the sweep's 384 scans (sigma-outer, b-inner, twice) over a
+    2^25-value column per width drawn from the same distribution -- the sample
+    size of the GPU arm's cpu_baseline leg, so the two oracle figures agree."""
     if rank != 0:
         return
     import oracle
 
     oracle.build()
     threads = os.cpu_count() or 1
-    n = 1 << 20                    # sample: a 2^20-value column per width, same distribution
+    n = 1 << args.cpu_sample_log2
     cols = []
     for b in WIDTHS:
         v = synth.uniform_values(synth.seed_for(2, b), n, b)
         cols.append((b, oracle.pack(v, b)))
-    preds = {(b, s): pred_for(b, s) for b in WIDTHS for s in SIGMAS}
+        del v
 
     def step():
-        nbytes = 0
-        for _ in STRATS:
-            for s in SIGMAS:
-                for b, words in cols:
-                    lo, hi = preds[(b, s)]
-                    oracle.scan_packed_threads(words, n, b, 0, lo, hi, threads)
-                    nbytes += n * b / 8
-        return nbytes
+        cpu_sample(cols, threads, budget_s=0.0, passes_max=1, strategies=len(STRATS))
+        return sum(n * b / 8 for b, _ in cols) * len(SIGMAS) * len(STRATS)
 
     for _ in range(args.warmup):
         step()
@@ -242,15 +245,17 @@ def run_reference(args, world, rank):
         nbytes += step()
     dt = time.perf_counter() - t0
     gbs = nbytes / dt / 1e9
-    sample = (f"384 scans per step (32 widths x 6 sigmas x 2) over a 2^20-value column per width drawn "
-              f"from the same distribution; oracle.scan_packed_threads on {threads} host threads")
+    sample = (f"384 scans per step (32 widths x 6 sigmas x 2 strategies, the sweep's order) over a "
+              f"2^{args.cpu_sample_log2}-value column per width drawn from the same distribution; "
+              f"oracle.scan_packed_threads on {threads} host threads")
     line = {
-        "impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "impl": "reference", "metric": METRIC, "value": round(gbs, 3), "unit": "GB/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic", "config": {"workload": WORKLOAD, "n_per_width_sampled": n},
-        "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": threads, "kind": "oracle", "sample": sample},
-        "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "cpu_baseline": {"value": round(gbs, 3), "unit": "GB/s", "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(gbs, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
@@ -403,7 +408,11 @@ def run_ours(args, world, rank, local):
                 "traffic_algorithmic": prof["algorithmic_bytes_per_launch"] if prof else None,
                 "traffic_case": prof["case"] if prof else None,
                 "traffic_ratio": (round(prof["dram_bytes_per_launch"] / prof["algorithmic_bytes_per_launch"], 4)
-                                  if prof else None)}
+                                  if prof else None),
+                "traffic_source": (f"not measured in this run: dram read + write bytes of one launch "
+                                   f"({prof['case']}) from the ncu capture in profiles/scan_full_traffic.json "
+                                   f"(same kernel source digest)" if prof else
+                                   "null: the committed ncu capture was taken on other kernel source")}
 
     # ---- realised selectivities
     realised = {}
@@ -471,11 +480,28 @@ def run_ours(args, world, rank, local):
             cols[b].upload_packed(host[b], up)
         e1.record(up)
         e1.synchronize()
-        e2e = {"value": step_bytes * args.steps * world / dt / 1e9, "unit": "GB/s",
+        # per-scan round trip, for contrast: every scan uploads its own column,
+        # scans it once (sigma = 0.1, branch-free) and reads its result back
+        # through scan_run before the next upload starts
+        one = None
+        torch.cuda.synchronize()
+        t_b = time.perf_counter()
+        for b in WIDTHS:
+            cols[b].upload_packed(host[b], stream)
+            lo, hi = preds[(b, 0.1)]
+            one = cols[b].run(lo, hi, "branchfree", stream)
+        dt1 = time.perf_counter() - t_b
+        assert one.count == int(r[order.index(("branchfree", 0.1, 32)), 0])
+        bytes1 = sum(bytes_of[b] for b in WIDTHS)
+        e2e = {"value": round(step_bytes * args.steps * world / dt / 1e9, 1), "unit": "GB/s",
                "h2d_bytes_per_step": h2d_bytes, "d2h_bytes_per_step": int(res_h.numel() * 8),
                "h2d_gbs_raw": round(h2d_bytes / (e0.elapsed_time(e1) * 1e-3) / 1e9, 1),
                "path": "per width: scan_column_upload_packed from pinned host memory, overlapped with the "
-                       "previous width's 12 scan_run_async calls; one result copy and one host sync per step"}
+                       "previous width's 12 scan_run_async calls (each upload serves the width's 12 scans); "
+                       "one result copy and one host sync per step",
+               "per_scan_roundtrip_gbs": round(bytes1 / dt1 / 1e9, 1),
+               "per_scan_roundtrip_path": "32 scans (b = 1..32, sigma 0.1): upload the column, one scan_run "
+                                          "with a host result, nothing overlapped"}
         del host
 
     # ---- CPU baseline: the oracle on a bounded sample, all host cores and one thread
@@ -495,24 +521,21 @@ def run_ours(args, world, rank, local):
                 out.append((b, t.cpu().numpy().view(np.uint32)))
             return out
 
-        host_cols = prefixes(1 << 27)
-        gbs, vps, scans, used, _ = cpu_sample(host_cols, threads, budget_s=10.0)
-        del host_cols
-        host_cols = prefixes(1 << 21)
-        gbs1, vps1, scans1, used1, per_b1 = cpu_sample(host_cols, 1, budget_s=2.0, passes_max=1)
+        host_cols = prefixes(1 << args.cpu_sample_log2)
+        gbs, vps, scans, used, _ = cpu_sample(host_cols, threads, budget_s=10.0, strategies=len(STRATS))
+        gbs1, vps1, scans1, used1, per_b1 = cpu_sample(host_cols, 1, budget_s=0.0, passes_max=1, sigmas=[0.1])
         del host_cols
         low = [v for b, v in per_b1.items() if b <= 16]
         cpu = {"value": round(gbs, 3), "unit": "GB/s", "cores": threads, "kind": "oracle",
-               "sample": f"{scans} scans (the sweep's sigma-outer, b-inner order) over the first 2^27 values of "
-                         f"each b=1..32 column ({used:.1f} s); oracle.scan_packed_threads",
+               "sample": f"{scans} scans (the sweep's 384-scan order, repeated within 10 s) over the first "
+                         f"2^{args.cpu_sample_log2} values of each b=1..32 column ({used:.1f} s); "
+                         f"oracle.scan_packed_threads",
                "cpu_model": cpu_model(),
                "values_per_s": round(vps, 1),
                "single_thread": {"gbs": round(gbs1, 3), "values_per_s": round(vps1, 1),
                                  "t_dec_gvals": round(statistics.median(low) / 1e9, 3) if low else None,
-                                 "sample": f"{scans1} scans over the first 2^21 values of each b=1..32 column "
-                                           f"({used1:.1f} s); oracle.scan_packed on one thread"},
-               "t_dec_note": "the oracle decodes one value at a time and stays compute-bound at every b on "
-                             "the host, so its T_dec is its values/s (median over b <= 16, one thread)"}
+                                 "sample": f"{scans1} scans (sigma 0.1) over the same 2^{args.cpu_sample_log2}-value "
+                                           f"prefixes ({used1:.1f} s); oracle.scan_packed on one thread"}}
 
     for c in cols.values():
         c.close()
@@ -531,36 +554,102 @@ def run_ours(args, world, rank, local):
     torch.cuda.empty_cache()
     serving = run_serving(args, dev, stream, gbscan) if not args.no_serve and world == 1 else None
 
-    line = {
+    detail = {"per_b": per_b, "branch_crossover": branch, "plain_scan": plain, "probes": probes,
+              "zone_sweep": zone, "select": select, "layouts": layouts, "conjunctive": conj,
+              "batched": batched, "serving": serving, "realised_sigma": realised, "roofline": roofline,
+              "law": law, "e2e": e2e, "cpu_baseline": cpu}
+    line = headline(args, world, value, ms_max, len(order), per_b, roofline, law, e2e, cpu,
+                    dict(plain=plain, probes=probes, zone=zone, select=select, layouts=layouts, conj=conj,
+                         batched=batched, serving=serving), beta_read, clocks)
+    if rank == 0:
+        if args.detail:
+            os.makedirs(os.path.dirname(os.path.abspath(args.detail)), exist_ok=True)
+            with open(args.detail, "w") as fh:
+                json.dump(detail, fh, indent=1)
+        print(json.dumps(line), flush=True)
+
+
+def headline(args, world, value, ms_max, scans_per_step, per_b, roofline, law, e2e, cpu, sections,
+             beta_read, clocks):
+    """The printed JSON line: the headline metric and a few KB of summary (the
+    detail sections go to the --detail file)."""
+    return {
         "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_per_width": N_SWEEP, "widths": "1..32", "sigmas": SIGMAS,
-                   "strategies": STRATS, "parallelism": f"replicas x{world} (independent sweeps, no collective)",
-                   "l2": "inputs larger than L2: each launch reads a different column than the one before; "
-                         "17.7 GB of columns per step vs 129 MB L2"},
+        "config": {"workload": WORKLOAD,
+                   "parallelism": f"replicas x{world} (independent sweeps, no collective)",
+                   "l2": "inputs larger than L2 (17.7 GB of columns per step, 129 MB L2; consecutive "
+                         "launches read different columns)"},
+        "values_per_s": round(N_SWEEP * scans_per_step * args.steps * world / (ms_max * 1e-3), 1),
         "beta_read_gbs": round(beta_read, 1),
-        "roofline": roofline,
-        "law": law,
-        "per_b": per_b,
-        "branch_crossover": branch,
-        "plain_scan": plain,
-        "probes": probes,
-        "zone_sweep": zone,
-        "select": select,
-        "layouts": layouts,
-        "conjunctive": conj,
-        "batched": batched,
-        "serving": serving,
-        "realised_sigma": realised,
-        "e2e": e2e,
-        "cpu_baseline": cpu,
-        "gpu_launches": len(order) * args.steps,
+        "f_by_b": {st: [round(per_b[str(b)][st]["f"], 3) for b in WIDTHS] for st in STRATS},
+        "roofline": compact_roofline(roofline),
+        "law": {st: {k: law[st][k] for k in ("t_dec_gvals", "b_star", "median_abs_err")} for st in STRATS},
+        "e2e": ({k: e2e[k] for k in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step",
+                                     "h2d_gbs_raw", "per_scan_roundtrip_gbs")}
+                | {"path": "C ABI from pinned host buffers; each upload serves its width's 12 scans "
+                           "(per-scan round trip beside it); paths in the detail file"} if e2e else None),
+        "cpu_baseline": ({k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample", "cpu_model",
+                                              "values_per_s")}
+                         | {"single_thread_gbs": cpu["single_thread"]["gbs"]} if cpu else None),
+        "summary": summarise(beta_read=beta_read, **sections),
+        "gpu_launches": scans_per_step * args.steps,
         "clocks": clocks,
         "source_digest": source_digest(),
+        "detail": os.path.relpath(args.detail, ROOT) if args.detail else None,
     }
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+
+
+def compact_roofline(r):
+    keys = ("kernel", "bound", "achieved", "peak", "unit", "frac", "peak_source", "frac_of_beta_read",
+            "achieved_branchfree", "achieved_branchy", "traffic", "traffic_ratio", "traffic_source")
+    return {k: r[k] for k in keys if k in r}
+
+
+def summarise(plain, probes, zone, select, layouts, conj, batched, serving, beta_read):
+    """A few figures per detail section for the printed line (the sections
+    themselves go to the detail file)."""
+    out = {}
+    if plain:
+        out["plain_scan_2p24_b8"] = {"us_l2_flushed": round(plain["ms_l2_flushed"] * 1e3, 2),
+                                     "gbs_l2_flushed": plain["gbs_l2_flushed"],
+                                     "us_l2_warm": round(plain["ms_l2_warm"] * 1e3, 2)}
+    if probes:
+        out["triad_gbs"] = probes["triad"]["gbs"]
+        dr = probes["decode_resident"]
+        out["t_dec_resident_gvals"] = dr["t_dec_median_below_ridge_gvals"]
+        out["negative_control_iii"] = dr.get("l2_control")
+    if zone:
+        rows = zone["rows"]
+        out["zone"] = {
+            "sorted_speedup_by_sigma": [r["speedup"] for r in rows if r["p"] == 0.0],
+            "min_speedup_p_ge_0.01": min(r["speedup"] for r in rows if r["p"] >= 0.01),
+            "sorted_speedup_zone_agg_min": min(r["speedup_zone_agg"] for r in rows if r["p"] == 0.0),
+            "exact": all(r["exact"] for r in rows)}
+    if select:
+        out["select_best_frac"] = {b: v["best_frac_branchfree"] for b, v in select["by_b"].items()}
+        out["select_exact"] = select["exact"]
+    if layouts:
+        out["layouts_t_dec_gvals"] = {k: v["t_dec_gvals"] for k, v in layouts["per_layout"].items()}
+    if conj:
+        out["conj_frac"] = [r["frac_conj"] for r in conj["rows"]]
+    if batched:
+        pl = batched["plans"]
+        out["batched"] = {"ms_per_column_graph": batched["ms_per_column_graph"],
+                          "ms": {k: v["ms"] for k, v in pl.items()},
+                          "speedup_law_vs_per_column": pl["law"]["speedup_vs_per_column_graph"],
+                          "exact": all(v["exact"] for v in pl.values())}
+        if "planner_vs_law" in batched:
+            out["batched"]["planner_vs_law"] = batched["planner_vs_law"]
+    if serving:
+        out["serving"] = {"serial_qps": serving["serial"]["qps"],
+                          "load": [x["load"] for x in serving["loads"]],
+                          "qps": [x["achieved_qps"] for x in serving["loads"]],
+                          "p50_us": [x["p50_us"] for x in serving["loads"]],
+                          "p99_us": [x["p99_us"] for x in serving["loads"]],
+                          "exact": all(x["exact_vs_alone"] for x in serving["loads"])}
+    return out
 
 
 def run_zone_sweep(args, dev, stream, gbscan):
@@ -897,6 +986,14 @@ def run_probes(args, dev, stream, gbscan, beta_read, law):
     ridge = law["branchfree"]["b_star"]
     below = [per_b[b]["gvals_per_s"] for b in WIDTHS if b < ridge]
     med = statistics.median(below) if below else None
+    # the paper's negative control (iii): a column resident in the last-level
+    # cache is scanned faster than the memory bandwidth beta; above the ridge
+    # (b >= 24, where decode does not bind) the slope-based rate is a read rate
+    wide = [per_b[b]["l2_gbs"] for b in WIDTHS if b >= 24]
+    l2_med = statistics.median(wide)
+    control = {"case": "L2-resident columns at b = 24..32, slope of t(N) - t(N/2) (fixed launch costs cancel)",
+               "l2_gbs_median": round(l2_med, 1), "l2_gbs_min": round(min(wide), 1),
+               "beta_read_gbs": round(beta_read, 1), "above_beta_read": bool(min(wide) > beta_read)}
     return {"triad": {"workload": "STREAM triad a = b + 3c over 2^28 float32 (3 GiB), best of 10",
                       "gbs": round(best, 1), "beta_read_gbs": round(beta_read, 1), "exact": triad_ok},
             "decode_resident": {"workload": "branch-free scan of an L2-resident column per b (N = six rounds of "
@@ -904,7 +1001,8 @@ def run_probes(args, dev, stream, gbscan, beta_read, law):
                                             "and N/2 values, CUDA graphs of 20 launches",
                                 "per_b": per_b, "t_dec_median_below_ridge_gvals": med,
                                 "t_dec_fitted_gvals": fitted, "b_star_fitted": ridge,
-                                "resident_over_fitted": round(med / fitted, 3) if med and fitted else None}}
+                                "resident_over_fitted": round(med / fitted, 3) if med and fitted else None,
+                                "l2_control": control}}
 
 
 def run_plain(args, dev, stream, gbscan, beta_read):
@@ -1198,6 +1296,91 @@ def run_serving(args, dev, stream, gbscan):
     return out
 
 
+def run_case(args):
+    """One configuration run a few times, for ncu captures and quick timing.
+
+      python bench.py --case scan --b 8 --n 268435456 --sigma 0.1 --strategy branchfree --reps 3
+      python bench.py --case select --b 16 --n 67108864 --sigma 0.5 --strategy branchy
+      python bench.py --case batch --batch-cols 4096 --n 2147483648 --strategy branchfree
+
+    scan / select: one device-resident column of n values at width b (drawn and
+    encoded on the device; uniform, sorted or 1%-displaced), scanned `reps`
+    times.  batch: the batched workload recipe scaled to `batch-cols` columns
+    and n values in total, one graph launch per rep.  Prints the CUDA-event time
+    of the last launch; under ncu pick launches with -k and -s/-c."""
+    import torch
+
+    from paper_2606_22423_gb300 import build as libbuild
+    from paper_2606_22423_gb300 import gbscan
+
+    libbuild.build()
+    gbscan.load()
+    s = torch.cuda.Stream()
+    if args.case == "batch":
+        spec = synth.batch_spec(synth.seed_for(4), ncols=args.batch_cols, total=args.n)
+        cols, preds = [], []
+        with torch.cuda.stream(s):
+            for i, (n, b, p, sigma) in enumerate(spec):
+                v = (synth.uniform_values_device(synth.seed_for(4, i), n, b) if p is None
+                     else synth.clustered_values_device(synth.seed_for(4, i), n, b, p))
+                c = gbscan.Column.from_device(v, n, b, stream=s)
+                c.zonemap_build(s)
+                cols.append(c)
+                preds.append(synth.pick_range(synth.seed_for(4, i, 1), b, sigma))
+        torch.cuda.synchronize()
+        bt = gbscan.Batch(cols, [args.strategy] * len(cols))
+        parr = gbscan.Batch.pred_array(preds)
+        out = torch.zeros((len(cols), 4), dtype=torch.int64, device="cuda")
+        ms = 0.0
+        for _ in range(args.reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            bt.run(parr, stream=s, dev_out=out, host=False)
+            e1.record(s)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+        nbytes = sum(gbscan.scan_packed_words(x[0], x[1]) * 4 for x in spec)
+        print(json.dumps({"case": "batch", "batch": len(cols), "values": sum(x[0] for x in spec),
+                          "strategy": args.strategy, "ms": ms, "gbs": nbytes / (ms * 1e-3) / 1e9}))
+        bt.close()
+        for c in cols:
+            c.close()
+        return
+    with torch.cuda.stream(s):
+        seed = synth.seed_for(7, args.b)
+        if args.order == "uniform":
+            v = synth.uniform_values_device(seed, args.n, args.b)
+        else:
+            v = synth.clustered_values_device(seed, args.n, args.b, 0.0 if args.order == "sorted" else 0.01)
+        col = gbscan.Column.from_device(v, args.n, args.b, stream=s)
+        del v
+    if args.strategy.startswith("zone") or args.strategy == "auto":
+        col.zonemap_build(s)
+    lo, hi = synth.pick_range(synth.seed_for(7, args.b, 1), args.b, args.sigma)
+    out = torch.zeros(4, dtype=torch.int64, device="cuda")
+    select = args.case == "select"
+    pos = torch.empty(args.n if select else 1, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    ms = 0.0
+    for _ in range(args.reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        if select:
+            col.select_async(lo, hi, pos, out, args.strategy, stream=s)
+        else:
+            col.run_async(lo, hi, out, args.strategy, s)
+        e1.record(s)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+    col.status(s)
+    r = out.cpu().tolist()
+    nbytes = gbscan.scan_packed_words(args.n, args.b) * 4 + (4 * r[0] if select else 0)
+    print(json.dumps({"case": args.case, "b": args.b, "n": args.n, "strategy": args.strategy,
+                      "order": args.order, "ms": ms, "gbs": nbytes / (ms * 1e-3) / 1e9,
+                      "count": r[0], "sum": r[1], "blocks": r[2]}))
+    col.close()
+
+
 def cudart_copy(dst_tensor, src_ptr: int, nbytes: int):
     """Device-to-device copy from a raw pointer the library owns into a torch tensor."""
     import ctypes
@@ -1230,7 +1413,23 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the plain-scan and zone-sweep sections")
     ap.add_argument("--serve-seconds", type=float, default=1.5)
+    ap.add_argument("--detail", default=os.path.join(ROOT, "bench_detail.json"),
+                    help="file that receives every detail section (the printed line carries a summary)")
+    ap.add_argument("--case", choices=["scan", "select", "batch"], default=None,
+                    help="run one configuration (for ncu captures) instead of the benchmark")
+    ap.add_argument("--b", type=int, default=16)
+    ap.add_argument("--n", type=int, default=1 << 27)
+    ap.add_argument("--sigma", type=float, default=0.1)
+    ap.add_argument("--strategy", default="branchfree")
+    ap.add_argument("--order", default="uniform", choices=["uniform", "sorted", "swapped"])
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--batch-cols", type=int, default=4096)
+    ap.add_argument("--cpu-sample-log2", type=int, default=CPU_SAMPLE_LOG2,
+                    help="log2 of the column prefix both oracle legs scan")
     args = ap.parse_args()
+    if args.case:
+        run_case(args)
+        return
     if args.warmup < 3:
         args.warmup = 3
     world, rank, local = dist_setup()

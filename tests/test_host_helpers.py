@@ -1,6 +1,7 @@
 """Host-side helpers of the planner and the bench, on CPU: the per-strategy
 calibration of the law's log times, the calibrated prior, and the oracle
 timing loop that the bench's CPU baseline reports."""
+import os
 import numpy as np
 import pytest
 
@@ -46,3 +47,57 @@ def test_cpu_sample_covers_the_sweep_order_and_reports_per_width_rates():
     _, _, scans2, _, _ = bench.cpu_sample(cols, 2, budget_s=1e9, passes_max=2)
     assert scans2 == 2 * scans                              # the pass cap bounds the sample
     assert isinstance(bench.cpu_model(), str) and bench.cpu_model()
+
+
+def test_headline_line_stays_small_with_every_section_present():
+    """The printed bench line must stay a few KB (a consumer that keeps only the
+    tail of stdout must still see one whole line); the sections go to a file."""
+    import argparse
+    import json
+
+    import bench
+
+    W, S = bench.WIDTHS, bench.SIGMAS
+    per_b = {str(b): {st: {"f": 0.91234, "gbs": 6000.1} for st in bench.STRATS} for b in W}
+    law = {st: {"t_dec_gvals": 4.0, "b_star": 14.2, "median_abs_err": 0.05, "rms_err": 0.1} for st in bench.STRATS}
+    roof = {"kernel": "k", "bound": "hbm", "achieved": 6300.0, "peak": 6702.8, "unit": "GB/s", "frac": 0.94,
+            "peak_source": "measured", "frac_of_beta_read": 0.9, "achieved_branchfree": 6500.0,
+            "achieved_branchy": 6100.0, "time_share_of_step": {"branchfree": 0.45}, "traffic": 808977152,
+            "traffic_ratio": 1.0046, "traffic_source": "x" * 180}
+    e2e = {"value": 2100.0, "unit": "GB/s", "h2d_bytes_per_step": 17716740096, "d2h_bytes_per_step": 12288,
+           "h2d_gbs_raw": 211.0, "path": "y" * 250, "per_scan_roundtrip_gbs": 190.0,
+           "per_scan_roundtrip_path": "z" * 120}
+    cpu = {"value": 12.4, "unit": "GB/s", "cores": 16, "kind": "oracle", "sample": "s" * 180,
+           "cpu_model": "Arm Neoverse V2", "values_per_s": 6.0e9, "single_thread": {"gbs": 0.84}}
+    sections = {
+        "plain": {"ms_l2_flushed": 0.0105, "gbs_l2_flushed": 1600.0, "ms_l2_warm": 0.0082},
+        "probes": {"triad": {"gbs": 6700.0}, "decode_resident": {
+            "t_dec_median_below_ridge_gvals": 5.0,
+            "l2_control": {"case": "c" * 100, "l2_gbs_median": 8500.0, "l2_gbs_min": 8100.0,
+                           "beta_read_gbs": 7100.0, "above_beta_read": True}}},
+        "zone": {"rows": [{"p": p, "sigma": s, "speedup": 12.5, "speedup_zone_agg": 13.1, "exact": True}
+                          for p in (0.0, 0.01, 0.1, 1.0) for s in (1e-4, 1e-3, 1e-2, 0.1, 0.5)]},
+        "select": {"by_b": {"32": {"best_frac_branchfree": 0.95}, "16": {"best_frac_branchfree": 0.79}},
+                   "exact": True},
+        "layouts": {"per_layout": {k: {"t_dec_gvals": 3.5} for k in ("lanes", "rowmajor", "bytes")}},
+        "conj": {"rows": [{"frac_conj": 0.77} for _ in range(4)]},
+        "batched": {"ms_per_column_graph": 23.7, "plans": {
+            k: {"ms": 0.97, "speedup_vs_per_column_graph": 24.4, "exact": True}
+            for k in ("branchfree", "law", "planned_mlp", "law_calibrated", "planned_mlp_law_prior")},
+            "planner_vs_law": {"speedup_median": 1.01, "spread": [0.98, 1.03], "retrainings": 3}},
+        "serving": {"serial": {"qps": 3200.0}, "loads": [
+            {"load": f, "achieved_qps": 800.0, "p50_us": 220.0, "p99_us": 600.0, "exact_vs_alone": True}
+            for f in (0.25, 0.5, 0.9, 1.5)]},
+    }
+    args = argparse.Namespace(steps=20, warmup=5, detail=os.path.join(bench.ROOT, "bench_detail.json"))
+    clocks = {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 100}
+    line = bench.headline(args, 1, 5080.0, 838.0, 384, per_b, roof, law, e2e, cpu, sections, 7100.0, clocks)
+    text = json.dumps(line)
+    assert len(text) < 4096, len(text)
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "roofline", "e2e", "cpu_baseline",
+                "gpu_launches", "clocks"):
+        assert key in line
+    assert line["roofline"]["frac"] == 0.94 and line["cpu_baseline"]["kind"] == "oracle"
+    assert line["summary"]["negative_control_iii"]["above_beta_read"] is True
+    assert line["gpu_launches"] == 384 * 20

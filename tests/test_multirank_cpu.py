@@ -12,7 +12,7 @@ def test_reference_arm_under_two_gloo_ranks():
     env = dict(os.environ, CUDA_VISIBLE_DEVICES="", MASTER_ADDR="127.0.0.1")
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node=2",
            "--master-addr", "127.0.0.1", "--master-port", "29533", "bench.py", "--impl", "reference",
-           "--gpus", "2", "--steps", "1", "--warmup", "3"]
+           "--gpus", "2", "--steps", "1", "--warmup", "3", "--cpu-sample-log2", "16"]
     r = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
