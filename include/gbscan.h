@@ -209,8 +209,10 @@ scan_status scan_column_blocksums(const scan_column *col, const uint64_t **dev_b
 scan_status scan_run(scan_column *col, scan_pred pred, scan_strategy strategy, void *stream,
                      scan_result *host_out);
 
-/* As scan_run, but writes the 32-byte result to device memory and returns
- * without waiting.  Check scan_column_status afterwards for device errors. */
+/* As scan_run, but writes the 32-byte result to device memory (dev_out,
+ * caller-owned, 8-byte aligned; SCAN_EINVAL otherwise, checked before any
+ * CUDA call) and returns without waiting.  Check scan_column_status
+ * afterwards for device errors. */
 scan_status scan_run_async(scan_column *col, scan_pred pred, scan_strategy strategy, void *stream,
                            scan_result *dev_out);
 
@@ -441,7 +443,9 @@ scan_status scan_server_destroy(scan_server *server);
  * GPU with more SMs than that is refused with SCAN_EINVAL.
  *   - Outputs: *dev_out gets the 32-byte result, *dev_status gets 0 or error
  *     bits (nonzero means a bounded device wait gave up and the result is not
- *     valid); both are caller-owned device memory, written asynchronously.
+ *     valid); both are caller-owned device memory, written asynchronously;
+ *     dev_out must be 8-byte and dev_status 4-byte aligned (checked, with
+ *     the other arguments, before any CUDA call).
  *   - strategy: SCAN_AUTO / SCAN_BRANCHFREE or SCAN_BRANCHY; zone-skip
  *     strategies need a zone map and are refused with SCAN_EINVAL.
  *   - The first call on each device looks up the scratch array's address

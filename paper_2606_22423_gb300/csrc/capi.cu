@@ -897,6 +897,7 @@ scan_status scan_run_async(scan_column* col, scan_pred pred, scan_strategy strat
 {
     g_err.clear();
     if (!col || !dev_out) return fail(SCAN_EINVAL, "null pointer");
+    if (reinterpret_cast<uintptr_t>(dev_out) & 7u) return fail(SCAN_EINVAL, "dev_out must be 8-byte aligned");
     bool empty = false;
     scan_status s = enqueue_scan(col, pred, strategy, as_stream(stream),
                                  reinterpret_cast<long long*>(dev_out), &empty);

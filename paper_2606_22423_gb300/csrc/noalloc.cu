@@ -72,6 +72,12 @@ extern "C" scan_status scan_run_packed_noalloc(const uint32_t* dev_packed, uint6
 {
     gb_set_last_error("");
     if (!dev_out || !dev_status) return noalloc_fail(SCAN_EINVAL, "dev_out and dev_status are required");
+    // the kernel stores 64-bit words to dev_out and a 32-bit word to dev_status:
+    // a misaligned pointer would fault on the device, so refuse it here
+    if (reinterpret_cast<uintptr_t>(dev_out) & 7u)
+        return noalloc_fail(SCAN_EINVAL, "dev_out must be 8-byte aligned");
+    if (reinterpret_cast<uintptr_t>(dev_status) & 3u)
+        return noalloc_fail(SCAN_EINVAL, "dev_status must be 4-byte aligned");
     if (b < 1 || b > 32 || static_cast<uint64_t>(base) + ((1ull << b) - 1ull) > 0xffffffffull)
         return noalloc_fail(SCAN_EINVAL, "bad width or frame-of-reference base");
     if (n > (1ull << 31)) return noalloc_fail(SCAN_EINVAL, "n exceeds the 2^31-value maximum");

@@ -102,3 +102,42 @@ def test_batch_device_results_and_zone_requirement():
     plain.close()
     for c in cols:
         c.close()
+
+
+def test_full_size_batch_4096_columns_against_the_oracle():
+    """The batched workload at full size (4096 columns, lengths log-uniform in
+    [2^10, 2^26] scaled to 2^31 values in total, b uniform in 1..32, half
+    uniform / half sorted with displacement, sigma log-uniform in [1e-4, 1]),
+    drawn on the device as the benchmark does: every column's COUNT/SUM under
+    every plan equals brute force over the generator's raw values (all 4096
+    columns, no sampling)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    spec = synth.batch_spec(synth.seed_for(4))
+    cols, raws, preds = [], [], []
+    for i, (n, b, p, sigma) in enumerate(spec):
+        seed = synth.seed_for(4, i)
+        v = (synth.uniform_values_device(seed, n, b) if p is None
+             else synth.clustered_values_device(seed, n, b, p))
+        c = gbscan.Column.from_device(v, n, b)
+        c.zonemap_build()
+        cols.append(c)
+        raws.append(v.cpu().numpy().view(np.uint32))
+        preds.append(synth.pick_range(synth.seed_for(4, i, 1), b, sigma))
+        del v
+    assert sum(x[0] for x in spec) <= 1 << 31 and len(cols) == 4096
+    with ThreadPoolExecutor(16) as ex:
+        want = list(ex.map(lambda i: oracle.scan_values(raws[i], *preds[i]), range(len(cols))))
+    del raws
+    plans = {s: [s] * len(cols) for s in ALL}
+    plans["mixed"] = [ALL[i % 4] for i in range(len(cols))]
+    for name, strategies in plans.items():
+        bt = gbscan.Batch(cols, strategies)
+        for _ in range(2):                                  # the graph replayed
+            got = bt.run(preds)
+            bad = [i for i in range(len(cols)) if got[i].pair() != want[i]]
+            assert not bad, (name, bad[:5])
+        bt.close()
+    for c in cols:
+        c.close()
+    torch.cuda.empty_cache()

@@ -112,3 +112,21 @@ def test_triad_probe_rejects_bad_arguments(lib):
             gbscan.scan_probe_triad(a, b, c, 3.0, n)
         assert e.value.status == gbscan.SCAN_EINVAL
         assert why in str(e.value)
+
+
+def test_device_result_pointers_must_be_aligned(lib):
+    """The kernels store 64-bit words to the result and a 32-bit status word: a
+    misaligned caller pointer is refused with SCAN_EINVAL before any CUDA call
+    (the pointers below are never touched)."""
+    import ctypes
+
+    for out, status, why in [(0x2004, 0x3000, "dev_out must be 8-byte aligned"),
+                             (0x2000, 0x3002, "dev_status must be 4-byte aligned")]:
+        with pytest.raises(gbscan.ScanError) as e:
+            gbscan.scan_run_packed_noalloc(0x1000, 4096, 9, 0, 0, 10, out, status)
+        assert e.value.status == gbscan.SCAN_EINVAL and why in str(e.value)
+    # scan_run_async checks its result pointer before it reads the column handle
+    rc = lib.scan_run_async(ctypes.c_void_p(0x10), gbscan.scan_pred(0, 10), gbscan.SCAN_BRANCHFREE, None,
+                            ctypes.c_void_p(0x2001))
+    assert rc == gbscan.SCAN_EINVAL
+    assert "8-byte aligned" in lib.scan_last_error().decode()

@@ -174,45 +174,75 @@ def test_maximum_size_and_largest_sum():
 
 
 def _device_column(b, n, seed, p=None):
+    """A column drawn and encoded on the device (the benchmark's path), with host
+    copies of the generator's raw values and of the library's packed words."""
     v = (synth.uniform_values_device(seed, n, b) if p is None
          else synth.clustered_values_device(seed, n, b, p))
     col = gbscan.Column.from_device(v, n, b)
+    raw = v.cpu().numpy().view(np.uint32)
     host = d2h_u32(col.dev_packed, gbscan.scan_packed_words(n, b))
     del v
-    return col, host
+    return col, raw, host
+
+
+def _brute_force(raw, preds):
+    """oracle.scan_values over the raw values for every predicate, in threads
+    (the C loop releases the interpreter lock)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    with ThreadPoolExecutor(len(preds)) as ex:
+        return list(ex.map(lambda pr: oracle.scan_values(raw, *pr), preds))
 
 
 def test_plain_scan_n2pow24_b8():
     # plain single-column scan: 2^24 uniform values in [0, 2^8), sigma = 0.1
     n, b = 1 << 24, 8
-    col, words = _device_column(b, n, synth.seed_for(1))
+    col, raw, words = _device_column(b, n, synth.seed_for(1))
+    np.testing.assert_array_equal(words, oracle.pack(raw, b))
     lo, hi = synth.pick_range(synth.seed_for(1, 0, 1), b, 0.1)
-    want = oracle.scan_packed_threads(words, n, b, 0, lo, hi, 8)
+    want = oracle.scan_values(raw, lo, hi)
+    assert want == oracle.scan_packed_threads(words, n, b, 0, lo, hi, 8)
     for strat in ["branchfree", "branchy"]:
         assert col.run(lo, hi, strat).pair() == want
     col.close()
 
 
 @pytest.mark.parametrize("b", [1, 7, 16, 23, 32])
-def test_sweep_size_n2pow28_sampled(b):
+def test_sweep_size_n2pow28_from_raw_values(b):
+    """The sweep's column size, drawn and encoded on the device as the benchmark
+    does: the library's words equal oracle.pack of the generator's raw values,
+    and every strategy's COUNT/SUM equals brute force over those raw values."""
     n = 1 << 28
-    col, words = _device_column(b, n, synth.seed_for(2, b))
-    for s in [1e-3, 0.5]:
-        lo, hi = synth.pick_range(synth.seed_for(2, b, int(s * 1000)), b, s)
-        want = oracle.scan_packed_threads(words, n, b, 0, lo, hi, 16)
-        for strat in ["branchfree", "branchy"]:
-            assert col.run(lo, hi, strat).pair() == want, (b, s, strat)
+    col, raw, words = _device_column(b, n, synth.seed_for(2, b))
+    np.testing.assert_array_equal(words, oracle.pack(raw, b))
+    col.zonemap_build()
+    preds = [synth.pick_range(synth.seed_for(2, b, int(s * 1000)), b, s) for s in [1e-3, 0.5]]
+    for (lo, hi), want in zip(preds, _brute_force(raw, preds)):
+        for strat in ["branchfree", "branchy", "zone_bf", "zone_br", "zone_agg_bf"]:
+            r = col.run(lo, hi, strat)
+            assert r.pair() == want, (b, lo, hi, strat)
+            if not strat.startswith("zone"):
+                assert r.blocks_scanned == n // 1024
     col.close()
 
 
-def test_zone_size_n2pow30_b16_sampled():
+def test_zone_size_n2pow30_b16_from_raw_values():
+    """The zone sweep's column (2^30 values at b = 16, 1% displaced): encoder
+    bytes, zone maps, every strategy and the blocks read against the oracle."""
     n, b = 1 << 30, 16
-    col, words = _device_column(b, n, synth.seed_for(3, 0, 1), p=0.01)
+    col, raw, words = _device_column(b, n, synth.seed_for(3, 0, 1), p=0.01)
+    np.testing.assert_array_equal(words, oracle.pack(raw, b))
     col.zonemap_build()
-    lo, hi = synth.pick_range(synth.seed_for(3, 0, 2), b, 1e-3)
-    full = col.run(lo, hi, "branchfree")
-    skip = col.run(lo, hi, "zone_bf")
-    assert skip.pair() == full.pair()
-    assert full.pair() == oracle.scan_packed_threads(words, n, b, 0, lo, hi, 16)
-    assert skip.blocks_scanned < full.blocks_scanned
+    zmin, zmax = oracle.zonemap(words, n, b)
+    preds = [synth.pick_range(synth.seed_for(3, 0, 2 + i), b, s) for i, s in enumerate([1e-4, 1e-3, 0.1])]
+    for (lo, hi), want in zip(preds, _brute_force(raw, preds)):
+        zc, zs, touched = oracle.scan_zoneskip(words, zmin, zmax, n, b, 0, lo, hi)
+        assert (zc, zs) == want
+        full = col.run(lo, hi, "branchfree")
+        assert full.pair() == want and full.blocks_scanned == n // 1024
+        for strat in ["branchy", "zone_bf", "zone_br", "zone_agg_bf"]:
+            r = col.run(lo, hi, strat)
+            assert r.pair() == want, (lo, hi, strat)
+            if strat in ("zone_bf", "zone_br"):
+                assert r.blocks_scanned == touched
     col.close()

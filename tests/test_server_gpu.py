@@ -106,3 +106,43 @@ def test_admission_queue_limit_and_small_slots(table):
     with pytest.raises(gbscan.ScanError):            # more scans than one slot holds
         srv.submit(list(range(9)), [(0, 5)] * 9)
     srv.close()
+
+
+def test_served_query_at_the_serving_table_size_against_the_oracle():
+    """Columns of the serving table's size (2^27 values; b in {4, 8, 12, 16, 24,
+    32}; sorted and shuffled), drawn on the device: an 8-column query and a
+    burst of smaller ones served together give brute force over the raw values."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    widths = [4, 8, 12, 16, 24, 32]
+    n = 1 << 27
+    cols, raws = [], []
+    for c in range(8):
+        b = widths[c % 6]
+        seed = synth.seed_for(5, c)
+        v = (synth.clustered_values_device(seed, n, b, 0.0) if c % 2 == 0
+             else synth.uniform_values_device(seed, n, b))
+        col = gbscan.Column.from_device(v, n, b)
+        col.zonemap_build()
+        cols.append(col)
+        raws.append(v.cpu().numpy().view(np.uint32))
+        del v
+    rng = np.random.default_rng(synth.seed_for(5, 0, 7))
+    queries = [(list(range(8)), [synth.pick_range(int(rng.integers(1 << 30)), cols[c].b,
+                                                  float(synth.log_uniform(rng, 1e-4, 1.0))) for c in range(8)])]
+    queries += [q for q in _queries(cols, 12, 3)]
+    srv = gbscan.Server(cols, slots=4, device_bytes_per_slot=112 * 512)
+    ids = [srv.submit(ids_, preds) for ids_, preds in queries]          # submitted back to back
+    jobs = [(c, lo, hi) for ids_, preds in queries for c, (lo, hi) in zip(ids_, preds)]
+    with ThreadPoolExecutor(16) as ex:
+        flat = list(ex.map(lambda j: oracle.scan_values(raws[j[0]], j[1], j[2]), jobs))
+    k = 0
+    for qid, (ids_, preds) in zip(ids, queries):
+        done, res, _ = srv.poll(qid, len(ids_), wait=True)
+        assert done
+        assert [r.pair() for r in res] == flat[k:k + len(ids_)]
+        k += len(ids_)
+    srv.close()
+    for c in cols:
+        c.close()
+    torch.cuda.empty_cache()
