@@ -323,6 +323,50 @@ def run_ours(args, world, rank, local):
             if evs is not None:
                 evs[i][1].record(stream)
 
+    def one_step_ms():
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        step()
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    # ---- launch shapes: the autotuner times every candidate shape of both
+    # full-scan kernels at every width on the resident columns (sigma = 0.1) and
+    # installs the fastest; the timed steps below run with the tuned shapes
+    tune = None
+    gbscan.autotune_reset()
+    if args.shapes:
+        gbscan.autotune_load(args.shapes)
+        tune = {"source": f"loaded from {args.shapes}"}
+    elif not args.no_tune:
+        t_tune = time.perf_counter()
+        per_b_tune = {}
+        for b in WIDTHS:
+            lo, hi = preds[(b, 0.1)]
+            for st in STRATS:
+                r_ = cols[b].autotune(lo, hi, st, reps=3, stream=stream)
+                per_b_tune.setdefault(str(b), {})[st] = {
+                    "shape": [r_["best"][k] for k in ("warps", "stages", "tile_blocks", "vote_rows")],
+                    "us": round(r_["best_us"], 2), "rule_us": round(r_["rule_us"], 2),
+                    "candidates": r_["candidates"]}
+        tune_s = time.perf_counter() - t_tune
+        shapes_path = os.path.join(os.path.dirname(os.path.abspath(args.detail or "bench_detail.json")),
+                                   "bench_shapes.txt")
+        gbscan.autotune_save(shapes_path)
+        tuned_ms = one_step_ms()
+        gbscan.autotune_reset()
+        rule_ms = one_step_ms()
+        gbscan.autotune_load(shapes_path)
+        tune = {"workload": "every candidate shape of the branch-free and branchy full scans, per width, on "
+                            "the resident 2^28-value sweep columns at sigma 0.1 (3 back-to-back scans each, the "
+                            "three fastest re-timed against the rule); shape = [warps, stages, tile_blocks, "
+                            "vote_rows]",
+                "seconds": round(tune_s, 1), "saved_to": os.path.relpath(shapes_path, ROOT),
+                "sweep_step_ms_rule": round(rule_ms, 3), "sweep_step_ms_tuned": round(tuned_ms, 3),
+                "sweep_gain": round(rule_ms / tuned_ms, 4), "per_b": per_b_tune}
+
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -554,13 +598,13 @@ def run_ours(args, world, rank, local):
     torch.cuda.empty_cache()
     serving = run_serving(args, dev, stream, gbscan) if not args.no_serve and world == 1 else None
 
-    detail = {"per_b": per_b, "branch_crossover": branch, "plain_scan": plain, "probes": probes,
+    detail = {"autotune": tune, "per_b": per_b, "branch_crossover": branch, "plain_scan": plain, "probes": probes,
               "zone_sweep": zone, "select": select, "layouts": layouts, "conjunctive": conj,
               "batched": batched, "serving": serving, "realised_sigma": realised, "roofline": roofline,
               "law": law, "e2e": e2e, "cpu_baseline": cpu}
     line = headline(args, world, value, ms_max, len(order), per_b, roofline, law, e2e, cpu,
                     dict(plain=plain, probes=probes, zone=zone, select=select, layouts=layouts, conj=conj,
-                         batched=batched, serving=serving), beta_read, clocks)
+                         batched=batched, serving=serving, tune=tune), beta_read, clocks)
     if rank == 0:
         if args.detail:
             os.makedirs(os.path.dirname(os.path.abspath(args.detail)), exist_ok=True)
@@ -607,10 +651,13 @@ def compact_roofline(r):
     return {k: r[k] for k in keys if k in r}
 
 
-def summarise(plain, probes, zone, select, layouts, conj, batched, serving, beta_read):
+def summarise(plain, probes, zone, select, layouts, conj, batched, serving, beta_read, tune=None):
     """A few figures per detail section for the printed line (the sections
     themselves go to the detail file)."""
     out = {}
+    if tune and "sweep_gain" in tune:
+        out["autotune"] = {"sweep_step_ms_rule": tune["sweep_step_ms_rule"],
+                           "sweep_step_ms_tuned": tune["sweep_step_ms_tuned"], "gain": tune["sweep_gain"]}
     if plain:
         out["plain_scan_2p24_b8"] = {"us_l2_flushed": round(plain["ms_l2_flushed"] * 1e3, 2),
                                      "gbs_l2_flushed": plain["gbs_l2_flushed"],
@@ -662,7 +709,9 @@ def run_zone_sweep(args, dev, stream, gbscan):
                        "sigma in {1e-4,1e-3,1e-2,0.1,0.5}; full scan, zone skip, and zone skip answering "
                        "wholly-inside blocks from per-block (min, max, sum)", "rows": []}
     res = torch.zeros((3, 4), dtype=torch.int64, device=dev)
-    for pi, p in enumerate([0.0, 0.01, 0.1, 1.0]):
+    # the 1%-displaced column first: the zone-skip kernel's shape is tuned on it
+    # (sigma 0.1, most blocks survive) and then used for every row
+    for pi, p in [(1, 0.01), (0, 0.0), (2, 0.1), (3, 1.0)]:
         with torch.cuda.stream(stream):
             v = synth.clustered_values_device(synth.seed_for(3, pi), n, b, p, device=dev)
             col = gbscan.Column.from_device(v, n, b, stream=stream)
@@ -670,6 +719,11 @@ def run_zone_sweep(args, dev, stream, gbscan):
             col.zonemap_build(stream)
         torch.cuda.synchronize()
         torch.cuda.empty_cache()
+        if pi == 1 and not args.no_tune and not args.shapes:
+            lo, hi = synth.pick_range(synth.seed_for(3, pi, 4), b, 0.1)
+            r_ = col.autotune(lo, hi, "zone_bf", reps=3, stream=stream)
+            out["zone_bf_shape"] = {"shape": r_["best"], "us": round(r_["best_us"], 2),
+                                    "rule_us": round(r_["rule_us"], 2)}
         for si, sigma in enumerate([1e-4, 1e-3, 1e-2, 0.1, 0.5]):
             lo, hi = synth.pick_range(synth.seed_for(3, pi, si + 1), b, sigma)
             ts = {}
@@ -1424,6 +1478,8 @@ def main():
     ap.add_argument("--order", default="uniform", choices=["uniform", "sorted", "swapped"])
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--batch-cols", type=int, default=4096)
+    ap.add_argument("--no-tune", action="store_true", help="time the sweep with the built-in launch shapes")
+    ap.add_argument("--shapes", default=None, help="load tuned launch shapes from this cache instead of tuning")
     ap.add_argument("--cpu-sample-log2", type=int, default=CPU_SAMPLE_LOG2,
                     help="log2 of the column prefix both oracle legs scan")
     args = ap.parse_args()

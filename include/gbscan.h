@@ -495,9 +495,75 @@ scan_status scan_selftest_wait_timeout(uint64_t limit_ns, void *stream);
  * broken.  Nothing is written. */
 scan_status scan_selftest_select_timeout(scan_column *col, uint64_t limit_ns, void *stream);
 
-/* Number of SMs and the persistent grid size the scan kernels use for width b. */
+/* Number of SMs, the persistent grid size and the current shape (tuned or
+ * the built-in rule) of the branch-free full scan at width b. */
 scan_status scan_launch_shape(uint32_t b, uint32_t *sms, uint32_t *ctas, uint32_t *warps_per_cta,
                               uint32_t *blocks_per_tile, uint32_t *stages);
+
+/* ------------------------------------------------------ launch shapes */
+
+/* Launch shape of a persistent scan kernel (no paper counterpart: the paper's
+ * single-thread decoders have no launch geometry; the shapes only change how
+ * the fused scan of §3 is spread over the GPU, never its result).  One CTA per
+ * SM of `warps` warps; each warp streams tiles of `tile_blocks` 1024-value
+ * blocks through `stages` shared-memory slots (the zone-skip kernels pop
+ * `tile_blocks` candidate blocks at a time); vote_rows = 1 makes the branchy
+ * kernel vote once per row of a thread's lanes instead of once per value.
+ * Legal shapes: full scans 1..16 warps, zone-skip scans 1..8; 1..6 stages;
+ * tile_blocks a positive multiple of the warp step (4 for b <= 16, else 2),
+ * at most 64 (full) or 32 (zone skip); vote_rows only for SCAN_BRANCHY at
+ * b <= 21; warps * stages * (tile_blocks * 128 * b + 12) <= 226 KB (the
+ * kernels keep up to 1 KB of static shared memory). */
+typedef struct {
+    uint32_t warps, stages, tile_blocks, vote_rows;
+} scan_shape;
+
+/* Tuning outcome for one (strategy, b): the installed shape and the rule's,
+ * their mean times per scan on the tuning column, and the candidates timed. */
+typedef struct {
+    scan_shape best, rule;
+    float best_us, rule_us;
+    uint32_t candidates;
+} scan_tune_result;
+
+/* Shapes are kept per (kernel, b) for four kernels: SCAN_AUTO/SCAN_BRANCHFREE
+ * (branch-free full scan), SCAN_BRANCHY, SCAN_ZONE_SKIP_BF (with
+ * SCAN_ZONE_AGG_BF) and SCAN_ZONE_SKIP_BR (with SCAN_ZONE_AGG_BR); every
+ * later launch of that kernel at that width uses the installed shape.  The
+ * table is process-wide; changing it while scans are being enqueued on other
+ * threads is safe, but a scan picks up whichever shape is current when it is
+ * enqueued.  Every call below returns SCAN_EINVAL for a bad width, strategy or
+ * shape (scan_last_error names the rule). */
+scan_status scan_shape_get(uint32_t b, scan_strategy strategy, scan_shape *out);
+/* Install `shape` (validated), or the built-in rule again if shape is NULL. */
+scan_status scan_shape_set(uint32_t b, scan_strategy strategy, const scan_shape *shape);
+/* The tuner's candidate shapes for (strategy, b): *count gets their number,
+ * out (may be NULL) the first min(capacity, count) of them. */
+scan_status scan_shape_candidates(uint32_t b, scan_strategy strategy, scan_shape *out, uint32_t capacity,
+                                  uint32_t *count);
+/* Autotune the kernel of `strategy` at col's width: time every candidate on
+ * this column and predicate (`reps` back-to-back scans each, on `stream`),
+ * re-time the three fastest against the rule three times, interleaved, and
+ * install the fastest if it beats the rule (otherwise the rule stays).
+ * Blocking.  Tune on a column larger than L2 (at least 2^26 values at small
+ * b) so that the copies stream from HBM, with a predicate that selects
+ * something; zone-skip strategies need a built zone map.  The column's
+ * results are unaffected.  SCAN_ENOMEM / SCAN_ECUDA / SCAN_ETIMEOUT as for
+ * scans; on failure the previous shape stays installed. */
+scan_status scan_autotune_column(scan_column *col, scan_pred pred, scan_strategy strategy, uint32_t reps,
+                                 void *stream, scan_tune_result *out);
+/* Write the tuned shapes to `path`, a versioned text file: a "gbscan-shapes 1"
+ * line, a "device <name> <SMs>" line, then one "kind b warps stages
+ * tile_blocks vote_rows tuned_us rule_us" line per tuned (kernel, b). */
+scan_status scan_autotune_save(const char *path);
+/* Replace the installed shapes with those of a file written by
+ * scan_autotune_save.  All or nothing: a wrong magic or version, a file tuned
+ * on another device (name or SM count), an unknown kernel, an illegal shape,
+ * a duplicate or a malformed line returns SCAN_EINVAL with the line number in
+ * scan_last_error and leaves the installed shapes unchanged. */
+scan_status scan_autotune_load(const char *path);
+/* Every kernel back to the built-in rule. */
+scan_status scan_autotune_reset(void);
 
 #ifdef __cplusplus
 }

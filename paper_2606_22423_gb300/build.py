@@ -1,7 +1,7 @@
 """Build libgbscan.so in-tree with nvcc for sm_103a.
 
 Translation units compile in parallel (the per-width kernel instantiations
-are split into four ranges) and link into one shared library that depends
+are split into eight ranges of four widths) and link into one shared library that depends
 only on the CUDA runtime.  Run ``python -m paper_2606_22423_gb300.build``.
 """
 from __future__ import annotations
@@ -23,7 +23,7 @@ NVCC_FLAGS = ARCH + [
     "-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2", "--use_fast_math",
     "-I" + os.path.join(ROOT, "include"),
 ]
-RANGES = [(1, 8), (9, 16), (17, 24), (25, 32)]
+RANGES = [(1, 4), (5, 8), (9, 12), (13, 16), (17, 20), (21, 24), (25, 28), (29, 32)]
 
 
 def _nvcc() -> str:

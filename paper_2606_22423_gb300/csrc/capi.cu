@@ -81,12 +81,10 @@ DeviceInfo device_info()
     return d;
 }
 
+// Launches kernel `op` at width b with its current shape (tuned or the rule).
 cudaError_t launch(int b, int op, const gb::ScanParams& p, int grid, cudaStream_t st)
 {
-    if (b <= 8) return gb_launch_range_1_8(b, op, p, grid, st);
-    if (b <= 16) return gb_launch_range_9_16(b, op, p, grid, st);
-    if (b <= 24) return gb_launch_range_17_24(b, op, p, grid, st);
-    return gb_launch_range_25_32(b, op, p, grid, st);
+    return gb_launch(b, op, p, gb_shape_for(b, op), grid, st);
 }
 
 }  // namespace
@@ -599,6 +597,12 @@ scan_status enqueue_scan(scan_column* c, scan_pred pred, scan_strategy strategy,
 
 }  // namespace
 
+scan_status gb_enqueue_scan(scan_column* c, scan_pred pred, scan_strategy strategy, cudaStream_t st,
+                            long long* dev_result, bool* empty)
+{
+    return enqueue_scan(c, pred, strategy, st, dev_result, empty);
+}
+
 // =================================================================== ABI
 extern "C" {
 
@@ -1002,7 +1006,7 @@ scan_status scan_launch_shape(uint32_t b, uint32_t* sms, uint32_t* ctas, uint32_
 {
     g_err.clear();
     if (b < 1 || b > 32) return fail(SCAN_EINVAL, "b must be in 1..32");
-    const gb::ShapeInfo si = gb::shape_of(static_cast<int>(b));
+    const gb::LaunchShape si = gb_shape_for(static_cast<int>(b), gb::kOpFullBF);
     if (sms) *sms = static_cast<uint32_t>(device_info().sms);
     if (ctas) *ctas = static_cast<uint32_t>(persistent_grid());
     if (warps_per_cta) *warps_per_cta = static_cast<uint32_t>(si.warps);

@@ -37,7 +37,17 @@ cudaError_t gb_column_select_ws(scan_column* c, uint64_t words, cudaStream_t st,
 
 namespace gb {
 struct ScanParams;
+struct LaunchShape;
 }
+// Launch shape of kernel `op` (gb::OpKind) at width b: the installed tuned
+// shape for the four tunable scan kernels, else the built-in rule.
+gb::LaunchShape gb_shape_for(int b, int op);
+
+// Enqueues one scan of `c` (what scan_run_async does, with the result written
+// to dev_result); *empty is set when the predicate selects nothing and no
+// kernel was launched.
+scan_status gb_enqueue_scan(scan_column* c, scan_pred pred, scan_strategy strategy, cudaStream_t st,
+                            long long* dev_result, bool* empty);
 // Scan parameters of a column: its packed data, n, base, zone map and device
 // workspace (result, status, grid-finish ticket, queue counters, partials).
 gb::ScanParams gb_column_params(const scan_column* c);

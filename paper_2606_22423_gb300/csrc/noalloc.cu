@@ -21,8 +21,7 @@
 #include "../../include/gbscan.h"
 #include "scan_kernels.cuh"
 
-// Internal helper of the host library (not part of the C ABI).
-void gb_set_last_error(const char* msg);
+#include "internal.h"
 
 namespace {
 
@@ -129,11 +128,7 @@ extern "C" scan_status scan_run_packed_noalloc(const uint32_t* dev_packed, uint6
     p.partials = reinterpret_cast<unsigned long long*>(static_cast<unsigned char*>(scratch) + kNoAllocHeader);
     p.status = dev_status;
     p.result = reinterpret_cast<long long*>(dev_out);
-    cudaError_t e;
-    if (b <= 8) e = gb_launch_range_1_8(static_cast<int>(b), op, p, sms, st);
-    else if (b <= 16) e = gb_launch_range_9_16(static_cast<int>(b), op, p, sms, st);
-    else if (b <= 24) e = gb_launch_range_17_24(static_cast<int>(b), op, p, sms, st);
-    else e = gb_launch_range_25_32(static_cast<int>(b), op, p, sms, st);
+    const cudaError_t e = gb_launch(static_cast<int>(b), op, p, gb_shape_for(static_cast<int>(b), op), sms, st);
     if (e != cudaSuccess) return noalloc_fail(SCAN_ECUDA, cudaGetErrorString(e));
     return SCAN_OK;
 }

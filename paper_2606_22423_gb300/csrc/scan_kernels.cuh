@@ -45,6 +45,8 @@ struct ScanParams {
     unsigned long long* qctl;     // [0] candidates, [1] queue head, [2] tail kept,
                                   // [3] count and [4] code sum of wholly-inside blocks
     long long* result;            // count, sum, blocks_scanned, reserved
+    uint32_t tile_blocks;         // pipeline shape: blocks per tile (a multiple of the warp step)
+    uint32_t stages;              // and slots per warp; warps per CTA = blockDim.x / 32
 };
 
 // Launch shape for width B: warps per CTA, pipeline depth, blocks per tile.
@@ -62,11 +64,13 @@ struct Geo {
     using Vec = typename std::conditional<kLpt == 4, uint4, uint2>::type;
 };
 
-// Launch shape for width B: 8 warps per CTA, each with kStages slots of up
-// to 8 KB; a tile is the largest multiple of the warp step (kLpt blocks) that
-// fits a slot, and at most 16 blocks: below b = 4 a full slot would hold
-// 32-64 K values (~10-20 us of decode per warp), too coarse to share a
-// column's work evenly among the warps.
+// Default launch shape for width B (used until a tuned shape is installed):
+// 8 warps per CTA, each with kStages slots of up to 8 KB; a tile is the
+// largest multiple of the warp step (kLpt blocks) that fits a slot, and at
+// most 16 blocks: below b = 4 a full slot would hold 32-64 K values (~10-20 us
+// of decode per warp), too coarse to share a column's work evenly among the
+// warps.  The kernels take the shape at run time (ScanParams::tile_blocks,
+// ::stages and the block size), so the autotuner can replace it per width.
 template <int B>
 struct Shape {
     static constexpr int kWarps = 8;
@@ -82,6 +86,42 @@ struct Shape {
     static_assert(kSmemBytes <= 227 * 1024, "shared-memory budget");
     static_assert(kTileBytes % 16 == 0, "bulk copies move multiples of 16 bytes");
 };
+
+// Shared memory of a runtime-shaped pipeline: every warp owns `stages` slots of
+// tile_blocks * 128 * B bytes; then the slots' transaction barriers (8 bytes
+// each) and, for the queue kernel, the blocks held per slot (4 bytes each).
+// The dynamic part may take 226 KB: 1 KB of the 227 KB a CTA can use stays
+// for the kernels' static shared memory (the grid reduction's array).
+constexpr int kSmemMax = 226 * 1024;
+__host__ __device__ constexpr uint32_t pipe_smem_bytes(uint32_t b, uint32_t warps, uint32_t stages,
+                                                       uint32_t tile_blocks)
+{
+    return warps * stages * (tile_blocks * 128u * b + 8u + 4u);
+}
+
+struct Pipe {
+    unsigned char* slots;  // this warp's first slot
+    uint64_t* bars;        // this warp's barriers
+    uint32_t* slot_n;      // this warp's per-slot block counts
+    uint32_t tile_bytes;   // bytes of a full tile
+    uint32_t stages;
+    uint32_t tb;           // blocks per full tile
+};
+
+template <int B>
+__device__ __forceinline__ Pipe pipe_of(unsigned char* smem, const ScanParams& p, int warp, int nwarps)
+{
+    Pipe q;
+    q.tb = p.tile_blocks;
+    q.stages = p.stages;
+    q.tile_bytes = q.tb * 128u * B;
+    const size_t slot_area = static_cast<size_t>(nwarps) * q.stages * q.tile_bytes;
+    q.slots = smem + static_cast<size_t>(warp) * q.stages * q.tile_bytes;
+    q.bars = reinterpret_cast<uint64_t*>(smem + slot_area) + warp * q.stages;
+    q.slot_n = reinterpret_cast<uint32_t*>(smem + slot_area + static_cast<size_t>(nwarps) * q.stages * 8u) +
+               warp * q.stages;
+    return q;
+}
 
 // ------------------------------------------------------------- extraction
 __device__ __forceinline__ uint32_t lane_word(const uint4& v, int k)
@@ -277,14 +317,47 @@ __device__ __forceinline__ void acc1_alu(uint32_t& c, uint32_t& a, uint32_t ui, 
         : "+r"(c), "+r"(a) : "r"(ui), "r"(L.loi), "r"(L.hii));
 }
 
+// 64-bit accumulation on the FMA pipe: s += u (IMAD.WIDE by an opaque 1).
+__device__ __forceinline__ uint64_t imad_wide(uint32_t u, uint32_t one, uint64_t s)
+{
+    uint64_t d;
+    asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(d) : "r"(u), "r"(one), "l"(s));
+    return d;
+}
+
+// Mode 2 (64-bit sums): the compare stays on the ALU; the subtract (unless
+// `alu_sub`), the count and the 64-bit add are IMADs on the FMA pipe.
+template <bool ALU_SUB>
+__device__ __forceinline__ void acc2(uint32_t& c, uint64_t& s, uint32_t ui, const Lanes& L)
+{
+    if constexpr (ALU_SUB)
+        asm("{\n\t.reg .pred p;\n\t.reg .b32 t;\n\t"
+            "sub.u32 t, %2, %3;\n\t"
+            "setp.le.u32 p, t, %4;\n\t"
+            "@p mad.lo.u32 %0, %5, %5, %0;\n\t"
+            "@p mad.wide.u32 %1, %2, %5, %1;\n\t}"
+            : "+r"(c), "+l"(s) : "r"(ui), "r"(L.loi), "r"(L.wm1), "r"(L.one));
+    else
+        asm("{\n\t.reg .pred p;\n\t.reg .b32 t;\n\t"
+            "mad.lo.u32 t, %2, %5, %3;\n\t"
+            "setp.le.u32 p, t, %4;\n\t"
+            "@p mad.lo.u32 %0, %5, %5, %0;\n\t"
+            "@p mad.wide.u32 %1, %2, %5, %1;\n\t}"
+            : "+r"(c), "+l"(s) : "r"(ui), "r"(L.negloi), "r"(L.wm1), "r"(L.one));
+}
+
 // One block, this thread's 4 lanes x 32 rows, every value valid.
 // Accumulators stay 32-bit inside the block:
 //   B <= 21: one word per lane packs (count << (B+5)) + sum  (mode 0);
 //   B <= 27: a 32-bit sum per lane plus a count              (mode 1);
 //   else   : a 64-bit sum plus a count                       (mode 2).
-// BRANCHY adds a warp vote per 32-value group (one value per thread) and
-// skips the aggregation when no lane of the warp matches.
-template <int B, bool BRANCHY>
+// BRANCHY adds a warp vote and skips the aggregation when no value of the
+// voting group matches.  The group is one value per thread (32 values) by
+// default; with ROWVOTE it is a whole row of the thread's kLpt lanes (32 * kLpt
+// values over kLpt blocks): one vote per kLpt values, but all kLpt tests must
+// be held across the vote.  Which form is faster depends on the width and on
+// how many warps share an SM (the autotuner picks per width).
+template <int B, bool BRANCHY, bool ROWVOTE = false>
 __device__ __forceinline__ void agg_block(const typename Geo<B>::Vec* rows, const Lanes& L,
                                           uint64_t& cnt, uint64_t& sum)
 {
@@ -297,37 +370,69 @@ __device__ __forceinline__ void agg_block(const typename Geo<B>::Vec* rows, cons
     uint64_t s64 = 0u;
 #pragma unroll
     for (int r = 0; r < 32; ++r) {
+        if constexpr (BRANCHY && ROWVOTE) {
+            // subtract on the FMA pipe unless the extraction already used it
+            const bool top = top_field<B>(r);
+            uint32_t ui[kLpt];
+            bool m[kLpt];
+            bool any = false;
 #pragma unroll
-        for (int k = 0; k < kLpt; ++k) {
-            const uint32_t ui = field_add<B>(W, r, k, L);
-            if constexpr (BRANCHY) {
-                // subtract and add on the FMA pipe unless the extraction already used it
-                const bool top = top_field<B>(r);
-                const uint32_t t = top ? ui - L.loi : imad(ui, L.one, L.negloi);
-                const bool m = t <= L.wm1;
-                if (__any_sync(kFull, m)) {  // vote.any: the predicate directly, no compare
-                    if (m) {
-                        if constexpr (kMode != 0) c += 1u;
-                        if constexpr (kMode == 2) s64 += ui;
-                        else a[k] = top ? a[k] + ui : imad(ui, L.one, a[k]);
+            for (int k = 0; k < kLpt; ++k) {
+                ui[k] = field_add<B>(W, r, k, L);
+                const uint32_t t = top ? ui[k] - L.loi : imad(ui[k], L.one, L.negloi);
+                m[k] = t <= L.wm1;
+                any = any || m[k];
+            }
+            if (__any_sync(kFull, any)) {
+#pragma unroll
+                for (int k = 0; k < kLpt; ++k) {
+                    if (m[k]) {
+                        if constexpr (kMode != 0) c = imad(L.one, L.one, c);
+                        if constexpr (kMode == 2) s64 = imad_wide(ui[k], L.one, s64);
+                        else a[k] = top ? a[k] + ui[k] : imad(ui[k], L.one, a[k]);
                     }
                 }
-            } else if constexpr (kMode == 0) {
-                // Every compare keeps one ISETP on the ALU; the subtract and the
-                // add go to the FMA pipe, except that half the top-of-word
-                // fields (already extracted by IMAD.HI) add on the ALU: about
-                // 2.9 ALU and 2.0 IMAD per value (2.4 / 2.1 at b = 8).
-                if (top_field<B>(r) && ((r + k) & 1) == 0) acc0_fsub(a[k], ui, L);
-                else acc0_fma(a[k], ui, L);
-            } else if constexpr (kMode == 1) {
-                if (top_field<B>(r)) acc1_alu(c, a[k], ui, L);
-                else if (sub_on_fma<B>(r, k)) acc1_fma(c, a[k], ui, L);
-                else acc1_imad(c, a[k], ui, L);
-            } else {
-                // 64-bit sums: plain compare and add
-                if ((ui - L.loi) <= L.wm1) {
-                    c += 1u;
-                    s64 += ui;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < kLpt; ++k) {
+                const uint32_t ui = field_add<B>(W, r, k, L);
+                if constexpr (BRANCHY) {
+                    // subtract and add on the FMA pipe unless the extraction already used it
+                    const bool top = top_field<B>(r);
+                    const uint32_t t = top ? ui - L.loi : imad(ui, L.one, L.negloi);
+                    const bool m = t <= L.wm1;
+                    if (__any_sync(kFull, m)) {  // vote.any: the predicate directly, no compare
+                        if (m) {
+                            if constexpr (kMode != 0) c += 1u;
+                            if constexpr (kMode == 2) s64 += ui;
+                            else a[k] = top ? a[k] + ui : imad(ui, L.one, a[k]);
+                        }
+                    }
+                } else if constexpr (kMode == 0) {
+                    // Every compare keeps one ISETP on the ALU; the subtract and the
+                    // add go to the FMA pipe, except that half the top-of-word
+                    // fields (already extracted by IMAD.HI) add on the ALU: about
+                    // 2.9 ALU and 2.0 IMAD per value (2.4 / 2.1 at b = 8).
+                    if (top_field<B>(r) && ((r + k) & 1) == 0) acc0_fsub(a[k], ui, L);
+                    else acc0_fma(a[k], ui, L);
+                } else if constexpr (kMode == 1) {
+                    if (top_field<B>(r)) acc1_alu(c, a[k], ui, L);
+                    else if (sub_on_fma<B>(r, k)) acc1_fma(c, a[k], ui, L);
+                    else acc1_imad(c, a[k], ui, L);
+                } else if constexpr (B < 32) {
+                    // 64-bit sums: count and sum on the FMA pipe (IMAD.WIDE); a
+                    // top-of-word field (extracted by IMAD.HI) subtracts on the
+                    // ALU.  At b = 28..31 this ran 1.5-6% faster than ALU adds.
+                    if (top_field<B>(r)) acc2<true>(c, s64, ui, L);
+                    else acc2<false>(c, s64, ui, L);
+                } else {
+                    // b = 32 (no extraction): plain compare and ALU adds, 2% faster
+                    // than the FMA form above
+                    if ((ui - L.loi) <= L.wm1) {
+                        c += 1u;
+                        s64 += ui;
+                    }
                 }
             }
         }
@@ -575,7 +680,7 @@ __device__ __forceinline__ void scan_tail_layout(const ScanParams& p, int lane, 
 }
 
 // All `nb` blocks of a staged tile (blocks are contiguous in the slot).
-template <int B, bool BRANCHY>
+template <int B, bool BRANCHY, bool ROWVOTE = false>
 __device__ __forceinline__ void scan_tile(const unsigned char* tile, uint32_t nb, int lane,
                                           const Lanes& L, uint32_t lo, uint32_t wm1, uint64_t& cnt,
                                           uint64_t& sum)
@@ -587,7 +692,7 @@ __device__ __forceinline__ void scan_tile(const unsigned char* tile, uint32_t nb
     uint32_t g = 0;
 #pragma unroll 1
     for (; g + kStep <= nb; g += kStep)
-        agg_block<B, BRANCHY>(block_rows<B>(tile + (g + sub) * kBB, q), L, cnt, sum);
+        agg_block<B, BRANCHY, ROWVOTE>(block_rows<B>(tile + (g + sub) * kBB, q), L, cnt, sum);
     if (g < nb) {
         const bool ok = g + sub < nb;
         agg_block_masked<B>(block_rows<B>(tile + (ok ? g + sub : g) * kBB, q), lo, wm1, cnt, sum, ok,
@@ -599,13 +704,15 @@ __device__ __forceinline__ void scan_tile(const unsigned char* tile, uint32_t nb
 // Sum (count, sum) over the grid: warp shuffles, one word pair per CTA, and
 // the last CTA to arrive folds the pairs, applies the frame of reference
 // (SUM_v = SUM_u + base*COUNT) and resets the ticket for the next launch.
-template <int WARPS>
+// WMAX bounds the CTA's warps (blockDim.x / 32 at run time).
+template <int WMAX>
 __device__ __forceinline__ void grid_finish(const ScanParams& p, uint64_t cnt, uint64_t sum,
                                             bool queue_mode, uint64_t full_blocks_scanned)
 {
-    __shared__ unsigned long long red[WARPS][2];
+    __shared__ unsigned long long red[WMAX][2];
     __shared__ int is_last;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int WARPS = static_cast<int>(blockDim.x >> 5);
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
         cnt += __shfl_xor_sync(kFull, cnt, o);
@@ -687,40 +794,42 @@ __device__ __forceinline__ void scan_tail(const ScanParams& p, int lane, uint64_
 }
 
 // ------------------------------------------------------------- full scan
-template <int B, bool BRANCHY, int LAY = kLayLanes>
-__global__ void __launch_bounds__(Shape<B>::kWarps * 32, 1) k_scan_full(const ScanParams p)
+// WMAX: the largest CTA the instantiation is compiled for (launch bound; 8
+// warps leave up to 255 registers per thread, 16 warps 128).  ROWVOTE: the
+// branchy vote group (see agg_block).
+template <int B, bool BRANCHY, int LAY = kLayLanes, int WMAX = 8, bool ROWVOTE = false>
+__global__ void __launch_bounds__(WMAX * 32, 1) k_scan_full(const ScanParams p)
 {
-    using S = Shape<B>;
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    unsigned char* slots = smem + static_cast<size_t>(warp) * S::kStages * S::kTileBytes;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S::kSlotBytes) + warp * S::kStages;
+    const int nwarps = static_cast<int>(blockDim.x >> 5);
+    const Pipe P = pipe_of<B>(smem, p, warp, nwarps);
 
     const uint64_t full_blocks = p.n >> 10;
-    const uint64_t ntiles = (full_blocks + S::kTB - 1) / S::kTB;
+    const uint64_t ntiles = (full_blocks + P.tb - 1) / P.tb;
     // Warp-major numbering: a round's last, partial stretch of tiles goes to
     // warp slot w of every CTA before slot w + 1 of any, so the CTAs (SMs) of
     // a small column get equal shares (CTA-major numbering gave the first
     // CTAs two tiles per warp and the rest one at 2^24 values, b = 8).
     const uint64_t gw = static_cast<uint64_t>(warp) * gridDim.x + blockIdx.x;
-    const uint64_t GW = static_cast<uint64_t>(gridDim.x) * S::kWarps;
+    const uint64_t GW = static_cast<uint64_t>(gridDim.x) * nwarps;
 
     if (lane == 0) {
-        for (int s = 0; s < S::kStages; ++s) mbar_init(&bars[s], 1);
+        for (uint32_t s = 0; s < P.stages; ++s) mbar_init(&P.bars[s], 1);
         fence_mbar_init();
     }
     __syncwarp();
 
-    auto issue = [&](uint64_t t, int s) {
-        const uint64_t fb = t * S::kTB;
+    auto issue = [&](uint64_t t, uint32_t s) {
+        const uint64_t fb = t * P.tb;
         const uint64_t left = full_blocks - fb;
-        const uint32_t nb = left < S::kTB ? static_cast<uint32_t>(left) : S::kTB;
-        const uint32_t bytes = nb * S::kBlockBytes;
-        mbar_arrive_expect_tx(&bars[s], bytes);
-        bulk_g2s(slots + s * S::kTileBytes, p.packed + fb * 32u * B, bytes, &bars[s]);
+        const uint32_t nb = left < P.tb ? static_cast<uint32_t>(left) : P.tb;
+        const uint32_t bytes = nb * (128u * B);
+        mbar_arrive_expect_tx(&P.bars[s], bytes);
+        bulk_g2s(P.slots + s * P.tile_bytes, p.packed + fb * 32u * B, bytes, &P.bars[s]);
     };
     if (lane == 0) {
-        for (int s = 0; s < S::kStages; ++s) {
+        for (uint32_t s = 0; s < P.stages; ++s) {
             const uint64_t t = gw + s * GW;
             if (t < ntiles) issue(t, s);
         }
@@ -728,38 +837,40 @@ __global__ void __launch_bounds__(Shape<B>::kWarps * 32, 1) k_scan_full(const Sc
 
     const Lanes L = make_lanes<B>(p.lo, p.wm1);
     uint64_t cnt = 0, sum = 0;
-    uint32_t it = 0;
+    uint32_t it = 0, s = 0, parity = 0;
     bool failed = false;
 #pragma unroll 1
     for (uint64_t t = gw; t < ntiles; t += GW, ++it) {
-        const int s = static_cast<int>(it % S::kStages);
-        const uint32_t parity = (it / S::kStages) & 1u;
-        const bool ok = mbar_wait(&bars[s], parity, kWaitLimitNs);
+        const bool ok = mbar_wait(&P.bars[s], parity, kWaitLimitNs);
         if (!__all_sync(kFull, ok)) {
             failed = true;
             break;
         }
-        const uint64_t left = full_blocks - t * S::kTB;
-        const uint32_t nb = left < S::kTB ? static_cast<uint32_t>(left) : S::kTB;
+        const uint64_t left = full_blocks - t * P.tb;
+        const uint32_t nb = left < P.tb ? static_cast<uint32_t>(left) : P.tb;
         if constexpr (LAY == kLayLanes)
-            scan_tile<B, BRANCHY>(slots + s * S::kTileBytes, nb, lane, L, p.lo, p.wm1, cnt, sum);
+            scan_tile<B, BRANCHY, ROWVOTE>(P.slots + s * P.tile_bytes, nb, lane, L, p.lo, p.wm1, cnt, sum);
         else
-            scan_tile_layout<B, BRANCHY, LAY>(slots + s * S::kTileBytes, nb, lane, L, cnt, sum);
+            scan_tile_layout<B, BRANCHY, LAY>(P.slots + s * P.tile_bytes, nb, lane, L, cnt, sum);
         __syncwarp();
-        const uint64_t tn = t + static_cast<uint64_t>(S::kStages) * GW;
+        const uint64_t tn = t + static_cast<uint64_t>(P.stages) * GW;
         if (lane == 0 && tn < ntiles) {
             fence_proxy_async_smem();
             issue(tn, s);
+        }
+        if (++s == P.stages) {
+            s = 0;
+            parity ^= 1u;
         }
     }
     if (failed) {
         if (lane == 0) atomicOr(p.status, kErrTimeout);
         // let copies still in flight land before the CTA's shared memory goes away
-        for (uint32_t j = 0; j < static_cast<uint32_t>(S::kStages); ++j) {
+        for (uint32_t j = 0; j < P.stages; ++j) {
             const uint64_t t = gw + static_cast<uint64_t>(it + j) * GW;
             if (t >= ntiles) break;
             const uint32_t jt = it + j;
-            mbar_wait(&bars[jt % S::kStages], (jt / S::kStages) & 1u, kDrainLimitNs);
+            mbar_wait(&P.bars[jt % P.stages], (jt / P.stages) & 1u, kDrainLimitNs);
         }
     }
     if ((p.n & 1023u) && gw == GW - 1) {
@@ -768,41 +879,40 @@ __global__ void __launch_bounds__(Shape<B>::kWarps * 32, 1) k_scan_full(const Sc
         else
             scan_tail_layout<B, LAY>(p, lane, cnt, sum);
     }
-    grid_finish<S::kWarps>(p, cnt, sum, false, (p.n + 1023u) >> 10);
+    grid_finish<WMAX>(p, cnt, sum, false, (p.n + 1023u) >> 10);
 }
 
 // -------------------------------------------------------- zone-map build
 template <int B>
 __global__ void __launch_bounds__(Shape<B>::kWarps * 32, 1) k_zonemap_build(const ScanParams p)
 {
-    using S = Shape<B>;
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwarps = static_cast<int>(blockDim.x >> 5);
     const int q = lane % Geo<B>::kTpb;
     const uint32_t sub = static_cast<uint32_t>(lane / Geo<B>::kTpb);
-    unsigned char* slots = smem + static_cast<size_t>(warp) * S::kStages * S::kTileBytes;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S::kSlotBytes) + warp * S::kStages;
+    const Pipe P = pipe_of<B>(smem, p, warp, nwarps);
 
     const uint64_t full_blocks = p.n >> 10;
-    const uint64_t ntiles = (full_blocks + S::kTB - 1) / S::kTB;
-    const uint64_t gw = static_cast<uint64_t>(blockIdx.x) * S::kWarps + warp;
-    const uint64_t GW = static_cast<uint64_t>(gridDim.x) * S::kWarps;
+    const uint64_t ntiles = (full_blocks + P.tb - 1) / P.tb;
+    const uint64_t gw = static_cast<uint64_t>(blockIdx.x) * nwarps + warp;
+    const uint64_t GW = static_cast<uint64_t>(gridDim.x) * nwarps;
 
     if (lane == 0) {
-        for (int s = 0; s < S::kStages; ++s) mbar_init(&bars[s], 1);
+        for (uint32_t s = 0; s < P.stages; ++s) mbar_init(&P.bars[s], 1);
         fence_mbar_init();
     }
     __syncwarp();
-    auto issue = [&](uint64_t t, int s) {
-        const uint64_t fb = t * S::kTB;
+    auto issue = [&](uint64_t t, uint32_t s) {
+        const uint64_t fb = t * P.tb;
         const uint64_t left = full_blocks - fb;
-        const uint32_t nb = left < S::kTB ? static_cast<uint32_t>(left) : S::kTB;
-        const uint32_t bytes = nb * S::kBlockBytes;
-        mbar_arrive_expect_tx(&bars[s], bytes);
-        bulk_g2s(slots + s * S::kTileBytes, p.packed + fb * 32u * B, bytes, &bars[s]);
+        const uint32_t nb = left < P.tb ? static_cast<uint32_t>(left) : P.tb;
+        const uint32_t bytes = nb * (128u * B);
+        mbar_arrive_expect_tx(&P.bars[s], bytes);
+        bulk_g2s(P.slots + s * P.tile_bytes, p.packed + fb * 32u * B, bytes, &P.bars[s]);
     };
     if (lane == 0) {
-        for (int s = 0; s < S::kStages; ++s) {
+        for (uint32_t s = 0; s < P.stages; ++s) {
             const uint64_t t = gw + s * GW;
             if (t < ntiles) issue(t, s);
         }
@@ -819,21 +929,19 @@ __global__ void __launch_bounds__(Shape<B>::kWarps * 32, 1) k_zonemap_build(cons
             p.blocksum[blk] = sm + static_cast<unsigned long long>(p.base) * valid;
         }
     };
-    uint32_t it = 0;
+    uint32_t it = 0, s = 0, parity = 0;
     bool failed = false;
 #pragma unroll 1
     for (uint64_t t = gw; t < ntiles; t += GW, ++it) {
-        const int s = static_cast<int>(it % S::kStages);
-        const uint32_t parity = (it / S::kStages) & 1u;
-        const bool okw = mbar_wait(&bars[s], parity, kWaitLimitNs);
+        const bool okw = mbar_wait(&P.bars[s], parity, kWaitLimitNs);
         if (!__all_sync(kFull, okw)) {
             failed = true;
             break;
         }
-        const uint64_t fb = t * S::kTB;
+        const uint64_t fb = t * P.tb;
         const uint64_t left = full_blocks - fb;
-        const uint32_t nb = left < S::kTB ? static_cast<uint32_t>(left) : S::kTB;
-        const unsigned char* tile = slots + s * S::kTileBytes;
+        const uint32_t nb = left < P.tb ? static_cast<uint32_t>(left) : P.tb;
+        const unsigned char* tile = P.slots + s * P.tile_bytes;
 #pragma unroll 1
         for (uint32_t g = 0; g < nb; g += static_cast<uint32_t>(Geo<B>::kLpt)) {
             const bool ok = g + sub < nb;
@@ -843,19 +951,23 @@ __global__ void __launch_bounds__(Shape<B>::kWarps * 32, 1) k_zonemap_build(cons
             emit(fb + g + sub, ok, mn, mx, sm, 1024u);
         }
         __syncwarp();
-        const uint64_t tn = t + static_cast<uint64_t>(S::kStages) * GW;
+        const uint64_t tn = t + static_cast<uint64_t>(P.stages) * GW;
         if (lane == 0 && tn < ntiles) {
             fence_proxy_async_smem();
             issue(tn, s);
         }
+        if (++s == P.stages) {
+            s = 0;
+            parity ^= 1u;
+        }
     }
     if (failed) {
         if (lane == 0) atomicOr(p.status, kErrTimeout);
-        for (uint32_t j = 0; j < static_cast<uint32_t>(S::kStages); ++j) {
+        for (uint32_t j = 0; j < P.stages; ++j) {
             const uint64_t t = gw + static_cast<uint64_t>(it + j) * GW;
             if (t >= ntiles) break;
             const uint32_t jt = it + j;
-            mbar_wait(&bars[jt % S::kStages], (jt / S::kStages) & 1u, kDrainLimitNs);
+            mbar_wait(&P.bars[jt % P.stages], (jt / P.stages) & 1u, kDrainLimitNs);
         }
     }
     if ((p.n & 1023u) && gw == GW - 1) {
@@ -876,96 +988,102 @@ constexpr int kFilterPerCta = 2048;
 __global__ void k_zone_filter(const ScanParams p);
 
 // ------------------------------------------------------- zone-skip scan
-// Persistent warps pop up to kTB candidate ids per atomic from the queue,
-// merge consecutive ids into single bulk copies, and scan the staged blocks.
+// Persistent warps pop up to tile_blocks (<= 32) candidate ids per atomic
+// from the queue, merge consecutive ids into single bulk copies, and scan the
+// staged blocks.  Each warp pops its next chunk (the atomic and the id loads)
+// one iteration ahead, so that latency overlaps the decode of the current
+// slot instead of delaying the slot's refill.
 template <int B, bool BRANCHY>
 __global__ void __launch_bounds__(Shape<B>::kWarps * 32, 1) k_scan_queue(const ScanParams p)
 {
-    using S = Shape<B>;
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    unsigned char* slots = smem + static_cast<size_t>(warp) * S::kStages * S::kTileBytes;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S::kSlotBytes) + warp * S::kStages;
-    uint32_t* slot_n = reinterpret_cast<uint32_t*>(smem + S::kSlotBytes + S::kWarps * S::kStages * 8) +
-                       warp * S::kStages;
+    const int nwarps = static_cast<int>(blockDim.x >> 5);
+    const Pipe P = pipe_of<B>(smem, p, warp, nwarps);
 
     const uint64_t ncand = __ldcg(&p.qctl[0]);
     if (lane == 0) {
-        for (int s = 0; s < S::kStages; ++s) mbar_init(&bars[s], 1);
+        for (uint32_t s = 0; s < P.stages; ++s) mbar_init(&P.bars[s], 1);
         fence_mbar_init();
     }
     __syncwarp();
 
-    // Pop the next chunk into slot s; returns its block count (0 = queue empty).
-    auto grab = [&](int s) -> uint32_t {
+    // Pop the next chunk: its block count (0 = queue empty) and this lane's id.
+    auto pop = [&](uint32_t& id) -> uint32_t {
         unsigned long long start = 0;
-        if (lane == 0) start = atomicAdd(&p.qctl[1], static_cast<unsigned long long>(S::kTB));
+        if (lane == 0) start = atomicAdd(&p.qctl[1], static_cast<unsigned long long>(P.tb));
         start = __shfl_sync(kFull, start, 0);
         const unsigned long long avail = start < ncand ? ncand - start : 0ull;
-        const uint32_t nb = avail < static_cast<unsigned long long>(S::kTB) ? static_cast<uint32_t>(avail)
-                                                                            : static_cast<uint32_t>(S::kTB);
-        if (nb == 0) return 0u;
-        if (lane == 0) mbar_arrive_expect_tx(&bars[s], nb * S::kBlockBytes);
-        __syncwarp();
-        fence_proxy_async_smem();
-        unsigned char* dst = slots + s * S::kTileBytes;
-        for (uint32_t seg = 0; seg < nb; seg += 32u) {
-            const uint32_t i = seg + lane;
-            const bool valid = i < nb;
-            const uint32_t id = valid ? __ldcg(&p.cand[start + i]) : 0u;
-            const uint32_t prev = __shfl_up_sync(kFull, id, 1);
-            const bool head = valid && (lane == 0 || prev + 1u != id);
-            const uint32_t heads = __ballot_sync(kFull, head);
-            const uint32_t vmask = __ballot_sync(kFull, valid);
-            if (head) {
-                const uint32_t later = heads & ~((2u << lane) - 1u);
-                const uint32_t end = later ? static_cast<uint32_t>(__ffs(later) - 1)
-                                           : static_cast<uint32_t>(32 - __clz(vmask));
-                const uint32_t len = end - static_cast<uint32_t>(lane);
-                bulk_g2s(dst + i * S::kBlockBytes, p.packed + static_cast<uint64_t>(id) * 32u * B,
-                         len * S::kBlockBytes, &bars[s]);
-            }
-        }
+        const uint32_t nb = avail < static_cast<unsigned long long>(P.tb) ? static_cast<uint32_t>(avail) : P.tb;
+        id = static_cast<uint32_t>(lane) < nb ? __ldcg(&p.cand[start + lane]) : 0u;
         return nb;
     };
+    // Stage a popped chunk into slot s (one bulk copy per run of consecutive ids).
+    auto stage = [&](uint32_t nb, uint32_t id, uint32_t s) {
+        if (lane == 0) P.slot_n[s] = nb;
+        if (nb == 0) return;
+        if (lane == 0) mbar_arrive_expect_tx(&P.bars[s], nb * (128u * B));
+        __syncwarp();
+        fence_proxy_async_smem();
+        unsigned char* dst = P.slots + s * P.tile_bytes;
+        const bool valid = static_cast<uint32_t>(lane) < nb;
+        const uint32_t prev = __shfl_up_sync(kFull, id, 1);
+        const bool head = valid && (lane == 0 || prev + 1u != id);
+        const uint32_t heads = __ballot_sync(kFull, head);
+        const uint32_t vmask = __ballot_sync(kFull, valid);
+        if (head) {
+            const uint32_t later = heads & ~((2u << lane) - 1u);
+            const uint32_t end = later ? static_cast<uint32_t>(__ffs(later) - 1)
+                                       : static_cast<uint32_t>(32 - __clz(vmask));
+            const uint32_t len = end - static_cast<uint32_t>(lane);
+            bulk_g2s(dst + lane * (128u * B), p.packed + static_cast<uint64_t>(id) * 32u * B, len * (128u * B),
+                     &P.bars[s]);
+        }
+    };
 
-    for (int s = 0; s < S::kStages; ++s) {
-        const uint32_t nb = grab(s);
-        if (lane == 0) slot_n[s] = nb;
+    for (uint32_t s = 0; s < P.stages; ++s) {
+        uint32_t id;
+        const uint32_t nb = pop(id);
+        stage(nb, id, s);
         if (nb == 0) {
-            for (int r = s + 1; r < S::kStages; ++r)
-                if (lane == 0) slot_n[r] = 0u;
+            for (uint32_t r = s + 1; r < P.stages; ++r)
+                if (lane == 0) P.slot_n[r] = 0u;
             break;
         }
     }
     __syncwarp();
+    uint32_t next_id = 0;
+    uint32_t next_nb = P.slot_n[P.stages - 1] ? pop(next_id) : 0u;
 
     const Lanes L = make_lanes<B>(p.lo, p.wm1);
     uint64_t cnt = 0, sum = 0;
-    uint32_t it = 0;
+    uint32_t it = 0, s = 0, parity = 0;
     bool failed = false;
 #pragma unroll 1
     for (;; ++it) {
-        const int s = static_cast<int>(it % S::kStages);
-        const uint32_t nb = slot_n[s];
+        const uint32_t nb = P.slot_n[s];
         if (nb == 0) break;
-        const bool ok = mbar_wait(&bars[s], (it / S::kStages) & 1u, kWaitLimitNs);
+        const bool ok = mbar_wait(&P.bars[s], parity, kWaitLimitNs);
         if (!__all_sync(kFull, ok)) {
             failed = true;
             break;
         }
-        scan_tile<B, BRANCHY>(slots + s * S::kTileBytes, nb, lane, L, p.lo, p.wm1, cnt, sum);
+        scan_tile<B, BRANCHY>(P.slots + s * P.tile_bytes, nb, lane, L, p.lo, p.wm1, cnt, sum);
         __syncwarp();
-        const uint32_t nn = grab(s);
-        if (lane == 0) slot_n[s] = nn;
+        stage(next_nb, next_id, s);
         __syncwarp();
+        if (next_nb) next_nb = pop(next_id);
+        if (++s == P.stages) {
+            s = 0;
+            parity ^= 1u;
+        }
     }
     if (failed) {
         if (lane == 0) atomicOr(p.status, kErrTimeout);
-        for (uint32_t j = 0; j < static_cast<uint32_t>(S::kStages); ++j) {
+        for (uint32_t j = 0; j < P.stages; ++j) {
             const uint32_t jt = it + j;
-            if (slot_n[jt % S::kStages] == 0) break;
-            mbar_wait(&bars[jt % S::kStages], (jt / S::kStages) & 1u, kDrainLimitNs);
+            if (P.slot_n[jt % P.stages] == 0) break;
+            mbar_wait(&P.bars[jt % P.stages], (jt / P.stages) & 1u, kDrainLimitNs);
         }
     }
     // the zero-padded tail block is tested and scanned by CTA 0, warp 0
@@ -985,7 +1103,7 @@ __global__ void __launch_bounds__(Shape<B>::kWarps * 32, 1) k_scan_queue(const S
             }
         }
     }
-    grid_finish<S::kWarps>(p, cnt, sum, true, 0);
+    grid_finish<Shape<B>::kWarps>(p, cnt, sum, true, 0);
 }
 
 // ----------------------------------------------------------- dispatching
@@ -1005,6 +1123,15 @@ struct ShapeInfo {
     int warps, stages, tile_blocks, smem_bytes;
 };
 
+// A runtime launch shape: one CTA per SM of `warps` warps, each with `stages`
+// slots of `tile_blocks` blocks (the queue kernels pop that many candidates
+// at a time); vote_rows picks the branchy vote group (full branchy scans at
+// b <= 21 only).  Full scans take 8..16 warps (above 8 the 16-warp-bound
+// instantiation, <= 128 registers per thread); every other kernel 1..8.
+struct LaunchShape {
+    int warps, stages, tile_blocks, vote_rows;
+};
+
 template <int LO, int HI>
 __host__ inline ShapeInfo shape_range(int b)
 {
@@ -1022,7 +1149,33 @@ inline ShapeInfo shape_of(int b) { return shape_range<1, 32>(b); }
 
 // One translation unit per width range instantiates the kernels; these are
 // the entry points the host library dispatches to.
-cudaError_t gb_launch_range_1_8(int b, int op, const gb::ScanParams& p, int grid, cudaStream_t st);
-cudaError_t gb_launch_range_9_16(int b, int op, const gb::ScanParams& p, int grid, cudaStream_t st);
-cudaError_t gb_launch_range_17_24(int b, int op, const gb::ScanParams& p, int grid, cudaStream_t st);
-cudaError_t gb_launch_range_25_32(int b, int op, const gb::ScanParams& p, int grid, cudaStream_t st);
+// The shape's tile_blocks and stages override those fields of p.
+#define GB_DECLARE_RANGE(lo, hi)                                                                          \
+    cudaError_t gb_launch_range_##lo##_##hi(int b, int op, const gb::ScanParams& p, const gb::LaunchShape& sh, \
+                                            int grid, cudaStream_t st);
+GB_DECLARE_RANGE(1, 4)
+GB_DECLARE_RANGE(5, 8)
+GB_DECLARE_RANGE(9, 12)
+GB_DECLARE_RANGE(13, 16)
+GB_DECLARE_RANGE(17, 20)
+GB_DECLARE_RANGE(21, 24)
+GB_DECLARE_RANGE(25, 28)
+GB_DECLARE_RANGE(29, 32)
+#undef GB_DECLARE_RANGE
+
+// Dispatch to the range's launcher.
+inline cudaError_t gb_launch(int b, int op, const gb::ScanParams& p, const gb::LaunchShape& sh, int grid,
+                             cudaStream_t st)
+{
+    switch ((b - 1) / 4) {
+    case 0: return gb_launch_range_1_4(b, op, p, sh, grid, st);
+    case 1: return gb_launch_range_5_8(b, op, p, sh, grid, st);
+    case 2: return gb_launch_range_9_12(b, op, p, sh, grid, st);
+    case 3: return gb_launch_range_13_16(b, op, p, sh, grid, st);
+    case 4: return gb_launch_range_17_20(b, op, p, sh, grid, st);
+    case 5: return gb_launch_range_21_24(b, op, p, sh, grid, st);
+    case 6: return gb_launch_range_25_28(b, op, p, sh, grid, st);
+    case 7: return gb_launch_range_29_32(b, op, p, sh, grid, st);
+    default: return cudaErrorInvalidValue;
+    }
+}

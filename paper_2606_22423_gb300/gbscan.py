@@ -39,6 +39,20 @@ class scan_pred(ctypes.Structure):
     _fields_ = [("lo", ctypes.c_int64), ("hi", ctypes.c_int64)]
 
 
+class scan_shape(ctypes.Structure):
+    _fields_ = [("warps", ctypes.c_uint32), ("stages", ctypes.c_uint32), ("tile_blocks", ctypes.c_uint32),
+                ("vote_rows", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {"warps": int(self.warps), "stages": int(self.stages), "tile_blocks": int(self.tile_blocks),
+                "vote_rows": int(self.vote_rows)}
+
+
+class scan_tune_result(ctypes.Structure):
+    _fields_ = [("best", scan_shape), ("rule", scan_shape), ("best_us", ctypes.c_float),
+                ("rule_us", ctypes.c_float), ("candidates", ctypes.c_uint32)]
+
+
 class scan_result(ctypes.Structure):
     _fields_ = [("count", ctypes.c_int64), ("sum", ctypes.c_int64),
                 ("blocks_scanned", ctypes.c_uint64), ("reserved", ctypes.c_uint64)]
@@ -86,6 +100,13 @@ SIGNATURES = {
     "scan_probe_read": (_st, [_vp, _u64, _vp, _vp]),
     "scan_probe_triad": (_st, [_vp, _vp, _vp, ctypes.c_float, _u64, _vp]),
     "scan_launch_shape": (_st, [_u32] + [ctypes.POINTER(_u32)] * 5),
+    "scan_shape_get": (_st, [_u32, _st, ctypes.POINTER(scan_shape)]),
+    "scan_shape_set": (_st, [_u32, _st, ctypes.POINTER(scan_shape)]),
+    "scan_shape_candidates": (_st, [_u32, _st, _vp, _u32, ctypes.POINTER(_u32)]),
+    "scan_autotune_column": (_st, [_vp, scan_pred, _st, _u32, _vp, ctypes.POINTER(scan_tune_result)]),
+    "scan_autotune_save": (_st, [ctypes.c_char_p]),
+    "scan_autotune_load": (_st, [ctypes.c_char_p]),
+    "scan_autotune_reset": (_st, []),
     "scan_selftest_wait_timeout": (_st, [_u64, _vp]),
     "scan_run_packed_noalloc": (_st, [_vp, _u64, _u32, _u32, scan_pred, _st, _vp, _vp, _vp]),
     "scan_batch_create": (_st, [_vp, _u32, _vp, _u32, _vp, ctypes.POINTER(_vp)]),
@@ -214,6 +235,48 @@ def scan_launch_shape(b: int) -> dict:
     return {k: int(v.value) for k, v in zip(keys, vals)}
 
 
+def _strategy(strategy) -> int:
+    return STRATEGIES[strategy] if isinstance(strategy, str) else int(strategy)
+
+
+def shape_get(b: int, strategy="branchfree") -> dict:
+    """The launch shape the kernel of `strategy` uses at width b now."""
+    out = scan_shape()
+    _check(load().scan_shape_get(b, _strategy(strategy), ctypes.byref(out)))
+    return out.as_dict()
+
+
+def shape_set(b: int, strategy="branchfree", shape=None):
+    """Install a shape (dict or scan_shape), or the built-in rule with None."""
+    if shape is None:
+        _check(load().scan_shape_set(b, _strategy(strategy), None))
+        return
+    sh = shape if isinstance(shape, scan_shape) else scan_shape(shape["warps"], shape["stages"],
+                                                                 shape["tile_blocks"], shape.get("vote_rows", 0))
+    _check(load().scan_shape_set(b, _strategy(strategy), ctypes.byref(sh)))
+
+
+def shape_candidates(b: int, strategy="branchfree") -> list:
+    """The autotuner's candidate shapes for (strategy, b)."""
+    count = _u32()
+    _check(load().scan_shape_candidates(b, _strategy(strategy), None, 0, ctypes.byref(count)))
+    arr = (scan_shape * max(count.value, 1))()
+    _check(load().scan_shape_candidates(b, _strategy(strategy), arr, count.value, ctypes.byref(count)))
+    return [arr[i].as_dict() for i in range(count.value)]
+
+
+def autotune_save(path: str):
+    _check(load().scan_autotune_save(os.fsencode(path)))
+
+
+def autotune_load(path: str):
+    _check(load().scan_autotune_load(os.fsencode(path)))
+
+
+def autotune_reset():
+    _check(load().scan_autotune_reset())
+
+
 class Column:
     """Owning handle of a scan_column."""
 
@@ -269,6 +332,14 @@ class Column:
         dz = _vp()
         _check(load().scan_column_info(self._h, None, None, None, None, ctypes.byref(dz)))
         return dz.value or 0
+
+    def autotune(self, lo: int, hi: int, strategy="branchfree", reps: int = 3, stream=None) -> dict:
+        """Tune the kernel of `strategy` at this column's width (scan_autotune_column)."""
+        out = scan_tune_result()
+        _check(load().scan_autotune_column(self._h, scan_pred(lo, hi), _strategy(strategy), reps, _stream(stream),
+                                           ctypes.byref(out)))
+        return {"best": out.best.as_dict(), "rule": out.rule.as_dict(), "best_us": float(out.best_us),
+                "rule_us": float(out.rule_us), "candidates": int(out.candidates)}
 
     def run(self, lo: int, hi: int, strategy="branchfree", stream=None) -> scan_result:
         st = STRATEGIES[strategy] if isinstance(strategy, str) else int(strategy)
