@@ -444,7 +444,7 @@ def run_ours(args, world, rank, local):
     prof = traffic_from_profile()
     roofline = {"kernel": "k_scan_full<b, branch-free|branchy>, b=16..32", "bound": "hbm",
                 "achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s", "frac": round(ach / hbm_peak, 4),
-                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs, a read+write copy)",
+                "peak_source": f"{peak_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                 "frac_of_beta_read": round(ach / beta_read, 4),
                 "achieved_branchfree": round(ach_bf, 1), "achieved_branchy": round(ach_br, 1),
                 "time_share_of_step": share,
@@ -453,9 +453,8 @@ def run_ours(args, world, rank, local):
                 "traffic_case": prof["case"] if prof else None,
                 "traffic_ratio": (round(prof["dram_bytes_per_launch"] / prof["algorithmic_bytes_per_launch"], 4)
                                   if prof else None),
-                "traffic_source": (f"not measured in this run: dram read + write bytes of one launch "
-                                   f"({prof['case']}) from the ncu capture in profiles/scan_full_traffic.json "
-                                   f"(same kernel source digest)" if prof else
+                "traffic_source": (f"not measured in this run: ncu dram bytes of one launch ({prof['case']}), "
+                                   f"profiles/scan_full_traffic.json, same kernel source" if prof else
                                    "null: the committed ncu capture was taken on other kernel source")}
 
     # ---- realised selectivities
@@ -598,10 +597,11 @@ def run_ours(args, world, rank, local):
     torch.cuda.empty_cache()
     serving = run_serving(args, dev, stream, gbscan) if not args.no_serve and world == 1 else None
 
-    detail = {"autotune": tune, "per_b": per_b, "branch_crossover": branch, "plain_scan": plain, "probes": probes,
+    detail = {"autotune": tune, "per_b": per_b, "f_by_b": {st: [per_b[str(b)][st]["f"] for b in WIDTHS]
+                                                           for st in STRATS}, "branch_crossover": branch, "plain_scan": plain, "probes": probes,
               "zone_sweep": zone, "select": select, "layouts": layouts, "conjunctive": conj,
               "batched": batched, "serving": serving, "realised_sigma": realised, "roofline": roofline,
-              "law": law, "e2e": e2e, "cpu_baseline": cpu}
+              "law": law, "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks, "source_digest": source_digest()}
     line = headline(args, world, value, ms_max, len(order), per_b, roofline, law, e2e, cpu,
                     dict(plain=plain, probes=probes, zone=zone, select=select, layouts=layouts, conj=conj,
                          batched=batched, serving=serving, tune=tune), beta_read, clocks)
@@ -613,42 +613,40 @@ def run_ours(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+HEADLINE_MAX = 2400   # bytes: a consumer keeping only the last ~3 KB of stdout still sees one whole line
+
+
 def headline(args, world, value, ms_max, scans_per_step, per_b, roofline, law, e2e, cpu, sections,
              beta_read, clocks):
-    """The printed JSON line: the headline metric and a few KB of summary (the
-    detail sections go to the --detail file)."""
-    return {
+    """The printed JSON line: the headline metric and a short summary, under
+    HEADLINE_MAX bytes (the detail sections, per-width fractions included, go
+    to the --detail file; the summary is dropped if the line would not fit)."""
+    line = {
         "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": WORKLOAD,
-                   "parallelism": f"replicas x{world} (independent sweeps, no collective)",
-                   "l2": "inputs larger than L2 (17.7 GB of columns per step, 129 MB L2; consecutive "
-                         "launches read different columns)"},
+        "config": {"workload": WORKLOAD, "parallelism": f"replicas x{world}, no collective",
+                   "l2": "inputs > L2 (17.7 GB per step)"},
         "values_per_s": round(N_SWEEP * scans_per_step * args.steps * world / (ms_max * 1e-3), 1),
         "beta_read_gbs": round(beta_read, 1),
-        "f_by_b": {st: [round(per_b[str(b)][st]["f"], 3) for b in WIDTHS] for st in STRATS},
-        "roofline": compact_roofline(roofline),
-        "law": {st: {k: law[st][k] for k in ("t_dec_gvals", "b_star", "median_abs_err")} for st in STRATS},
+        "f_b16_32": {st: [min(per_b[str(b)][st]["f"] for b in WIDTHS if b >= 16),
+                          round(statistics.mean(per_b[str(b)][st]["f"] for b in WIDTHS if b >= 16), 4)]
+                     for st in STRATS},
+        "roofline": {k: roofline[k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic")},
+        "law": {st: [law[st]["t_dec_gvals"], law[st]["b_star"], law[st]["median_abs_err"]] for st in STRATS},
         "e2e": ({k: e2e[k] for k in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step",
-                                     "h2d_gbs_raw", "per_scan_roundtrip_gbs")}
-                | {"path": "C ABI from pinned host buffers; each upload serves its width's 12 scans "
-                           "(per-scan round trip beside it); paths in the detail file"} if e2e else None),
-        "cpu_baseline": ({k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample", "cpu_model",
-                                              "values_per_s")}
-                         | {"single_thread_gbs": cpu["single_thread"]["gbs"]} if cpu else None),
-        "summary": summarise(beta_read=beta_read, **sections),
+                                     "per_scan_roundtrip_gbs")} if e2e else None),
+        "cpu_baseline": ({k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")} if cpu else None),
         "gpu_launches": scans_per_step * args.steps,
-        "clocks": clocks,
-        "source_digest": source_digest(),
+        "clocks": {k: clocks.get(k) for k in ("sm_mhz", "sm_max_mhz", "reasons")},
         "detail": os.path.relpath(args.detail, ROOT) if args.detail else None,
     }
-
-
-def compact_roofline(r):
-    keys = ("kernel", "bound", "achieved", "peak", "unit", "frac", "peak_source", "frac_of_beta_read",
-            "achieved_branchfree", "achieved_branchy", "traffic", "traffic_ratio", "traffic_source")
-    return {k: r[k] for k in keys if k in r}
+    summary = summarise(beta_read=beta_read, **sections)
+    if summary:
+        line["summary"] = summary
+        if len(json.dumps(line)) > HEADLINE_MAX:
+            del line["summary"]
+    return line
 
 
 def summarise(plain, probes, zone, select, layouts, conj, batched, serving, beta_read, tune=None):
@@ -656,46 +654,27 @@ def summarise(plain, probes, zone, select, layouts, conj, batched, serving, beta
     themselves go to the detail file)."""
     out = {}
     if tune and "sweep_gain" in tune:
-        out["autotune"] = {"sweep_step_ms_rule": tune["sweep_step_ms_rule"],
-                           "sweep_step_ms_tuned": tune["sweep_step_ms_tuned"], "gain": tune["sweep_gain"]}
+        out["tune_gain"] = tune["sweep_gain"]
     if plain:
-        out["plain_scan_2p24_b8"] = {"us_l2_flushed": round(plain["ms_l2_flushed"] * 1e3, 2),
-                                     "gbs_l2_flushed": plain["gbs_l2_flushed"],
-                                     "us_l2_warm": round(plain["ms_l2_warm"] * 1e3, 2)}
+        out["plain_us"] = round(plain["ms_l2_flushed"] * 1e3, 2)
     if probes:
-        out["triad_gbs"] = probes["triad"]["gbs"]
-        dr = probes["decode_resident"]
-        out["t_dec_resident_gvals"] = dr["t_dec_median_below_ridge_gvals"]
-        out["negative_control_iii"] = dr.get("l2_control")
+        out["neg_ctrl_iii"] = probes["decode_resident"]["l2_control"]["above_beta_read"]
     if zone:
         rows = zone["rows"]
-        out["zone"] = {
-            "sorted_speedup_by_sigma": [r["speedup"] for r in rows if r["p"] == 0.0],
-            "min_speedup_p_ge_0.01": min(r["speedup"] for r in rows if r["p"] >= 0.01),
-            "sorted_speedup_zone_agg_min": min(r["speedup_zone_agg"] for r in rows if r["p"] == 0.0),
-            "exact": all(r["exact"] for r in rows)}
+        out["zone"] = [min(r["speedup"] for r in rows if r["p"] >= 0.01),
+                       min(r["speedup_auto"] for r in rows),
+                       max(r["speedup_auto"] for r in rows), all(r["exact"] for r in rows)]
     if select:
-        out["select_best_frac"] = {b: v["best_frac_branchfree"] for b, v in select["by_b"].items()}
-        out["select_exact"] = select["exact"]
-    if layouts:
-        out["layouts_t_dec_gvals"] = {k: v["t_dec_gvals"] for k, v in layouts["per_layout"].items()}
-    if conj:
-        out["conj_frac"] = [r["frac_conj"] for r in conj["rows"]]
+        out["select_frac"] = max(v["best_frac_branchfree"] for v in select["by_b"].values())
     if batched:
         pl = batched["plans"]
-        out["batched"] = {"ms_per_column_graph": batched["ms_per_column_graph"],
-                          "ms": {k: v["ms"] for k, v in pl.items()},
-                          "speedup_law_vs_per_column": pl["law"]["speedup_vs_per_column_graph"],
-                          "exact": all(v["exact"] for v in pl.values())}
-        if "planner_vs_law" in batched:
-            out["batched"]["planner_vs_law"] = batched["planner_vs_law"]
+        out["batch_ms"] = [batched["ms_per_column_graph"], pl["law"]["ms"], pl["planned_mlp"]["ms"],
+                           all(v["exact"] for v in pl.values())]
     if serving:
-        out["serving"] = {"serial_qps": serving["serial"]["qps"],
-                          "load": [x["load"] for x in serving["loads"]],
-                          "qps": [x["achieved_qps"] for x in serving["loads"]],
-                          "p50_us": [x["p50_us"] for x in serving["loads"]],
-                          "p99_us": [x["p99_us"] for x in serving["loads"]],
-                          "exact": all(x["exact_vs_alone"] for x in serving["loads"])}
+        ld = {x["load"]: x for x in serving["loads"]}
+        if 0.9 in ld:
+            out["serve_0.9"] = [ld[0.9]["achieved_qps"], ld[0.9]["p50_us"], ld[0.9]["p99_us"]]
+        out["serve_exact"] = all(x["exact_vs_alone"] for x in serving["loads"])
     return out
 
 
@@ -708,7 +687,7 @@ def run_zone_sweep(args, dev, stream, gbscan):
     out = {"workload": "zone sweep: N=2^30 at b=16, sorted then p in {0,0.01,0.1,1} displaced, "
                        "sigma in {1e-4,1e-3,1e-2,0.1,0.5}; full scan, zone skip, and zone skip answering "
                        "wholly-inside blocks from per-block (min, max, sum)", "rows": []}
-    res = torch.zeros((3, 4), dtype=torch.int64, device=dev)
+    res = torch.zeros((4, 4), dtype=torch.int64, device=dev)
     # the 1%-displaced column first: the zone-skip kernel's shape is tuned on it
     # (sigma 0.1, most blocks survive) and then used for every row
     for pi, p in [(1, 0.01), (0, 0.0), (2, 0.1), (3, 1.0)]:
@@ -719,6 +698,11 @@ def run_zone_sweep(args, dev, stream, gbscan):
             col.zonemap_build(stream)
         torch.cuda.synchronize()
         torch.cuda.empty_cache()
+        # a freshly built column's first scans ran ~40% slower for a few ms
+        # (0.44 against 0.31 ms): warm it before any row is timed
+        for _ in range(20):
+            col.run_async(0, 1 << b, res[0], "branchfree", stream)
+        torch.cuda.synchronize()
         if pi == 1 and not args.no_tune and not args.shapes:
             lo, hi = synth.pick_range(synth.seed_for(3, pi, 4), b, 0.1)
             r_ = col.autotune(lo, hi, "zone_bf", reps=3, stream=stream)
@@ -727,7 +711,7 @@ def run_zone_sweep(args, dev, stream, gbscan):
         for si, sigma in enumerate([1e-4, 1e-3, 1e-2, 0.1, 0.5]):
             lo, hi = synth.pick_range(synth.seed_for(3, pi, si + 1), b, sigma)
             ts = {}
-            for k, strat in enumerate(["branchfree", "zone_bf", "zone_agg_bf"]):
+            for k, strat in enumerate(["branchfree", "zone_bf", "zone_agg_bf", "auto"]):
                 col.run_async(lo, hi, res[k], strat, stream)
                 vals = []
                 for _ in range(3):
@@ -747,7 +731,10 @@ def run_zone_sweep(args, dev, stream, gbscan):
                                 "ms_zone_agg": round(ts["zone_agg_bf"], 4),
                                 "speedup_zone_agg": round(ts["branchfree"] / ts["zone_agg_bf"], 2),
                                 "blocks_read_fraction_zone_agg": round(int(r[2, 2]) / int(r[0, 2]), 6),
-                                "exact": bool((r[0, :2] == r[1, :2]).all() and (r[0, :2] == r[2, :2]).all())})
+                                "ms_auto": round(ts["auto"], 4),
+                                "speedup_auto": round(ts["branchfree"] / ts["auto"], 2),
+                                "blocks_read_fraction_auto": round(int(r[3, 2]) / int(r[0, 2]), 6),
+                                "exact": bool(all((r[0, :2] == r[k, :2]).all() for k in (1, 2, 3)))})
         col.close()
         torch.cuda.empty_cache()
     return out

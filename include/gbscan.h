@@ -60,11 +60,24 @@ typedef enum {
 } scan_status;
 
 typedef enum {
-    SCAN_AUTO = 0,         /* library picks (law / planner); always the same result */
+    /* Library picks, per call, by the paper's law (§2) and its clustering
+     * crossover (§6: skipping pays on clustered data only).  Without a zone
+     * map: the branch-free full scan.  With one (lane layout): the exact
+     * number of blocks the zone test would keep is counted on the host from
+     * sorted copies of the zone map's bounds (no device work, no
+     * synchronization), and the branch-free full scan runs when they reach the
+     * law's break-even -- a fraction min(0.9, (128b - 8) / (128b + 8)) of the
+     * blocks, where the 8 bytes of zone map and id per block cost what the
+     * 128b data bytes of the skipped ones save -- else branch-free zone
+     * skipping.  The first SCAN_AUTO call after scan_zonemap_build copies the
+     * zone map to the host and sorts its bounds, synchronizing `stream` once
+     * (make it before any stream capture).  blocks_scanned reports which was
+     * run.  Always the same COUNT/SUM. */
+    SCAN_AUTO = 0,
     SCAN_BRANCHFREE = 1,   /* full scan, predicated (mask) aggregation */
     SCAN_BRANCHY = 2,      /* full scan, warp-vote early-out per 32-value group */
-    SCAN_ZONE_SKIP_BF = 3, /* zone-map block skipping + persistent queue, branch-free */
-    SCAN_ZONE_SKIP_BR = 4, /* zone-map block skipping + persistent queue, branchy */
+    SCAN_ZONE_SKIP_BF = 3, /* zone-map block skipping (a persistent walk over the survivors), branch-free */
+    SCAN_ZONE_SKIP_BR = 4, /* zone-map block skipping (a persistent walk over the survivors), branchy */
     /* Zone skipping that also answers every block wholly inside [lo, hi)
      * (lo <= min and max < hi) from its metadata -- its valid count and the
      * per-block sum built by scan_zonemap_build -- without reading its data;

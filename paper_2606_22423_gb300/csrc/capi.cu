@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <atomic>
 #include <cstdarg>
 #include <cstdio>
@@ -212,6 +213,10 @@ struct scan_column {
     uint2* zonemap = nullptr;
     unsigned long long* blocksum = nullptr;  // per-block sums, built with the zone map
     bool zonemap_valid = false;
+    // SCAN_AUTO: the zone map's block minima and maxima, each sorted, on the
+    // host (taken on the first SCAN_AUTO call after the zone map is built)
+    std::vector<uint32_t> zmin_sorted, zmax_sorted;
+    bool zsorted_valid = false;
     unsigned int* cand = nullptr;
     void* ws_raw = nullptr;
     Workspace ws{};
@@ -543,6 +548,53 @@ bool translate(const scan_column* c, scan_pred pr, gb::ScanParams& p)
     return true;
 }
 
+// SCAN_AUTO reads every block once the zone test would keep at least this
+// many of the column's blocks: the law's break-even, where the 8 bytes of zone
+// map and candidate id per block cost as much as the 128*b data bytes the
+// skipped blocks save, f = (128b - 8) / (128b + 8), capped at 0.9.
+uint64_t auto_dense_min(uint32_t b, uint64_t nblocks)
+{
+    const double db = static_cast<double>(b);
+    const double f = std::min(0.9, (128.0 * db - 8.0) / (128.0 * db + 8.0));
+    return static_cast<uint64_t>(std::ceil(f * static_cast<double>(nblocks)));
+}
+
+// Exact number of blocks the zone test keeps for [zlo, zhi): a block is
+// skipped iff max < zlo or min >= zhi, two disjoint cases since min <= max,
+// so survivors = blocks - #(max < zlo) - #(min >= zhi): two binary searches
+// over sorted copies of the bounds (copied and sorted on first use).
+scan_status auto_survivors(scan_column* c, uint64_t zlo, uint64_t zhi, cudaStream_t st, uint64_t* out)
+{
+    const uint64_t nb = n_blocks(c->n);
+    if (!c->zsorted_valid) {
+        std::vector<uint2> z(nb);
+        GB_CUDA(cudaMemcpyAsync(z.data(), c->zonemap, nb * sizeof(uint2), cudaMemcpyDeviceToHost, st));
+        GB_CUDA(cudaStreamSynchronize(st));
+        c->zmin_sorted.resize(nb);
+        c->zmax_sorted.resize(nb);
+        for (uint64_t i = 0; i < nb; ++i) {
+            c->zmin_sorted[i] = z[i].x;
+            c->zmax_sorted[i] = z[i].y;
+        }
+        std::sort(c->zmin_sorted.begin(), c->zmin_sorted.end());
+        std::sort(c->zmax_sorted.begin(), c->zmax_sorted.end());
+        c->zsorted_valid = true;
+    }
+    // #(max < zlo): maxima below zlo; #(min >= zhi): minima at or above zhi
+    const uint64_t below = zlo > 0xffffffffull
+                               ? nb
+                               : static_cast<uint64_t>(std::lower_bound(c->zmax_sorted.begin(), c->zmax_sorted.end(),
+                                                                        static_cast<uint32_t>(zlo)) -
+                                                       c->zmax_sorted.begin());
+    const uint64_t above = zhi > 0xffffffffull
+                               ? 0
+                               : static_cast<uint64_t>(c->zmin_sorted.end() -
+                                                       std::lower_bound(c->zmin_sorted.begin(), c->zmin_sorted.end(),
+                                                                        static_cast<uint32_t>(zhi)));
+    *out = nb - below - above;
+    return SCAN_OK;
+}
+
 scan_status enqueue_scan(scan_column* c, scan_pred pred, scan_strategy strategy, cudaStream_t st,
                          long long* dev_result, bool* empty)
 {
@@ -553,7 +605,15 @@ scan_status enqueue_scan(scan_column* c, scan_pred pred, scan_strategy strategy,
         return SCAN_OK;
     }
     if (dev_result) p.result = dev_result;
-    if (strategy == SCAN_AUTO) strategy = SCAN_BRANCHFREE;
+    if (strategy == SCAN_AUTO) {
+        strategy = SCAN_BRANCHFREE;
+        if (c->zonemap_valid && c->layout == SCAN_LAYOUT_LANES) {
+            uint64_t survivors = 0;
+            const scan_status s = auto_survivors(c, p.zlo, p.zhi, st, &survivors);
+            if (s != SCAN_OK) return s;
+            if (survivors < auto_dense_min(c->b, n_blocks(c->n))) strategy = SCAN_ZONE_SKIP_BF;
+        }
+    }
     const int grid = persistent_grid();
     int op;
     switch (strategy) {
@@ -838,6 +898,7 @@ scan_status scan_column_upload_packed(scan_column* col, const uint32_t* host_pac
         GB_CUDA(cudaMemcpyAsync(col->packed, host_packed, words * 4, cudaMemcpyHostToDevice,
                                 as_stream(stream)));
     col->zonemap_valid = false;
+    col->zsorted_valid = false;
     return SCAN_OK;
 }
 
@@ -893,6 +954,7 @@ scan_status scan_zonemap_build(scan_column* col, void* stream)
         if (e != cudaSuccess) return cuda_fail(e, "zone-map build launch");
     }
     col->zonemap_valid = true;
+    col->zsorted_valid = false;
     return SCAN_OK;
 }
 

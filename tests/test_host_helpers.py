@@ -63,7 +63,7 @@ def test_headline_line_stays_small_with_every_section_present():
     roof = {"kernel": "k", "bound": "hbm", "achieved": 6300.0, "peak": 6702.8, "unit": "GB/s", "frac": 0.94,
             "peak_source": "measured", "frac_of_beta_read": 0.9, "achieved_branchfree": 6500.0,
             "achieved_branchy": 6100.0, "time_share_of_step": {"branchfree": 0.45}, "traffic": 808977152,
-            "traffic_ratio": 1.0046, "traffic_source": "x" * 180}
+            "traffic_ratio": 1.0046, "traffic_source": "x" * 150}
     e2e = {"value": 2100.0, "unit": "GB/s", "h2d_bytes_per_step": 17716740096, "d2h_bytes_per_step": 12288,
            "h2d_gbs_raw": 211.0, "path": "y" * 250, "per_scan_roundtrip_gbs": 190.0,
            "per_scan_roundtrip_path": "z" * 120}
@@ -75,12 +75,13 @@ def test_headline_line_stays_small_with_every_section_present():
             "t_dec_median_below_ridge_gvals": 5.0,
             "l2_control": {"case": "c" * 100, "l2_gbs_median": 8500.0, "l2_gbs_min": 8100.0,
                            "beta_read_gbs": 7100.0, "above_beta_read": True}}},
-        "zone": {"rows": [{"p": p, "sigma": s, "speedup": 12.5, "speedup_zone_agg": 13.1, "exact": True}
+        "zone": {"rows": [{"p": p, "sigma": s, "speedup": 12.5, "speedup_zone_agg": 13.1, "speedup_auto": 12.4, "exact": True}
                           for p in (0.0, 0.01, 0.1, 1.0) for s in (1e-4, 1e-3, 1e-2, 0.1, 0.5)]},
         "select": {"by_b": {"32": {"best_frac_branchfree": 0.95}, "16": {"best_frac_branchfree": 0.79}},
                    "exact": True},
         "layouts": {"per_layout": {k: {"t_dec_gvals": 3.5} for k in ("lanes", "rowmajor", "bytes")}},
         "conj": {"rows": [{"frac_conj": 0.77} for _ in range(4)]},
+        "tune": {"sweep_gain": 1.097},
         "batched": {"ms_per_column_graph": 23.7, "plans": {
             k: {"ms": 0.97, "speedup_vs_per_column_graph": 24.4, "exact": True}
             for k in ("branchfree", "law", "planned_mlp", "law_calibrated", "planned_mlp_law_prior")},
@@ -93,11 +94,12 @@ def test_headline_line_stays_small_with_every_section_present():
     clocks = {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 100}
     line = bench.headline(args, 1, 5080.0, 838.0, 384, per_b, roof, law, e2e, cpu, sections, 7100.0, clocks)
     text = json.dumps(line)
-    assert len(text) < 4096, len(text)
+    assert len(text) <= bench.HEADLINE_MAX, len(text)
+    assert "summary" in line                            # it fits with every section present
     for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
                 "scaling", "vs_baseline", "dtype", "data", "config", "roofline", "e2e", "cpu_baseline",
                 "gpu_launches", "clocks"):
         assert key in line
     assert line["roofline"]["frac"] == 0.94 and line["cpu_baseline"]["kind"] == "oracle"
-    assert line["summary"]["negative_control_iii"]["above_beta_read"] is True
+    assert line["summary"]["neg_ctrl_iii"] is True and line["summary"]["tune_gain"] > 1
     assert line["gpu_launches"] == 384 * 20

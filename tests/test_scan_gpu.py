@@ -4,6 +4,8 @@ Integer work, so the bar is bit-exact: COUNT, SUM and (for zone skipping)
 the number of blocks read must equal the oracle's.  Small cases span several
 tiles of every width plus a ragged tail; the large cases use the sizes and
 launch shapes the benchmark times."""
+import math
+
 import numpy as np
 import pytest
 
@@ -15,7 +17,13 @@ from tests._cudart import d2h_u32
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-STRATS = ["branchfree", "branchy", "zone_bf", "zone_br"]
+STRATS = ["branchfree", "branchy", "zone_bf", "zone_br", "auto"]
+
+
+def auto_dense_min(nblocks, b):
+    """SCAN_AUTO's break-even survivor count (header: a fraction
+    min(0.9, (128b - 8) / (128b + 8)) of the blocks)."""
+    return math.ceil(min(0.9, (128.0 * b - 8.0) / (128.0 * b + 8.0)) * nblocks)
 SIGMAS = [1e-3, 0.1, 0.5, 1.0]
 
 
@@ -50,6 +58,9 @@ def _check_column(col, v, b, base, preds, zmin=None, zmax=None, words=None):
                 empty = max(lo, base) >= min(hi, base + (1 << b))
                 if not empty:
                     expect_blocks = touched if strat.startswith("zone") else nblocks
+                    if strat == "auto":
+                        # the zone test's survivors against the break-even: all blocks, or the survivors
+                        expect_blocks = nblocks if touched >= auto_dense_min(nblocks, b) else touched
                     assert r.blocks_scanned == expect_blocks, (strat, r.blocks_scanned, expect_blocks)
 
 
