@@ -212,6 +212,7 @@ def cpu_sample(columns_host, threads, budget_s, passes_max=3, strategies=1, sigm
     return total_bytes / t_used / 1e9, total_vals / t_used, scans, t_used, vps
 
 
+TUNED_SHAPES = os.path.join(ROOT, "paper_2606_22423_gb300", "tuned", "gb300_shapes.txt")
 CPU_SAMPLE_LOG2 = 25   # both oracle legs (the reference arm, cpu_baseline) scan 2^25-value columns
 
 
@@ -1356,6 +1357,13 @@ def run_case(args):
 
     libbuild.build()
     gbscan.load()
+    # the launch shapes the benchmark tunes (the packaged GB300 cache unless --shapes names another)
+    shapes = args.shapes or TUNED_SHAPES
+    if os.path.exists(shapes):
+        try:
+            gbscan.autotune_load(shapes)
+        except gbscan.ScanError as e:   # tuned on another device: keep the built-in rule
+            print(f"shapes not loaded: {e}", file=sys.stderr)
     s = torch.cuda.Stream()
     if args.case == "batch":
         spec = synth.batch_spec(synth.seed_for(4), ncols=args.batch_cols, total=args.n)
@@ -1417,6 +1425,7 @@ def run_case(args):
     r = out.cpu().tolist()
     nbytes = gbscan.scan_packed_words(args.n, args.b) * 4 + (4 * r[0] if select else 0)
     print(json.dumps({"case": args.case, "b": args.b, "n": args.n, "strategy": args.strategy,
+                      "shape": gbscan.shape_get(args.b, args.strategy if args.strategy != "auto" else "branchfree"),
                       "order": args.order, "ms": ms, "gbs": nbytes / (ms * 1e-3) / 1e9,
                       "count": r[0], "sum": r[1], "blocks": r[2]}))
     col.close()
