@@ -671,6 +671,8 @@ def summarise(plain, probes, zone, select, layouts, conj, batched, serving, beta
         pl = batched["plans"]
         out["batch_ms"] = [batched["ms_per_column_graph"], pl["law"]["ms"], pl["planned_mlp"]["ms"],
                            all(v["exact"] for v in pl.values())]
+        if batched.get("autotune"):
+            out["batch_tune_gain"] = batched["autotune"]["gain"]
     if serving:
         ld = {x["load"]: x for x in serving["loads"]}
         if 0.9 in ld:
@@ -1205,6 +1207,28 @@ def run_batched(args, dev, stream, gbscan, beta_gbs, t_dec_gvals):
              "law_calibrated": calib_plan, "planned_mlp_law_prior": mlp_law_plan}
     res_b = torch.zeros((ncols, 4), dtype=torch.int64, device=dev)
     parr = gbscan.Batch.pred_array(preds)      # marshalled once, outside the timed region
+    # launch shapes of the batched kernels: each width group of the law plan (its
+    # branch-free and zone-skip groups) tuned alone; every plan below runs with them
+    batch_tune = None
+    if not args.no_tune and not args.shapes:
+        bt_l = gbscan.Batch(cols, law_plan)
+        bt_l.run(parr, stream=stream, dev_out=res_b, host=False)
+        ms_rule = time_calls(lambda: bt_l.run(parr, stream=stream, dev_out=res_b, host=False), 7)
+        t_tune = time.perf_counter()
+        r_ = bt_l.autotune(parr, reps=3, stream=stream)
+        tune_s = time.perf_counter() - t_tune
+        bt_l.run(parr, stream=stream, dev_out=res_b, host=False)
+        ms_tuned = time_calls(lambda: bt_l.run(parr, stream=stream, dev_out=res_b, host=False), 7)
+        bt_l.close()
+        batch_tune = {"plan": "law", "groups": r_["groups"], "seconds": round(tune_s, 1),
+                      "ms_graph_rule": round(ms_rule, 4), "ms_graph_tuned": round(ms_tuned, 4),
+                      "gain": round(ms_rule / ms_tuned, 4),
+                      "groups_alone_us_rule": round(r_["rule_us"], 1), "groups_alone_us_tuned": round(r_["tuned_us"], 1),
+                      "shapes": {f"b{b}": [gbscan.batch_shape_get(b, False)[k]
+                                           for k in ("warps", "stages", "tile_blocks")] for b in range(1, 33)}}
+        shapes_path = os.path.join(os.path.dirname(os.path.abspath(args.detail or "bench_detail.json")),
+                                   "bench_shapes.txt")
+        gbscan.autotune_save(shapes_path)
     for name, strategies in plans.items():
         bt = gbscan.Batch(cols, strategies)
         bt.run(parr, stream=stream, dev_out=res_b, host=False)
@@ -1223,7 +1247,7 @@ def run_batched(args, dev, stream, gbscan, beta_gbs, t_dec_gvals):
         c.close()
     return {"workload": BATCH_WORKLOAD, "ncols": ncols, "values": total_values, "packed_bytes": total_bytes,
             "ms_per_column_graph": round(ms_graph, 4), "ms_per_column_loop": round(ms_loop, 4),
-            "per_column_launches": ncols, "plans": out,
+            "per_column_launches": ncols, "plans": out, "autotune": batch_tune,
             "planner": {"training_columns": TRAIN_COLS, "training_lengths": "log-uniform in [2^22, 2^27] values",
                         "labels": "log of each strategy's marginal device time as a one-entry batch",
                         "steps": 1500, "loss_first": round(hist[0], 4), "loss_last": round(hist[-1], 4),

@@ -307,6 +307,18 @@ scan_status scan_batch_create(scan_column *const *cols, uint32_t ncols,
 scan_status scan_batch_exec(scan_batch *batch, const scan_pred *preds, void *stream,
                             scan_result *host_out, scan_result *dev_out);
 
+/* Autotune the batch's width-group kernels on these predicates (no paper
+ * counterpart; the shapes never change a result): for every width group,
+ * time its kernel alone (`reps` launches on `stream`, after a warm-up) with
+ * the rule and with every candidate shape of its flavour and width, and
+ * install the fastest in the process-wide batch shape table; the batch is then
+ * laid out again with the installed shapes.  Blocking.  *groups_tuned gets the
+ * number of width groups, *rule_us and *tuned_us (may be NULL) the sums of the
+ * groups' times alone before and after -- the groups overlap in a replay, so
+ * these bound rather than predict its time.  Results are unaffected. */
+scan_status scan_batch_autotune(scan_batch *batch, const scan_pred *preds, uint32_t reps, void *stream,
+                                uint32_t *groups_tuned, float *rule_us, float *tuned_us);
+
 /* Free the plan (synchronises the device first). */
 scan_status scan_batch_destroy(scan_batch *batch);
 
@@ -577,6 +589,21 @@ scan_status scan_autotune_save(const char *path);
 scan_status scan_autotune_load(const char *path);
 /* Every kernel back to the built-in rule. */
 scan_status scan_autotune_reset(void);
+
+/* Shapes of the batched kernels, one per (predicate flavour, b): every width
+ * group of a batch launches one kernel with its width's shape (tile_blocks =
+ * blocks per batch tile; vote_rows must be 0).  Legal: 1..16 warps, 1..6
+ * stages, tile_blocks a multiple of the warp step and at most 64, warps *
+ * stages * (tile_blocks * 128 * b + 24) <= 226 KB.  branchy = 0 for the
+ * branch-free kernel, 1 for the branchy one.  They are saved and loaded with
+ * the others ("batch_bf" / "batch_br" lines).  A batch picks up shape
+ * changes when it is created, when its strategies are set, or when it is
+ * tuned. */
+scan_status scan_batch_shape_get(uint32_t b, int branchy, scan_shape *out);
+scan_status scan_batch_shape_set(uint32_t b, int branchy, const scan_shape *shape);
+scan_status scan_batch_shape_candidates(uint32_t b, int branchy, scan_shape *out, uint32_t capacity,
+                                        uint32_t *count);
+
 
 #ifdef __cplusplus
 }

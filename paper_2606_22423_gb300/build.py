@@ -41,8 +41,9 @@ def _units():
         units.append((os.path.join(CSRC, "scan_inst.cu"), f"scan_b{lo:02d}_{hi:02d}.o",
                       [f"-DGB_BLO={lo}", f"-DGB_BHI={hi}"]))
     for flavour in (0, 1):
-        units.append((os.path.join(CSRC, "batch_inst.cu"), f"batch_k{flavour}.o",
-                      [f"-DGB_BATCH_BRANCHY={flavour}"]))
+        for lo, hi in RANGES:
+            units.append((os.path.join(CSRC, "batch_inst.cu"), f"batch_k{flavour}_b{lo:02d}_{hi:02d}.o",
+                          [f"-DGB_BATCH_BRANCHY={flavour}", f"-DGB_BLO={lo}", f"-DGB_BHI={hi}"]))
     for f in sorted(os.listdir(CSRC)):
         if f.endswith(".cu") and f not in ("scan_inst.cu", "batch_inst.cu"):
             units.append((os.path.join(CSRC, f), f[:-3] + ".o", []))

@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -42,7 +43,6 @@ scan_status bcuda(cudaError_t e, const char* what)
 
 int batch_grid() { return gb_device_sms(); }
 
-uint32_t tile_blocks_for(uint32_t b) { return gb::batch_tile_blocks(b); }
 
 // Control words after the results: one pop counter per width group (u32),
 // then the status word at u32 index kMaxGroups.
@@ -67,6 +67,8 @@ struct scan_batch {
         uint32_t first, count, ntiles, chunk;
         int grid;
         uint32_t chunk_off;  // offset of this group's chunk -> column table
+        gb::LaunchShape shape;  // warps, stages and tile blocks of this width group
+        double est_us;          // its time alone: tuned, else the law's max(bytes / beta, values / T_dec)
     };
     std::vector<Group> groups;  // one width-specialised launch each
     uint32_t* d_chunk_col = nullptr;  // all groups' chunk -> first-column tables
@@ -81,13 +83,11 @@ struct scan_batch {
     cudaGraphExec_t graph = nullptr;
 };
 
-cudaError_t gb_launch_batch_branchfree(int b, const gb::BatchParams& p, int grid, cudaStream_t st);
-cudaError_t gb_launch_batch_branchy(int b, const gb::BatchParams& p, int grid, cudaStream_t st);
-
 namespace gb {
-static cudaError_t launch_batch_kernel(bool branchy, int b, const BatchParams& p, int grid, cudaStream_t st)
+static cudaError_t launch_batch_kernel(bool branchy, int b, const BatchParams& p, int warps, int grid,
+                                       cudaStream_t st)
 {
-    return branchy ? gb_launch_batch_branchy(b, p, grid, st) : gb_launch_batch_branchfree(b, p, grid, st);
+    return gb_launch_batch(branchy, b, p, warps, grid, st);
 }
 }  // namespace gb
 
@@ -125,7 +125,9 @@ scan_status layout(scan_batch* bt)
         const int k = bt->kernel_of[i];
         if (bt->groups.empty() || bt->groups.back().kernel != k ||
             bt->groups.back().b != static_cast<int>(width[i])) {
-            bt->groups.push_back({k, static_cast<int>(width[i]), j, 0, 0, 1});
+            scan_batch::Group g{k, static_cast<int>(width[i]), j, 0, 0, 1, 1, 0, {}, 0.0};
+            g.shape = gb_shape_for(g.b, k == 1 ? gb::kOpBatchBR : gb::kOpBatchBF);
+            bt->groups.push_back(g);
             group_tiles = 0;
         }
         const uint2* zm = nullptr;
@@ -139,7 +141,7 @@ scan_status layout(scan_batch* bt)
         d.n = n;
         d.b = b;
         d.base = base;
-        d.tile_blocks = tile_blocks_for(b);
+        d.tile_blocks = static_cast<uint32_t>(bt->groups.back().shape.tile_blocks);
         d.tile_begin = group_tiles;  // tile numbers restart in every width group
         d.out = i;
         const uint64_t nblocks = (n + 1023u) >> 10;
@@ -147,6 +149,10 @@ scan_status layout(scan_batch* bt)
         if (group_tiles + t > 0xffffffffull) return bfail(SCAN_EINVAL, "too many tiles in one batch");
         group_tiles += static_cast<uint32_t>(t);
         tiles[k] += static_cast<uint32_t>(t);
+        // default estimate of the group's time alone (us): the law with a 6.6 TB/s
+        // read rate and 4 Tvalues/s of decode; a tuned group's own time replaces it
+        bt->groups.back().est_us += std::max(static_cast<double>(nblocks) * 128.0 * b / 6.6e6,
+                                             static_cast<double>(n) / 4.0e6);
         bt->groups.back().count += 1;
         bt->groups.back().ntiles = group_tiles;
         bt->slot_of[i] = j;
@@ -160,9 +166,10 @@ scan_status layout(scan_batch* bt)
     std::vector<uint32_t> chunk_col;
     const int sms = batch_grid();
     for (auto& g : bt->groups) {
-        const uint64_t want = (static_cast<uint64_t>(g.ntiles) + 16 * gb::kBatchWarps - 1) / (16 * gb::kBatchWarps);
+        const uint64_t gw = static_cast<uint64_t>(g.shape.warps);
+        const uint64_t want = (static_cast<uint64_t>(g.ntiles) + 16 * gw - 1) / (16 * gw);
         g.grid = static_cast<int>(std::max<uint64_t>(1, std::min<uint64_t>(want, sms)));
-        const uint32_t warps = static_cast<uint32_t>(g.grid) * gb::kBatchWarps;
+        const uint32_t warps = static_cast<uint32_t>(g.grid * gw);
         const uint32_t c = bt->tiles_per_pop ? bt->tiles_per_pop : std::max<uint32_t>(4, g.ntiles / (4 * warps));
         g.chunk = std::min<uint32_t>(c, 1024);
         g.chunk_off = static_cast<uint32_t>(chunk_col.size());
@@ -552,12 +559,19 @@ scan_status scan_batch_exec(scan_batch* bt, const scan_pred* preds, void* stream
         cudaMemcpyAsync(bt->d_table, bt->h_table, table_bytes, cudaMemcpyHostToDevice, cs);
         cudaMemsetAsync(bt->d_results, 0, res_words * sizeof(unsigned long long), cs);
         cudaEventRecord(bt->fork, cs);
+        // longest group first onto the least-loaded branch (LPT): the branches'
+        // sums of group times, the replay's critical paths, stay balanced
         bool used[kBranches] = {};
-        int next_branch = 0;
-        for (size_t gi = 0; gi < bt->groups.size(); ++gi) {
+        double load[kBranches] = {};
+        std::vector<size_t> order(bt->groups.size());
+        for (size_t gi = 0; gi < order.size(); ++gi) order[gi] = gi;
+        std::stable_sort(order.begin(), order.end(),
+                         [&](size_t x, size_t y) { return bt->groups[x].est_us > bt->groups[y].est_us; });
+        for (const size_t gi : order) {
             const auto& g = bt->groups[gi];
             if (!g.ntiles) continue;
-            const int k = next_branch++ % kBranches;
+            const int k = static_cast<int>(std::min_element(load, load + kBranches) - load);
+            load[k] += g.est_us;
             cudaStream_t bs = bt->branch[k];
             if (!used[k]) cudaStreamWaitEvent(bs, bt->fork, 0);  // joins the capture
             used[k] = true;
@@ -570,7 +584,9 @@ scan_status scan_batch_exec(scan_batch* bt, const scan_pred* preds, void* stream
             p.head = reinterpret_cast<unsigned int*>(ctl) + gi;
             p.results = bt->d_results;
             p.status = reinterpret_cast<unsigned int*>(ctl) + kMaxGroups;
-            gb::launch_batch_kernel(g.kernel == 1, g.b, p, g.grid, bs);
+            p.stages = static_cast<uint32_t>(g.shape.stages);
+            p.slot_bytes = static_cast<uint32_t>(g.shape.tile_blocks) * 128u * static_cast<uint32_t>(g.b);
+            gb::launch_batch_kernel(g.kernel == 1, g.b, p, g.shape.warps, g.grid, bs);
         }
         for (int k = 0; k < kBranches; ++k) {
             if (!used[k]) continue;
@@ -597,6 +613,99 @@ scan_status scan_batch_exec(scan_batch* bt, const scan_pred* preds, void* stream
         if (status) return bfail(SCAN_ETIMEOUT, "a device-side wait timed out in the batch kernel");
         std::memcpy(host_out, bt->h_results, sizeof(scan_result) * bt->ncols);
     }
+    return SCAN_OK;
+}
+
+scan_status scan_batch_autotune(scan_batch* bt, const scan_pred* preds, uint32_t reps, void* stream,
+                                uint32_t* groups_tuned, float* rule_us, float* tuned_us)
+{
+    gb_set_last_error("");
+    if (!bt || (bt->ncols && !preds)) return bfail(SCAN_EINVAL, "null pointer");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    reps = std::max<uint32_t>(1, std::min<uint32_t>(reps, 100));
+    BT_CUDA(cudaStreamSynchronize(st));
+    fill_predicates(bt, preds);
+    unsigned long long* ctl = bt->d_results + 4ull * std::max<uint32_t>(1, bt->ncols);
+    const size_t table_bytes = std::max<size_t>(1, bt->ncols) * sizeof(gb::BatchCol);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    BT_CUDA(cudaEventCreate(&e0));
+    BT_CUDA(cudaEventCreate(&e1));
+    float sum_rule = 0.f, sum_best = 0.f;
+    uint32_t tuned = 0;
+    scan_status status = SCAN_OK;
+    // Mean time of `reps` launches of group gi alone, with the shapes installed now.
+    auto time_group = [&](size_t gi, float* us) -> scan_status {
+        scan_status s = layout(bt);
+        if (s != SCAN_OK) return s;
+        fill_predicates(bt, preds);
+        const auto& g = bt->groups[gi];
+        BT_CUDA(cudaMemcpyAsync(bt->d_table, bt->h_table, table_bytes, cudaMemcpyHostToDevice, st));
+        gb::BatchParams p{};
+        p.cols = bt->d_table + g.first;
+        p.chunk_col = bt->d_chunk_col + g.chunk_off;
+        p.ncols = g.count;
+        p.ntiles = g.ntiles;
+        p.chunk = g.chunk;
+        p.head = reinterpret_cast<unsigned int*>(ctl) + gi;
+        p.results = bt->d_results;
+        p.status = reinterpret_cast<unsigned int*>(ctl) + kMaxGroups;
+        p.stages = static_cast<uint32_t>(g.shape.stages);
+        p.slot_bytes = static_cast<uint32_t>(g.shape.tile_blocks) * 128u * static_cast<uint32_t>(g.b);
+        float total = 0.f;
+        for (uint32_t r = 0; r <= reps; ++r) {  // the first launch warms up
+            BT_CUDA(cudaMemsetAsync(p.head, 0, sizeof(unsigned int), st));
+            BT_CUDA(cudaEventRecord(e0, st));
+            BT_CUDA(gb::launch_batch_kernel(g.kernel == 1, g.b, p, g.shape.warps, g.grid, st));
+            BT_CUDA(cudaEventRecord(e1, st));
+            BT_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (r) total += ms;
+        }
+        *us = total * 1000.f / static_cast<float>(reps);
+        return SCAN_OK;
+    };
+    const std::vector<scan_batch::Group> groups = bt->groups;
+    std::map<std::pair<int, int>, double> tuned_est;
+    for (size_t gi = 0; gi < groups.size() && status == SCAN_OK; ++gi) {
+        const auto& g = groups[gi];
+        if (!g.ntiles) continue;
+        const int op = g.kernel == 1 ? gb::kOpBatchBR : gb::kOpBatchBF;
+        gb_shape_install(g.b, op, nullptr, 0.f, 0.f);
+        float rule = 0.f;
+        if ((status = time_group(gi, &rule)) != SCAN_OK) break;
+        float best = rule;
+        gb::LaunchShape best_shape{};
+        bool have = false;
+        for (const gb::LaunchShape& c : gb_shape_candidates(g.b, op)) {
+            gb_shape_install(g.b, op, &c, 0.f, 0.f);
+            float us = 0.f;
+            if ((status = time_group(gi, &us)) != SCAN_OK) break;
+            if (us < best) {
+                best = us;
+                best_shape = c;
+                have = true;
+            }
+        }
+        if (status != SCAN_OK) break;
+        gb_shape_install(g.b, op, have ? &best_shape : nullptr, best, rule);
+        tuned_est[std::make_pair(g.kernel, g.b)] = best;
+        sum_rule += rule;
+        sum_best += best;
+        ++tuned;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const scan_status ls = layout(bt);  // the installed shapes; the graph is recorded again
+    if (status != SCAN_OK) return status;
+    if (ls != SCAN_OK) return ls;
+    for (auto& g : bt->groups) {  // the measured times alone schedule the branches
+        const auto it = tuned_est.find(std::make_pair(g.kernel, g.b));
+        if (it != tuned_est.end()) g.est_us = it->second;
+    }
+    if (groups_tuned) *groups_tuned = tuned;
+    if (rule_us) *rule_us = sum_rule;
+    if (tuned_us) *tuned_us = sum_best;
     return SCAN_OK;
 }
 

@@ -1,57 +1,67 @@
-// Instantiates the batched scan kernel for one predicate flavour
-// (GB_BATCH_BRANCHY = 0 or 1, set by the build) and exposes its launcher.
+// Instantiates the batched scan kernel for one predicate flavour and a range
+// of widths (GB_BATCH_BRANCHY = 0 or 1, GB_BLO..GB_BHI, set by the build, one
+// object per range so the ranges compile in parallel) and exposes its launcher.
 #include <atomic>
 
 #include "batch_kernels.cuh"
 
-#ifndef GB_BATCH_BRANCHY
-#error "GB_BATCH_BRANCHY must be defined by the build"
+#if !defined(GB_BATCH_BRANCHY) || !defined(GB_BLO) || !defined(GB_BHI)
+#error "GB_BATCH_BRANCHY, GB_BLO and GB_BHI must be defined by the build"
 #endif
 
+#define GB_CAT3(a, b, c, d) a##b##_##c##_##d
+#define GB_NAME(a, b, c, d) GB_CAT3(a, b, c, d)
 #if GB_BATCH_BRANCHY
-#define GB_BATCH_LAUNCH gb_launch_batch_branchy
+#define GB_BATCH_LAUNCH GB_NAME(gb_launch_batch_br_, GB_BLO, GB_BHI, w)
 #else
-#define GB_BATCH_LAUNCH gb_launch_batch_branchfree
+#define GB_BATCH_LAUNCH GB_NAME(gb_launch_batch_bf_, GB_BLO, GB_BHI, w)
 #endif
 
 namespace {
 
 constexpr bool kBr = GB_BATCH_BRANCHY != 0;
 
-template <int BFIX>
-cudaError_t launch_fixed(const gb::BatchParams& p, int grid, cudaStream_t st)
+template <int BFIX, int WMAX>
+cudaError_t launch_one(const gb::BatchParams& p, int warps, int grid, cudaStream_t st)
 {
     static std::atomic<unsigned long long> configured{0ull};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     const unsigned long long bit = 1ull << (dev & 63);
-    const void* fn = reinterpret_cast<const void*>(gb::k_scan_batch<kBr, BFIX>);
+    const void* fn = reinterpret_cast<const void*>(gb::k_scan_batch<kBr, BFIX, WMAX>);
     if (!(configured.load() & bit)) {
-        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, gb::kBatchSmem);
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, gb::kSmemMax);
         if (e != cudaSuccess) return e;
         configured.fetch_or(bit);
     }
-    gb::k_scan_batch<kBr, BFIX><<<grid, gb::kBatchWarps * 32, gb::kBatchSmem, st>>>(p);
+    const uint32_t smem = gb::batch_smem_bytes(static_cast<uint32_t>(warps), p.stages, p.slot_bytes);
+    gb::k_scan_batch<kBr, BFIX, WMAX><<<grid, warps * 32, smem, st>>>(p);
     return cudaGetLastError();
 }
 
+template <int BFIX>
+cudaError_t launch_fixed(const gb::BatchParams& p, int warps, int grid, cudaStream_t st)
+{
+    if (warps < 1 || warps > 16) return cudaErrorInvalidValue;
+    return warps > 8 ? launch_one<BFIX, 16>(p, warps, grid, st) : launch_one<BFIX, 8>(p, warps, grid, st);
+}
+
 template <int LO, int HI>
-cudaError_t launch_width(int b, const gb::BatchParams& p, int grid, cudaStream_t st)
+cudaError_t launch_width(int b, const gb::BatchParams& p, int warps, int grid, cudaStream_t st)
 {
     if constexpr (LO > HI) {
         return cudaErrorInvalidValue;
     } else {
-        if (b == LO) return launch_fixed<LO>(p, grid, st);
-        return launch_width<LO + 1, HI>(b, p, grid, st);
+        if (b == LO) return launch_fixed<LO>(p, warps, grid, st);
+        return launch_width<LO + 1, HI>(b, p, warps, grid, st);
     }
 }
 
 }  // namespace
 
-// Columns of any width (b = 0) or all of width b (1..32).
-cudaError_t GB_BATCH_LAUNCH(int b, const gb::BatchParams& p, int grid, cudaStream_t st)
+// Columns all of width b (GB_BLO..GB_BHI), CTAs of `warps` warps.
+cudaError_t GB_BATCH_LAUNCH(int b, const gb::BatchParams& p, int warps, int grid, cudaStream_t st)
 {
-    if (b == 0) return launch_fixed<0>(p, grid, st);
-    return launch_width<1, 32>(b, p, grid, st);
+    return launch_width<GB_BLO, GB_BHI>(b, p, warps, grid, st);
 }

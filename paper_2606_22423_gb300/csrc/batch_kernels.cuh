@@ -43,18 +43,28 @@ struct BatchParams {
     unsigned int* head;            // pop counter, zero before the launch
     unsigned long long* results;   // per output slot: count, sum, blocks, 0
     unsigned int* status;
+    uint32_t stages;               // slots per warp (warps per CTA = blockDim.x / 32)
+    uint32_t slot_bytes;           // bytes per slot: the group's largest tile
 };
 
-// 8 warps, each with 2 slots of 12 KB: per tile the batch kernel spends about a
-// third of its issue on bookkeeping (column lookup, keep mask, copy issue),
-// so tiles larger than the scans' 8 KB pay (3 x 8 KB slots: -12% time).
+// Default batch shape: 8 warps, each with 2 slots of 12 KB (per tile the batch
+// kernel spends about a third of its issue on bookkeeping -- column lookup,
+// keep mask, copy issue -- so tiles larger than the scans' 8 KB paid: 3 x 8 KB
+// slots took 12% longer).  The shape is a run-time choice per width group;
+// the autotuner may replace it.
 constexpr int kBatchWarps = 8;
 constexpr int kBatchStages = 2;
 constexpr int kBatchSlot = 12 * 1024;
-constexpr int kBatchSmem = kBatchWarps * kBatchStages * (kBatchSlot + 8 + 16);
+constexpr uint32_t kBatchSlotExtra = 8 + 16;   // a slot's barrier and metadata
 
-// Blocks per batch tile at width b: as many as fill a slot, a multiple of
-// the warp step (4 blocks for b <= 16, else 2), at most 64 (the keep mask).
+__host__ __device__ constexpr uint32_t batch_smem_bytes(uint32_t warps, uint32_t stages, uint32_t slot_bytes)
+{
+    return warps * stages * (slot_bytes + kBatchSlotExtra);
+}
+
+// Default blocks per batch tile at width b: as many as fill a 12 KB slot, a
+// multiple of the warp step (4 blocks for b <= 16, else 2), at most 64 (the
+// keep mask).
 __host__ __device__ constexpr uint32_t batch_tile_blocks(uint32_t b)
 {
     const uint32_t step = b <= 16 ? 4u : 2u;
@@ -97,40 +107,27 @@ __device__ __forceinline__ CountSum batch_consume_body(const unsigned char* slot
     return CountSum{cnt, sum};
 }
 
-template <int B, bool BRANCHY>
-__device__ __noinline__ CountSum batch_consume_b(const unsigned char* slot, const SlotMeta m,
-                                                 const ConsCol& c, int lane)
+// Every column of the launch has width BFIX and its decode is inlined: one
+// width's code per kernel keeps the instruction cache warm (a kernel holding
+// all 32 unrolled decoders stalled on instruction fetch), so a batch runs one
+// such kernel per width group.  WMAX: the largest CTA the instantiation is
+// compiled for (8 or 16 warps).
+template <bool BRANCHY, int BFIX, int WMAX = 8>
+__global__ void __launch_bounds__(WMAX * 32, 1) k_scan_batch(const BatchParams P)
 {
-    return batch_consume_body<B, BRANCHY>(slot, m, c, lane);
-}
-
-template <bool BRANCHY, int LO, int HI>
-__device__ __forceinline__ CountSum batch_consume_range(int b, const unsigned char* slot,
-                                                        const SlotMeta m, const ConsCol& c, int lane)
-{
-    if constexpr (LO > HI) {
-        return CountSum{0, 0};
-    } else {
-        if (b == LO) return batch_consume_b<LO, BRANCHY>(slot, m, c, lane);
-        return batch_consume_range<BRANCHY, LO + 1, HI>(b, slot, m, c, lane);
-    }
-}
-
-// BFIX = 0: any width (switch per tile).  BFIX = b: every column of the
-// launch has width b, and the decode is inlined (one width's code per kernel
-// keeps the instruction cache warm; a batch runs one such kernel per width).
-template <bool BRANCHY, int BFIX>
-__global__ void __launch_bounds__(kBatchWarps * 32, 1) k_scan_batch(const BatchParams P)
-{
+    static_assert(BFIX >= 1 && BFIX <= 32, "batch kernels are width-specialised");
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    unsigned char* slots = smem + static_cast<size_t>(warp) * kBatchStages * kBatchSlot;
-    uint64_t* bars =
-        reinterpret_cast<uint64_t*>(smem + kBatchWarps * kBatchStages * kBatchSlot) + warp * kBatchStages;
-    SlotMeta* meta = reinterpret_cast<SlotMeta*>(smem + kBatchWarps * kBatchStages * (kBatchSlot + 8)) +
-                     warp * kBatchStages;
+    const uint32_t nwarps = blockDim.x >> 5;
+    const int kStages = static_cast<int>(P.stages);
+    const uint32_t kSlot = P.slot_bytes;
+    unsigned char* slots = smem + static_cast<size_t>(warp) * kStages * kSlot;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + static_cast<size_t>(nwarps) * kStages * kSlot) +
+                     warp * kStages;
+    SlotMeta* meta =
+        reinterpret_cast<SlotMeta*>(smem + static_cast<size_t>(nwarps) * kStages * (kSlot + 8)) + warp * kStages;
     if (lane == 0) {
-        for (int s = 0; s < kBatchStages; ++s) mbar_init(&bars[s], 1);
+        for (int s = 0; s < kStages; ++s) mbar_init(&bars[s], 1);
         fence_mbar_init();
     }
     __syncwarp();
@@ -151,7 +148,7 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 1) k_scan_batch(const BatchP
         pc_packed = d->packed;
         pc_zm = d->zonemap;
         pc_n = d->n;
-        pc_b = BFIX > 0 ? static_cast<uint32_t>(BFIX) : d->b;
+        pc_b = static_cast<uint32_t>(BFIX);
         pc_begin = d->tile_begin;
         pc_tb = d->tile_blocks;
         pc_flags = d->flags;
@@ -229,7 +226,7 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 1) k_scan_batch(const BatchP
             if (nk) {
                 fence_proxy_async_smem();
                 mbar_arrive_expect_tx(&bars[s], nk * bb);
-                unsigned char* dst = slots + s * kBatchSlot;
+                unsigned char* dst = slots + s * kSlot;
                 uint64_t rem = keep;
                 uint32_t placed = 0;
                 while (rem) {
@@ -248,7 +245,7 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 1) k_scan_batch(const BatchP
     };
 
     int produced = 0;
-    for (int s = 0; s < kBatchStages; ++s) {
+    for (int s = 0; s < kStages; ++s) {
         if (!produce(s)) break;
         ++produced;
     }
@@ -276,10 +273,9 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 1) k_scan_batch(const BatchP
     };
 
     bool failed = false;
-    int it = 0;
+    int it = 0, s = 0;  // s = it mod stages, kept without a division per tile
 #pragma unroll 1
-    for (; it < produced; ++it) {
-        const int s = it % kBatchStages;
+    for (; it < produced; ++it, s = (s + 1 == kStages) ? 0 : s + 1) {
         const SlotMeta m = meta[s];
         if (static_cast<int>(m.col) != cur) {
             flush();
@@ -288,7 +284,7 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 1) k_scan_batch(const BatchP
             cc.lo = d->lo;
             cc.wm1 = d->wm1;
             cc.tail = static_cast<uint32_t>(d->n & 1023u);
-            cc.b = BFIX > 0 ? static_cast<uint32_t>(BFIX) : d->b;
+            cc.b = static_cast<uint32_t>(BFIX);
             cur_out = d->out;
             cur_base = d->base;
         }
@@ -299,12 +295,7 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 1) k_scan_batch(const BatchP
                 break;
             }
             phase ^= 1u << s;
-            CountSum r;
-            if constexpr (BFIX > 0)
-                r = batch_consume_body<BFIX, BRANCHY>(slots + s * kBatchSlot, m, cc, lane);
-            else
-                r = batch_consume_range<BRANCHY, 1, 32>(static_cast<int>(cc.b), slots + s * kBatchSlot, m, cc,
-                                                        lane);
+            const CountSum r = batch_consume_body<BFIX, BRANCHY>(slots + s * kSlot, m, cc, lane);
             cnt += r.cnt;
             sum += r.sum;
             blocks += m.nk;
@@ -315,8 +306,8 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 1) k_scan_batch(const BatchP
     if (failed) {
         if (lane == 0) atomicOr(P.status, kErrTimeout);
         // let this warp's copies in flight land before shared memory is released
-        for (int j = it; j < produced && j < it + kBatchStages; ++j) {
-            const int s = j % kBatchStages;
+        for (int j = it; j < produced && j < it + kStages; ++j) {
+            const int s = j % kStages;
             if (meta[s].nk) {
                 mbar_wait(&bars[s], (phase >> s) & 1u, kDrainLimitNs);
                 phase ^= 1u << s;
@@ -327,4 +318,43 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 1) k_scan_batch(const BatchP
 }
 
 }  // namespace gb
+
+// One launcher per flavour and range of four widths (separate objects).
+#define GB_DECLARE_BATCH(lo, hi)                                                                                \
+    cudaError_t gb_launch_batch_bf_##lo##_##hi##_w(int b, const gb::BatchParams& p, int warps, int grid,        \
+                                                   cudaStream_t st);                                             \
+    cudaError_t gb_launch_batch_br_##lo##_##hi##_w(int b, const gb::BatchParams& p, int warps, int grid,        \
+                                                   cudaStream_t st);
+GB_DECLARE_BATCH(1, 4)
+GB_DECLARE_BATCH(5, 8)
+GB_DECLARE_BATCH(9, 12)
+GB_DECLARE_BATCH(13, 16)
+GB_DECLARE_BATCH(17, 20)
+GB_DECLARE_BATCH(21, 24)
+GB_DECLARE_BATCH(25, 28)
+GB_DECLARE_BATCH(29, 32)
+#undef GB_DECLARE_BATCH
+
+// The batch kernel of one width group: flavour, width b, CTAs of `warps` warps.
+inline cudaError_t gb_launch_batch(bool branchy, int b, const gb::BatchParams& p, int warps, int grid,
+                                   cudaStream_t st)
+{
+#define GB_RANGE(k, lo, hi)                                                                                       \
+    case k:                                                                                                      \
+        return branchy ? gb_launch_batch_br_##lo##_##hi##_w(b, p, warps, grid, st)                                 \
+                       : gb_launch_batch_bf_##lo##_##hi##_w(b, p, warps, grid, st);
+    switch ((b - 1) / 4) {
+        GB_RANGE(0, 1, 4)
+        GB_RANGE(1, 5, 8)
+        GB_RANGE(2, 9, 12)
+        GB_RANGE(3, 13, 16)
+        GB_RANGE(4, 17, 20)
+        GB_RANGE(5, 21, 24)
+        GB_RANGE(6, 25, 28)
+        GB_RANGE(7, 29, 32)
+    default: return cudaErrorInvalidValue;
+    }
+#undef GB_RANGE
+}
+
 

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <vector>
 
 #include "../../include/gbscan.h"
 
@@ -42,6 +43,11 @@ struct LaunchShape;
 // Launch shape of kernel `op` (gb::OpKind) at width b: the installed tuned
 // shape for the four tunable scan kernels, else the built-in rule.
 gb::LaunchShape gb_shape_for(int b, int op);
+
+// The tuner's candidate shapes for (op, b), and installing one (nullptr: the
+// rule again); false for an illegal shape.
+std::vector<gb::LaunchShape> gb_shape_candidates(int b, int op);
+bool gb_shape_install(int b, int op, const gb::LaunchShape* shape, float tuned_us, float rule_us);
 
 // Enqueues one scan of `c` (what scan_run_async does, with the result written
 // to dev_result); *empty is set when the predicate selects nothing and no

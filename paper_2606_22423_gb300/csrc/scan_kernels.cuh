@@ -1132,6 +1132,8 @@ enum OpKind : int {
     kOpRowBR = 6,
     kOpBytesBF = 7,   // byte-aligned layout, b = 8 or 16 (§3 strategy iii)
     kOpBytesBR = 8,
+    kOpBatchBF = 9,   // batched scans (one width group of a batch); only their shapes
+    kOpBatchBR = 10,  // are kept here, the kernels live with the batch
 };
 
 struct ShapeInfo {

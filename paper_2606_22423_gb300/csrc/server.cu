@@ -31,7 +31,6 @@
 void gb_set_last_error(const char* msg);
 bool gb_column_view(const scan_column* c, const uint32_t** packed, uint64_t* n, uint32_t* b,
                     uint32_t* base, const uint2** zonemap);
-cudaError_t gb_launch_batch_branchfree(int b, const gb::BatchParams& p, int grid, cudaStream_t st);
 
 namespace {
 
@@ -155,7 +154,10 @@ cudaError_t launch_slot(scan_server* sv, Slot& s, const char** step)
         p.head = ctl + gi;
         p.results = s.d_res;
         p.status = ctl + 33;
-        e = gb_launch_batch_branchfree(static_cast<int>(g.b), p, sv->sms, s.stream);
+        // the default batch shape: the tiles were cut by batch_tile_blocks
+        p.stages = gb::kBatchStages;
+        p.slot_bytes = gb::batch_tile_blocks(g.b) * 128u * g.b;
+        e = gb_launch_batch(false, static_cast<int>(g.b), p, gb::kBatchWarps, sv->sms, s.stream);
     }
     if (e == cudaSuccess) {
         // results of the n entries, then the control words (pop counters, status)

@@ -25,12 +25,13 @@
 #include <vector>
 
 #include "internal.h"
+#include "batch_kernels.cuh"
 #include "scan_kernels.cuh"
 
 namespace {
 
-enum Kind : int { kKFullBF = 0, kKFullBR = 1, kKQueueBF = 2, kKQueueBR = 3, kKinds = 4 };
-const char* const kKindName[kKinds] = {"full_bf", "full_br", "queue_bf", "queue_br"};
+enum Kind : int { kKFullBF = 0, kKFullBR = 1, kKQueueBF = 2, kKQueueBR = 3, kKBatchBF = 4, kKBatchBR = 5, kKinds = 6 };
+const char* const kKindName[kKinds] = {"full_bf", "full_br", "queue_bf", "queue_br", "batch_bf", "batch_br"};
 
 struct Entry {
     bool tuned = false;
@@ -48,6 +49,8 @@ int kind_of_op(int op)
     case gb::kOpFullBR: return kKFullBR;
     case gb::kOpQueueBF: return kKQueueBF;
     case gb::kOpQueueBR: return kKQueueBR;
+    case gb::kOpBatchBF: return kKBatchBF;
+    case gb::kOpBatchBR: return kKBatchBR;
     default: return -1;
     }
 }
@@ -66,10 +69,23 @@ int kind_of_strategy(scan_strategy s)
     }
 }
 
-gb::LaunchShape default_shape(int b)
+bool is_batch(int kind) { return kind == kKBatchBF || kind == kKBatchBR; }
+
+gb::LaunchShape default_shape(int kind, int b)
 {
+    if (is_batch(kind))
+        return gb::LaunchShape{gb::kBatchWarps, gb::kBatchStages,
+                               static_cast<int>(gb::batch_tile_blocks(static_cast<uint32_t>(b))), 0};
     const gb::ShapeInfo si = gb::shape_of(b);
     return gb::LaunchShape{si.warps, si.stages, si.tile_blocks, 0};
+}
+
+uint32_t smem_of(int kind, int b, const gb::LaunchShape& s)
+{
+    const uint32_t w = static_cast<uint32_t>(s.warps), st = static_cast<uint32_t>(s.stages);
+    const uint32_t tile = static_cast<uint32_t>(s.tile_blocks) * 128u * static_cast<uint32_t>(b);
+    return is_batch(kind) ? gb::batch_smem_bytes(w, st, tile)
+                          : gb::pipe_smem_bytes(static_cast<uint32_t>(b), w, st, static_cast<uint32_t>(s.tile_blocks));
 }
 
 int step_of(int b) { return b <= 16 ? 4 : 2; }
@@ -77,23 +93,23 @@ int step_of(int b) { return b <= 16 ? 4 : 2; }
 // Legality of a shape for (kind, b); `why` names the first violated rule.
 bool shape_ok(int kind, int b, const gb::LaunchShape& s, const char** why)
 {
-    const bool full = kind == kKFullBF || kind == kKFullBR;
+    const bool wide = kind == kKFullBF || kind == kKFullBR || is_batch(kind);  // up to 16 warps, 64-block tiles
     const int step = step_of(b);
     if (b < 1 || b > 32) return *why = "b must be in 1..32", false;
-    if (s.warps < 1 || s.warps > (full ? 16 : 8))
-        return *why = full ? "full scans take 1..16 warps per CTA" : "queue scans take 1..8 warps per CTA", false;
+    if (s.warps < 1 || s.warps > (wide ? 16 : 8))
+        return *why = wide ? "full and batched scans take 1..16 warps per CTA" : "zone-skip scans take 1..8 warps per CTA",
+               false;
     if (s.stages < 1 || s.stages > 6) return *why = "stages must be in 1..6", false;
     if (s.tile_blocks < step || s.tile_blocks % step != 0)
         return *why = "tile_blocks must be a positive multiple of the warp step (4 blocks for b <= 16, else 2)",
                false;
-    if (s.tile_blocks > (full ? 64 : 32))
-        return *why = full ? "full scans take at most 64 blocks per tile" : "queue scans pop at most 32 blocks",
+    if (s.tile_blocks > (wide ? 64 : 32))
+        return *why = wide ? "full and batched scans take at most 64 blocks per tile" : "zone-skip tiles hold at most 32 blocks",
                false;
     if (s.vote_rows != 0 && s.vote_rows != 1) return *why = "vote_rows must be 0 or 1", false;
     if (s.vote_rows && (kind != kKFullBR || b > 21))
         return *why = "the row vote applies to full branchy scans at b <= 21", false;
-    if (gb::pipe_smem_bytes(static_cast<uint32_t>(b), static_cast<uint32_t>(s.warps), static_cast<uint32_t>(s.stages),
-                            static_cast<uint32_t>(s.tile_blocks)) > static_cast<uint32_t>(gb::kSmemMax))
+    if (smem_of(kind, b, s) > static_cast<uint32_t>(gb::kSmemMax))
         return *why = "the slots do not fit 226 KB of shared memory", false;
     return *why = "", true;
 }
@@ -101,23 +117,28 @@ bool shape_ok(int kind, int b, const gb::LaunchShape& s, const char** why)
 // The tuner's search space for (kind, b): 8/12/16 warps (full scans; queue
 // scans 8), 2..4 stages, tiles of about 2..24 KB in whole warp steps, and for
 // full branchy scans at b <= 21 both vote groups; illegal shapes dropped.
+// Batched scans: 8/12/16 warps, 2 or 3 stages, tiles of about 8..32 KB (their
+// per-tile bookkeeping favours larger tiles).
 std::vector<gb::LaunchShape> candidates(int kind, int b)
 {
-    const bool full = kind == kKFullBF || kind == kKFullBR;
+    const bool full = kind == kKFullBF || kind == kKFullBR || is_batch(kind);
     const int step = step_of(b);
     std::vector<int> warps = full ? std::vector<int>{8, 12, 16} : std::vector<int>{8};
     std::vector<int> tiles;
-    for (int kb : {2, 4, 6, 8, 12, 16, 24}) {
+    const std::vector<int> kbs = is_batch(kind) ? std::vector<int>{8, 12, 16, 24, 32}
+                                                : std::vector<int>{2, 4, 6, 8, 12, 16, 24};
+    for (int kb : kbs) {
         int tb = (kb * 1024 / (128 * b)) / step * step;
         tb = std::max(tb, step);
-        tb = std::min(tb, 32);
+        tb = std::min(tb, is_batch(kind) ? 64 : 32);
         if (std::find(tiles.begin(), tiles.end(), tb) == tiles.end()) tiles.push_back(tb);
     }
     const int votes = (kind == kKFullBR && b <= 21) ? 2 : 1;
+    const std::vector<int> stages = is_batch(kind) ? std::vector<int>{2, 3} : std::vector<int>{2, 3, 4};
     std::vector<gb::LaunchShape> out;
     for (int v = 0; v < votes; ++v)
         for (int w : warps)
-            for (int st : {2, 3, 4})
+            for (int st : stages)
                 for (int tb : tiles) {
                     const gb::LaunchShape s{w, st, tb, v};
                     const char* why = nullptr;
@@ -173,28 +194,52 @@ gb::LaunchShape gb_shape_for(int b, int op)
         std::lock_guard<std::mutex> lock(g_mu);
         const Entry& e = g_table[kind][b];
         if (e.tuned) return e.shape;
+        return default_shape(kind, b);
     }
-    return default_shape(b);
+    return default_shape(kKFullBF, b);
 }
 
-extern "C" {
-
-scan_status scan_shape_get(uint32_t b, scan_strategy strategy, scan_shape* out)
+// Candidate shapes of (op, b) for the batch tuner.
+std::vector<gb::LaunchShape> gb_shape_candidates(int b, int op)
 {
-    gb_set_last_error("");
-    const int kind = kind_of_strategy(strategy);
-    if (!out || kind < 0 || b < 1 || b > 32) return shapes_fail(SCAN_EINVAL, "bad width, strategy or NULL out");
-    const int op = kind == kKFullBF ? gb::kOpFullBF
-                                    : (kind == kKFullBR ? gb::kOpFullBR : (kind == kKQueueBF ? gb::kOpQueueBF : gb::kOpQueueBR));
-    *out = to_abi(gb_shape_for(static_cast<int>(b), op));
+    const int kind = kind_of_op(op);
+    if (kind < 0 || b < 1 || b > 32) return {};
+    return candidates(kind, b);
+}
+
+// Install a shape for (op, b) (nullptr: the rule); false if illegal.
+bool gb_shape_install(int b, int op, const gb::LaunchShape* shape, float tuned_us, float rule_us)
+{
+    const int kind = kind_of_op(op);
+    if (kind < 0 || b < 1 || b > 32) return false;
+    const char* why = nullptr;
+    if (shape && !shape_ok(kind, b, *shape, &why)) return false;
+    std::lock_guard<std::mutex> lock(g_mu);
+    Entry& e = g_table[kind][b];
+    if (!shape) {
+        e = Entry{};
+        return true;
+    }
+    e.tuned = true;
+    e.shape = *shape;
+    e.best_us = tuned_us;
+    e.default_us = rule_us;
+    return true;
+}
+
+namespace {
+scan_status kind_shape_get(int kind, uint32_t b, scan_shape* out)
+{
+    if (!out || kind < 0 || b < 1 || b > 32) return shapes_fail(SCAN_EINVAL, "bad width, kernel or NULL out");
+    std::lock_guard<std::mutex> lock(g_mu);
+    const Entry& e = g_table[kind][b];
+    *out = to_abi(e.tuned ? e.shape : default_shape(kind, static_cast<int>(b)));
     return SCAN_OK;
 }
 
-scan_status scan_shape_set(uint32_t b, scan_strategy strategy, const scan_shape* shape)
+scan_status kind_shape_set(int kind, uint32_t b, const scan_shape* shape)
 {
-    gb_set_last_error("");
-    const int kind = kind_of_strategy(strategy);
-    if (kind < 0 || b < 1 || b > 32) return shapes_fail(SCAN_EINVAL, "bad width or strategy");
+    if (kind < 0 || b < 1 || b > 32) return shapes_fail(SCAN_EINVAL, "bad width or kernel");
     std::lock_guard<std::mutex> lock(g_mu);
     Entry& e = g_table[kind][b];
     if (!shape) {  // back to the built-in rule
@@ -210,17 +255,55 @@ scan_status scan_shape_set(uint32_t b, scan_strategy strategy, const scan_shape*
     return SCAN_OK;
 }
 
-scan_status scan_shape_candidates(uint32_t b, scan_strategy strategy, scan_shape* out, uint32_t capacity,
-                                  uint32_t* count)
+scan_status kind_candidates(int kind, uint32_t b, scan_shape* out, uint32_t capacity, uint32_t* count)
 {
-    gb_set_last_error("");
-    const int kind = kind_of_strategy(strategy);
-    if (!count || kind < 0 || b < 1 || b > 32) return shapes_fail(SCAN_EINVAL, "bad width, strategy or NULL count");
+    if (!count || kind < 0 || b < 1 || b > 32) return shapes_fail(SCAN_EINVAL, "bad width, kernel or NULL count");
     const std::vector<gb::LaunchShape> c = candidates(kind, static_cast<int>(b));
     *count = static_cast<uint32_t>(c.size());
     if (out)
         for (uint32_t i = 0; i < std::min<uint32_t>(capacity, *count); ++i) out[i] = to_abi(c[i]);
     return SCAN_OK;
+}
+}  // namespace
+
+extern "C" {
+
+scan_status scan_batch_shape_get(uint32_t b, int branchy, scan_shape* out)
+{
+    gb_set_last_error("");
+    return kind_shape_get(branchy ? kKBatchBR : kKBatchBF, b, out);
+}
+
+scan_status scan_batch_shape_set(uint32_t b, int branchy, const scan_shape* shape)
+{
+    gb_set_last_error("");
+    return kind_shape_set(branchy ? kKBatchBR : kKBatchBF, b, shape);
+}
+
+scan_status scan_batch_shape_candidates(uint32_t b, int branchy, scan_shape* out, uint32_t capacity,
+                                        uint32_t* count)
+{
+    gb_set_last_error("");
+    return kind_candidates(branchy ? kKBatchBR : kKBatchBF, b, out, capacity, count);
+}
+
+scan_status scan_shape_get(uint32_t b, scan_strategy strategy, scan_shape* out)
+{
+    gb_set_last_error("");
+    return kind_shape_get(kind_of_strategy(strategy), b, out);
+}
+
+scan_status scan_shape_set(uint32_t b, scan_strategy strategy, const scan_shape* shape)
+{
+    gb_set_last_error("");
+    return kind_shape_set(kind_of_strategy(strategy), b, shape);
+}
+
+scan_status scan_shape_candidates(uint32_t b, scan_strategy strategy, scan_shape* out, uint32_t capacity,
+                                  uint32_t* count)
+{
+    gb_set_last_error("");
+    return kind_candidates(kind_of_strategy(strategy), b, out, capacity, count);
 }
 
 scan_status scan_autotune_reset(void)
@@ -331,12 +414,12 @@ scan_status scan_autotune_column(scan_column* col, scan_pred pred, scan_strategy
         Entry& e = g_table[kind][b];
         const bool win = best_us < def_us;
         e.tuned = win;
-        e.shape = win ? cand[best] : default_shape(static_cast<int>(b));
+        e.shape = win ? cand[best] : default_shape(kind, static_cast<int>(b));
         e.best_us = win ? best_us : def_us;
         e.default_us = def_us;
         out->best = to_abi(e.shape);
     }
-    out->rule = to_abi(default_shape(static_cast<int>(b)));
+    out->rule = to_abi(default_shape(kind, static_cast<int>(b)));
     out->best_us = best_us < def_us ? best_us : def_us;
     out->rule_us = def_us;
     out->candidates = static_cast<uint32_t>(cand.size());

@@ -107,6 +107,11 @@ SIGNATURES = {
     "scan_autotune_save": (_st, [ctypes.c_char_p]),
     "scan_autotune_load": (_st, [ctypes.c_char_p]),
     "scan_autotune_reset": (_st, []),
+    "scan_batch_shape_get": (_st, [_u32, ctypes.c_int, ctypes.POINTER(scan_shape)]),
+    "scan_batch_shape_set": (_st, [_u32, ctypes.c_int, ctypes.POINTER(scan_shape)]),
+    "scan_batch_shape_candidates": (_st, [_u32, ctypes.c_int, _vp, _u32, ctypes.POINTER(_u32)]),
+    "scan_batch_autotune": (_st, [_vp, _vp, _u32, _vp, ctypes.POINTER(_u32), ctypes.POINTER(ctypes.c_float),
+                                  ctypes.POINTER(ctypes.c_float)]),
     "scan_selftest_wait_timeout": (_st, [_u64, _vp]),
     "scan_run_packed_noalloc": (_st, [_vp, _u64, _u32, _u32, scan_pred, _st, _vp, _vp, _vp]),
     "scan_batch_create": (_st, [_vp, _u32, _vp, _u32, _vp, ctypes.POINTER(_vp)]),
@@ -262,6 +267,30 @@ def shape_candidates(b: int, strategy="branchfree") -> list:
     _check(load().scan_shape_candidates(b, _strategy(strategy), None, 0, ctypes.byref(count)))
     arr = (scan_shape * max(count.value, 1))()
     _check(load().scan_shape_candidates(b, _strategy(strategy), arr, count.value, ctypes.byref(count)))
+    return [arr[i].as_dict() for i in range(count.value)]
+
+
+def batch_shape_get(b: int, branchy: bool = False) -> dict:
+    """The shape the batched kernel of this flavour uses for width-b groups."""
+    out = scan_shape()
+    _check(load().scan_batch_shape_get(b, int(bool(branchy)), ctypes.byref(out)))
+    return out.as_dict()
+
+
+def batch_shape_set(b: int, branchy: bool = False, shape=None):
+    if shape is None:
+        _check(load().scan_batch_shape_set(b, int(bool(branchy)), None))
+        return
+    sh = shape if isinstance(shape, scan_shape) else scan_shape(shape["warps"], shape["stages"],
+                                                                 shape["tile_blocks"], shape.get("vote_rows", 0))
+    _check(load().scan_batch_shape_set(b, int(bool(branchy)), ctypes.byref(sh)))
+
+
+def batch_shape_candidates(b: int, branchy: bool = False) -> list:
+    count = _u32()
+    _check(load().scan_batch_shape_candidates(b, int(bool(branchy)), None, 0, ctypes.byref(count)))
+    arr = (scan_shape * max(count.value, 1))()
+    _check(load().scan_batch_shape_candidates(b, int(bool(branchy)), arr, count.value, ctypes.byref(count)))
     return [arr[i].as_dict() for i in range(count.value)]
 
 
@@ -453,6 +482,14 @@ class Batch:
         out = (scan_result * max(n, 1))() if host else None
         _check(load().scan_batch_exec(self._h, pr, _stream(stream), out if host else None, _ptr(dev_out)))
         return [out[i] for i in range(n)] if host else None
+
+    def autotune(self, preds, reps: int = 3, stream=None) -> dict:
+        """Tune every width group's kernel on these predicates (scan_batch_autotune)."""
+        pr = preds if isinstance(preds, ctypes.Array) else self.pred_array(preds)
+        groups, rule, tuned = _u32(), ctypes.c_float(), ctypes.c_float()
+        _check(load().scan_batch_autotune(self._h, pr, reps, _stream(stream), ctypes.byref(groups),
+                                          ctypes.byref(rule), ctypes.byref(tuned)))
+        return {"groups": int(groups.value), "rule_us": float(rule.value), "tuned_us": float(tuned.value)}
 
     def close(self):
         if self._h is not None and self._h.value:

@@ -141,3 +141,66 @@ def test_full_size_batch_4096_columns_against_the_oracle():
     for c in cols:
         c.close()
     torch.cuda.empty_cache()
+
+
+def _width_columns(seed, n):
+    """Two columns per width b = 1..32 (uniform; sorted with 1% displaced), n values each."""
+    cols, vals = [], []
+    for b in range(1, 33):
+        for k, v in enumerate([synth.uniform_values(synth.seed_for(61, b, seed), n, b),
+                               synth.clustered_values(synth.seed_for(61, b, seed + 1), n, b, 0.01)]):
+            c = gbscan.Column.from_host(v, b)
+            c.zonemap_build()
+            cols.append(c)
+            vals.append(v)
+    return cols, vals
+
+
+def test_every_batch_candidate_shape_matches_the_oracle():
+    """Every shape the batch tuner may install, for both flavours, with and
+    without zone skipping: results equal the oracle's (all candidates of every
+    width are run, the i-th candidate of every width in the same batch)."""
+    gbscan.autotune_reset()
+    n = 150_000 + 77                      # more than two 64-block tiles, ragged tail
+    cols, vals = _width_columns(1, n)
+    rng = np.random.default_rng(7)
+    preds = [synth.pick_range(int(rng.integers(1 << 30)), c.b, float(synth.log_uniform(rng, 1e-3, 1.0)))
+             for c in cols]
+    want = [oracle.scan_values(v, lo, hi) for v, (lo, hi) in zip(vals, preds)]
+    for branchy in (False, True):
+        cands = {b: gbscan.batch_shape_candidates(b, branchy) for b in range(1, 33)}
+        strategies = [("branchy" if branchy else "branchfree") if i % 2 == 0 else ("zone_br" if branchy else "zone_bf")
+                      for i in range(len(cols))]
+        for ci in range(max(len(c) for c in cands.values())):
+            for b in range(1, 33):
+                gbscan.batch_shape_set(b, branchy, cands[b][ci % len(cands[b])])
+            bt = gbscan.Batch(cols, strategies)
+            got = bt.run(preds)
+            bad = [i for i in range(len(cols)) if got[i].pair() != want[i]]
+            assert not bad, (branchy, ci, [(cols[i].b, strategies[i]) for i in bad[:4]])
+            bt.close()
+    gbscan.autotune_reset()
+    for c in cols:
+        c.close()
+
+
+def test_batch_autotune_installs_group_shapes_and_stays_exact():
+    gbscan.autotune_reset()
+    cols, vals = _width_columns(3, 1 << 18)
+    strategies = ["branchfree" if i % 2 == 0 else "zone_br" for i in range(len(cols))]
+    rng = np.random.default_rng(8)
+    preds = [synth.pick_range(int(rng.integers(1 << 30)), c.b, float(synth.log_uniform(rng, 1e-4, 1.0)))
+             for c in cols]
+    bt = gbscan.Batch(cols, strategies)
+    res = bt.autotune(preds, reps=2)
+    assert res["groups"] == 64 and 0 < res["tuned_us"] <= res["rule_us"]
+    for b in (1, 16, 32):
+        assert gbscan.batch_shape_get(b, False) in gbscan.batch_shape_candidates(b, False) + \
+            [dict(warps=8, stages=2, tile_blocks=gbscan.batch_shape_get(b, False)["tile_blocks"], vote_rows=0)]
+    for rep in range(2):
+        got = bt.run(preds)
+        assert [r.pair() for r in got] == [oracle.scan_values(v, lo, hi) for v, (lo, hi) in zip(vals, preds)]
+    bt.close()
+    gbscan.autotune_reset()
+    for c in cols:
+        c.close()

@@ -140,3 +140,35 @@ def test_cache_validation_is_all_or_nothing(tmp_path):
     assert gbscan.shape_get(5, "branchfree")["warps"] == 8                # replaced, not merged
     gbscan.autotune_reset()
     assert os.path.exists(good)
+
+
+def test_batch_shapes_candidates_rules_and_cache(tmp_path):
+    gbscan.autotune_reset()
+    for br in (False, True):
+        for b in range(1, 33):
+            rule = gbscan.batch_shape_get(b, br)
+            step = 4 if b <= 16 else 2
+            assert rule["warps"] == 8 and rule["stages"] == 2 and rule["vote_rows"] == 0
+            assert rule["tile_blocks"] % step == 0 and rule["tile_blocks"] * 128 * b <= 12 * 1024
+            cands = gbscan.batch_shape_candidates(b, br)
+            assert cands and max(c["warps"] for c in cands) > 8
+            for c in cands:
+                assert c["vote_rows"] == 0 and c["tile_blocks"] % step == 0 and c["tile_blocks"] <= 64
+                assert c["warps"] * c["stages"] * (c["tile_blocks"] * 128 * b + 24) <= 226 * 1024
+    with pytest.raises(gbscan.ScanError) as e:
+        gbscan.batch_shape_set(9, False, dict(warps=8, stages=2, tile_blocks=4, vote_rows=1))
+    assert "row vote" in str(e.value)
+    with pytest.raises(gbscan.ScanError) as e:
+        gbscan.batch_shape_set(32, True, dict(warps=16, stages=3, tile_blocks=4))
+    assert "226 KB" in str(e.value)
+    s = dict(warps=16, stages=2, tile_blocks=4, vote_rows=0)
+    gbscan.batch_shape_set(9, True, s)
+    assert gbscan.batch_shape_get(9, True) == s and gbscan.batch_shape_get(9, False)["warps"] == 8
+    path = str(tmp_path / "b.txt")
+    gbscan.autotune_save(path)
+    assert "batch_br 9 16 2 4 0" in open(path).read()
+    gbscan.autotune_reset()
+    assert gbscan.batch_shape_get(9, True)["warps"] == 8
+    gbscan.autotune_load(path)
+    assert gbscan.batch_shape_get(9, True) == s
+    gbscan.autotune_reset()
