@@ -1223,7 +1223,7 @@ def run_batched(args, dev, stream, gbscan, beta_gbs, t_dec_gvals):
         batch_tune = {"plan": "law", "groups": r_["groups"], "seconds": round(tune_s, 1),
                       "ms_graph_rule": round(ms_rule, 4), "ms_graph_tuned": round(ms_tuned, 4),
                       "gain": round(ms_rule / ms_tuned, 4),
-                      "groups_alone_us_rule": round(r_["rule_us"], 1), "groups_alone_us_tuned": round(r_["tuned_us"], 1),
+                      "tuner_replay_us_rule": round(r_["rule_us"], 1), "tuner_replay_us_tuned": round(r_["tuned_us"], 1),
                       "shapes": {f"b{b}": [gbscan.batch_shape_get(b, False)[k]
                                            for k in ("warps", "stages", "tile_blocks")] for b in range(1, 33)}}
         shapes_path = os.path.join(os.path.dirname(os.path.abspath(args.detail or "bench_detail.json")),

@@ -308,14 +308,19 @@ scan_status scan_batch_exec(scan_batch *batch, const scan_pred *preds, void *str
                             scan_result *host_out, scan_result *dev_out);
 
 /* Autotune the batch's width-group kernels on these predicates (no paper
- * counterpart; the shapes never change a result): for every width group,
- * time its kernel alone (`reps` launches on `stream`, after a warm-up) with
- * the rule and with every candidate shape of its flavour and width, and
- * install the fastest in the process-wide batch shape table; the batch is then
- * laid out again with the installed shapes.  Blocking.  *groups_tuned gets the
- * number of width groups, *rule_us and *tuned_us (may be NULL) the sums of the
- * groups' times alone before and after -- the groups overlap in a replay, so
- * these bound rather than predict its time.  Results are unaffected. */
+ * counterpart; the shapes never change a result).  Two phases: every width
+ * group's kernel is timed alone (`reps` launches on `stream` after a warm-up)
+ * with the rule and every candidate shape of its flavour and width, keeping
+ * the three fastest; then, largest group first, each finalist is tried in the
+ * whole graph replay (median of 2 * reps + 1) with the other groups' shapes
+ * fixed, and kept only if the replay gets faster by more than 0.3% -- the
+ * groups overlap on the graph's branches, so a group's time alone does not
+ * predict the replay.  The result is kept only if it beats the rule's replay
+ * measured again, else every group goes back to the rule.  Installed in the
+ * process-wide batch shape table; the batch is laid out again.  Blocking.
+ * *groups_tuned gets the number of groups whose shape changed, *rule_us and
+ * *tuned_us (may be NULL) the replay times with the rule and the installed
+ * shapes.  Results are unaffected. */
 scan_status scan_batch_autotune(scan_batch *batch, const scan_pred *preds, uint32_t reps, void *stream,
                                 uint32_t *groups_tuned, float *rule_us, float *tuned_us);
 

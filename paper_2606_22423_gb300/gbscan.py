@@ -484,7 +484,8 @@ class Batch:
         return [out[i] for i in range(n)] if host else None
 
     def autotune(self, preds, reps: int = 3, stream=None) -> dict:
-        """Tune every width group's kernel on these predicates (scan_batch_autotune)."""
+        """Tune the width groups' kernels on these predicates (scan_batch_autotune): groups
+        changed, and the graph replay's time with the rule and the installed shapes."""
         pr = preds if isinstance(preds, ctypes.Array) else self.pred_array(preds)
         groups, rule, tuned = _u32(), ctypes.c_float(), ctypes.c_float()
         _check(load().scan_batch_autotune(self._h, pr, reps, _stream(stream), ctypes.byref(groups),
