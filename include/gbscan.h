@@ -161,17 +161,28 @@ scan_status scan_encode_device_layout(const uint32_t *dev_values, uint64_t n, ui
 
 /* -------------------------------------------------------------- columns */
 
-/* Encode host values on the host, allocate device memory and upload.
- * Returns after the upload is complete. */
+/* A column in the paper's problem statement (§2: N values stored in b bits
+ * each), encoded in §3's transposed layout with a frame of reference: encode
+ * host_values (n of them, caller owned, read only) on the host, allocate the
+ * column's device memory (owned by the column) and upload.  Returns after the
+ * upload is complete.  SCAN_EINVAL as scan_encode_host (bad b or base, n >
+ * 2^31, NULL pointers, a value outside [base, base + 2^b)); SCAN_ENOMEM if an
+ * allocation fails. */
 scan_status scan_column_create(const uint32_t *host_values, uint64_t n, uint32_t b, uint32_t base,
                                void *stream, scan_column **out);
 
-/* Allocate a column and encode device-resident values on the GPU. */
+/* As scan_column_create for values already in device memory (dev_values, n
+ * of them, caller owned): §3's encoding runs on the GPU into memory the
+ * column owns.  Synchronises `stream` to report out-of-range values as
+ * SCAN_EINVAL. */
 scan_status scan_column_create_device(const uint32_t *dev_values, uint64_t n, uint32_t b,
                                       uint32_t base, void *stream, scan_column **out);
 
-/* Wrap an already packed device buffer (scan_packed_words(n, b) words,
- * 16-byte aligned) without copying; the caller keeps ownership. */
+/* Wrap a device buffer already packed in §3's layout (scan_packed_words(n, b)
+ * words, 16-byte aligned) without copying; the caller keeps ownership and
+ * the buffer must outlive the column.  The column allocates only its small
+ * workspace.  SCAN_EINVAL for bad b or base, n > 2^31, a NULL (n > 0) or
+ * misaligned buffer. */
 scan_status scan_column_create_packed(const uint32_t *dev_packed, uint64_t n, uint32_t b,
                                       uint32_t base, void *stream, scan_column **out);
 
@@ -191,7 +202,9 @@ scan_status scan_column_get_layout(const scan_column *col, scan_layout *layout);
  * Any zone map built before is marked stale and must be rebuilt. */
 scan_status scan_column_upload_packed(scan_column *col, const uint32_t *host_packed, void *stream);
 
-/* Free the column and what it owns.  Synchronises the device first. */
+/* Free the column and the device memory it owns (not a borrowed packed
+ * buffer).  Synchronises the device first, so no scan of the column is still
+ * running.  NULL is accepted and ignored. */
 scan_status scan_column_destroy(scan_column *col);
 
 /* Shape and device pointers of a column (any out pointer may be NULL).
@@ -214,17 +227,22 @@ scan_status scan_column_blocksums(const scan_column *col, const uint64_t **dev_b
 
 /* ---------------------------------------------------------------- scans */
 
-/* Fused decode -> filter -> aggregate.  Enqueues the kernels on `stream`,
- * waits for them and writes the result to host memory.  The result is the
- * same, bit for bit, for every strategy.  Zone-skip strategies need a built
- * zone map (SCAN_EINVAL otherwise).  SCAN_ETIMEOUT if a bounded device wait
- * gave up (the result is then not valid). */
+/* The paper's operation (§2 problem statement; §3 "fused
+ * decode->filter->aggregate in one pass"): COUNT and exact int64 SUM of the
+ * column's decoded values v with pred.lo <= v < pred.hi.  Enqueues the
+ * kernels on `stream`, waits for them and writes the result to host_out
+ * (caller owned).  The result is the same, bit for bit, for every strategy;
+ * blocks_scanned says how many 1024-value blocks were read.  Zone-skip
+ * strategies need a built zone map (SCAN_EINVAL otherwise).  SCAN_ETIMEOUT if
+ * a bounded device wait gave up (the result is then not valid; the column's
+ * state is reset and it stays usable). */
 scan_status scan_run(scan_column *col, scan_pred pred, scan_strategy strategy, void *stream,
                      scan_result *host_out);
 
-/* As scan_run, but writes the 32-byte result to device memory (dev_out,
- * caller-owned, 8-byte aligned; SCAN_EINVAL otherwise, checked before any
- * CUDA call) and returns without waiting.  Check scan_column_status
+/* The same operation as scan_run (§2, §3), asynchronous: writes the 32-byte
+ * result to device memory (dev_out, caller-owned, 8-byte aligned; SCAN_EINVAL
+ * otherwise, checked before any CUDA call) and returns without waiting.  An
+ * empty predicate writes zeros without a kernel.  Check scan_column_status
  * afterwards for device errors. */
 scan_status scan_run_async(scan_column *col, scan_pred pred, scan_strategy strategy, void *stream,
                            scan_result *dev_out);
