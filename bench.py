@@ -673,6 +673,9 @@ def summarise(plain, probes, zone, select, layouts, conj, batched, serving, beta
                            all(v["exact"] for v in pl.values())]
         if batched.get("autotune"):
             out["batch_tune_gain"] = batched["autotune"]["gain"]
+        if batched.get("planner_vs_law"):
+            pv = batched["planner_vs_law"]
+            out["planner_vs_law"] = [pv["min"], pv["median"], pv["max"]]
     if serving:
         ld = {x["load"]: x for x in serving["loads"]}
         if 0.9 in ld:
@@ -1203,8 +1206,21 @@ def run_batched(args, dev, stream, gbscan, beta_gbs, t_dec_gvals):
     mlp_law_plan = plmod.choose(net_r, feats, stream, margin=margin_r, prior=P_batch)
     net.close()
     net_r.close()
+    # the law as fallback and judge: three networks (three initial seeds, the same
+    # labels) each move a column off the law's plan only where they predict a
+    # gain above their own RMS error
+    L_batch = plmod.law_log_times(cols, feats, beta_gbs, t_dec_gvals, stream)
+    guarded = {}
+    for seed in (5, 6, 7):
+        net_g = gbscan.Planner(4, seed=seed)
+        hist_g = plmod.train(net_g, X, T, steps=1500, lr=3e-3, stream=stream)
+        m_g = float(np.sqrt(max(hist_g[-1], 0.0)))
+        guarded[f"guarded_s{seed}"] = (plmod.choose_guarded(net_g, feats, law_plan, L_batch, m_g, stream,
+                                                            box=plmod.feature_box(X)), m_g)
+        net_g.close()
     plans = {"branchfree": ["branchfree"] * ncols, "law": law_plan, "planned_mlp": mlp_plan,
              "law_calibrated": calib_plan, "planned_mlp_law_prior": mlp_law_plan}
+    plans.update({k: v[0] for k, v in guarded.items()})
     res_b = torch.zeros((ncols, 4), dtype=torch.int64, device=dev)
     parr = gbscan.Batch.pred_array(preds)      # marshalled once, outside the timed region
     # launch shapes of the batched kernels: each width group of the law plan (its
@@ -1245,7 +1261,13 @@ def run_batched(args, dev, stream, gbscan, beta_gbs, t_dec_gvals):
         bt.close()
     for c in cols:
         c.close()
+    sp = [out["law"]["ms"] / out[k]["ms"] for k in guarded]
+    planner_vs_law = {"plans": list(guarded), "speedup_over_law": [round(x, 4) for x in sp],
+                      "median": round(statistics.median(sp), 4), "min": round(min(sp), 4), "max": round(max(sp), 4),
+                      "columns_moved_off_the_law": [sum(a != b for a, b in zip(v[0], law_plan)) for v in guarded.values()],
+                      "margins_log_time": [round(v[1], 4) for v in guarded.values()]}
     return {"workload": BATCH_WORKLOAD, "ncols": ncols, "values": total_values, "packed_bytes": total_bytes,
+            "planner_vs_law": planner_vs_law,
             "ms_per_column_graph": round(ms_graph, 4), "ms_per_column_loop": round(ms_loop, 4),
             "per_column_launches": ncols, "plans": out, "autotune": batch_tune,
             "planner": {"training_columns": TRAIN_COLS, "training_lengths": "log-uniform in [2^22, 2^27] values",

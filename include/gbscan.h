@@ -436,6 +436,21 @@ scan_status scan_planner_choose_margin(scan_planner *planner, const float *dev_x
 scan_status scan_planner_choose_prior(scan_planner *planner, const float *dev_x, uint32_t rows,
                                       float margin, const float *dev_prior, int32_t *dev_choice,
                                       void *stream);
+
+/* The law as the fallback and the judge (spec planner; the paper's law,
+ * §2 Eq. 2, gives dev_fallback and dev_fallback_log_ms, e.g. from
+ * scan_batch_law_choose and scan_batch_law_times): per row, the fallback's
+ * strategy, unless (1) the row's features lie inside host_feature_box (8
+ * floats: the 4 lower bounds, then the 4 upper bounds of the features the
+ * network was trained on; NULL = no box) and (2) the strategy the network
+ * predicts fastest among the available ones (fallback log time < 29) is
+ * predicted faster than the fallback's by more than `margin` in log time.
+ * With margin = the network's RMS error on its labels, noise alone rarely
+ * moves a column off the law's plan, and the box keeps the network from
+ * extrapolating.  dev_x rows x 4, dev_fallback_log_ms rows x S, int32 out. */
+scan_status scan_planner_choose_guarded(scan_planner *planner, const float *dev_x, uint32_t rows, float margin,
+                                        const int32_t *dev_fallback, const float *dev_fallback_log_ms,
+                                        const float *host_feature_box, int32_t *dev_choice, void *stream);
 /* Binary checkpoint: 16-byte header (magic, version 1, S, count) + floats. */
 scan_status scan_planner_save(const scan_planner *planner, const char *path);
 scan_status scan_planner_load(scan_planner *planner, const char *path);

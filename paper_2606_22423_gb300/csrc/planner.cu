@@ -156,6 +156,44 @@ __global__ void k_argmin_rows_prior(const float* __restrict__ y, const float* __
     out[n] = best;
 }
 
+// Bounds of the features the network was trained on: outside them its
+// predictions are extrapolations, and the fallback decides.
+struct FeatureBox {
+    float lo[kIn], hi[kIn];
+    int on;
+};
+
+// The fallback's choice unless the network is confident and on familiar
+// ground: per row whose features lie inside the box, the strategy the network
+// predicts fastest among those available (the fallback's log time below
+// kUnavailable) replaces the fallback's choice only if its predicted log time
+// is lower than the network's prediction for the fallback's choice by more
+// than `margin`.
+constexpr float kUnavailable = 29.0f;
+__global__ void k_choose_guarded(const float* __restrict__ x, const float* __restrict__ y,
+                                 const int32_t* __restrict__ fallback, const float* __restrict__ fallback_log_ms,
+                                 int rows, int S, float margin, FeatureBox box, int32_t* __restrict__ out)
+{
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= rows) return;
+    const int f = fallback[n];
+    if (box.on) {
+        for (int k = 0; k < kIn; ++k) {
+            const float v = x[n * kIn + k];
+            if (v < box.lo[k] || v > box.hi[k]) {
+                out[n] = f;
+                return;
+            }
+        }
+    }
+    int best = f;
+    for (int s = 0; s < S; ++s) {
+        if (fallback_log_ms[n * S + s] >= kUnavailable) continue;
+        if (y[n * S + s] < y[n * S + best]) best = s;
+    }
+    out[n] = (y[n * S + best] < y[n * S + f] - margin) ? best : f;
+}
+
 inline unsigned blocks_for(long long n, int t = 256) { return static_cast<unsigned>((n + t - 1) / t); }
 
 // splitmix64 (Steele, Lea, Flood 2014) for the deterministic initial weights
@@ -405,6 +443,30 @@ scan_status scan_planner_choose_prior(scan_planner* pl, const float* dev_x, uint
     if (s != SCAN_OK || !rows) return s;
     k_argmin_rows_prior<<<blocks_for(rows), 256, 0, static_cast<cudaStream_t>(stream)>>>(
         a.y, dev_prior, static_cast<int>(rows), pl->S, margin, dev_choice);
+    PL_CUDA(cudaGetLastError());
+    return SCAN_OK;
+}
+
+scan_status scan_planner_choose_guarded(scan_planner* pl, const float* dev_x, uint32_t rows, float margin,
+                                        const int32_t* dev_fallback, const float* dev_fallback_log_ms,
+                                        const float* host_feature_box, int32_t* dev_choice, void* stream)
+{
+    if (!pl || (rows && (!dev_x || !dev_fallback || !dev_fallback_log_ms || !dev_choice)))
+        return pfail(SCAN_EINVAL, "null pointer");
+    if (!(margin >= 0.0f)) return pfail(SCAN_EINVAL, "margin must be >= 0");
+    scan_status s = ensure_ws(pl, rows ? rows : 1);
+    if (s != SCAN_OK) return s;
+    const Acts a = acts(pl);
+    s = scan_planner_forward(pl, dev_x, rows, a.y, stream);
+    if (s != SCAN_OK || !rows) return s;
+    FeatureBox box{};
+    box.on = host_feature_box != nullptr;
+    for (int k = 0; k < kIn && box.on; ++k) {
+        box.lo[k] = host_feature_box[k];
+        box.hi[k] = host_feature_box[kIn + k];
+    }
+    k_choose_guarded<<<blocks_for(rows), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        dev_x, a.y, dev_fallback, dev_fallback_log_ms, static_cast<int>(rows), pl->S, margin, box, dev_choice);
     PL_CUDA(cudaGetLastError());
     return SCAN_OK;
 }

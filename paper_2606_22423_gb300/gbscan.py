@@ -133,6 +133,7 @@ SIGNATURES = {
     "scan_planner_choose": (_st, [_vp, _vp, _u32, _vp, _vp]),
     "scan_planner_choose_margin": (_st, [_vp, _vp, _u32, ctypes.c_float, _vp, _vp]),
     "scan_planner_choose_prior": (_st, [_vp, _vp, _u32, ctypes.c_float, _vp, _vp, _vp]),
+    "scan_planner_choose_guarded": (_st, [_vp, _vp, _u32, ctypes.c_float, _vp, _vp, _vp, _vp, _vp]),
     "scan_planner_save": (_st, [_vp, ctypes.c_char_p]),
     "scan_planner_load": (_st, [_vp, ctypes.c_char_p]),
     "scan_server_create": (_st, [_vp, _u32, _u32, _u64, _u32, ctypes.POINTER(_vp)]),
@@ -593,6 +594,16 @@ class Planner:
                                                      _stream(stream)))
         else:
             _check(load().scan_planner_choose(self._h, _ptr(dev_x), rows, _ptr(dev_choice), _stream(stream)))
+
+    def choose_guarded(self, dev_x, rows, margin, dev_fallback, dev_fallback_log_ms, dev_choice, stream=None,
+                       feature_box=None):
+        """The fallback's choice unless the row lies inside feature_box (lo[4] + hi[4],
+        or None) and the network predicts another available strategy faster by more
+        than `margin` (scan_planner_choose_guarded)."""
+        box = None if feature_box is None else (ctypes.c_float * 8)(*[float(v) for v in feature_box])
+        _check(load().scan_planner_choose_guarded(self._h, _ptr(dev_x), rows, float(margin), _ptr(dev_fallback),
+                                                  _ptr(dev_fallback_log_ms), box, _ptr(dev_choice),
+                                                  _stream(stream)))
 
     def save(self, path):
         _check(load().scan_planner_save(self._h, path.encode()))

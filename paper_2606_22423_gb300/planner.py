@@ -103,6 +103,33 @@ def choose(planner, X, stream=None, margin=0.0, prior=None):
     return [STRATEGIES[i] for i in out.cpu().tolist()]
 
 
+def feature_box(X_train):
+    """Per-feature bounds (lo[4] + hi[4]) of the training features."""
+    lo = X_train.min(dim=0).values.cpu().tolist()
+    hi = X_train.max(dim=0).values.cpu().tolist()
+    return lo + hi
+
+
+def choose_guarded(planner, X, law_plan, law_log_ms, margin, stream=None, box=None):
+    """The law's plan, except for columns inside the training features' box
+    where the network predicts another available strategy faster by more than
+    `margin` (its own RMS error): the law is the fallback and the judge, the
+    network refines it where it is sure and on familiar ground."""
+    torch = _torch()
+    rows = X.shape[0]
+    fb = torch.tensor([STRATEGIES.index(s) for s in law_plan], dtype=torch.int32, device="cuda")
+    out = torch.zeros(rows, dtype=torch.int32, device="cuda")
+    # only the law's (branch-free) flavour is open to the network: in a batch a
+    # column moved to the branchy flavour adds a width-group kernel to the
+    # replay, a fixed cost the one-entry-batch labels never see (and branchy
+    # never beats branch-free for counts on this GPU)
+    avail = law_log_ms.clone()
+    avail[:, [STRATEGIES.index("branchy"), STRATEGIES.index("zone_br")]] = 30.0
+    planner.choose_guarded(X, rows, margin, fb, avail, out, stream, feature_box=box)
+    torch.cuda.synchronize()
+    return [STRATEGIES[i] for i in out.cpu().tolist()]
+
+
 def law_log_times(columns, X, beta_gbs, t_dec_gvals, stream=None):
     """The bandwidth law's predicted log milliseconds per (column, strategy), on the GPU."""
     torch = _torch()

@@ -235,3 +235,71 @@ def test_trained_planner_beats_the_fixed_full_scan_on_clustered_low_selectivity_
     for c in cols + tcols:
         c.close()
     pl.close()
+
+
+def test_guarded_planner_against_the_law_on_a_held_out_batch():
+    """What the trained network gains over the method without it, the law: on a
+    held-out batch drawn from the batched-workload recipe (512 columns, 2^28
+    values in total), the law's plan and the law-guarded network's plan (the
+    law's strategy unless the column lies inside the training features' range
+    and the network predicts a gain above its own RMS error)
+    give identical, oracle-exact results, and the guarded plan never takes more
+    than 3% longer than the law's (medians of interleaved graph replays).  The
+    gain, positive or not, is printed."""
+    import math
+
+    from paper_2606_22423_gb300 import planner as plmod
+
+    s = torch.cuda.Stream()
+    tcols, tpreds = plmod.training_columns(seed=2, count=80, n_lo=1 << 20, n_hi=1 << 25, stream=s)
+    X, T = plmod.collect(tcols, tpreds, s, reps=3)
+    for c in tcols:
+        c.close()
+    pl = gbscan.Planner(4, seed=5)
+    hist = plmod.train(pl, X, T, steps=1000, lr=3e-3)
+    margin = math.sqrt(max(hist[-1], 0.0))
+    spec = synth.batch_spec(synth.seed_for(41), ncols=512, total=1 << 28)
+    cols, preds, raws = [], [], []
+    with torch.cuda.stream(s):
+        for i, (n, b, p, sigma) in enumerate(spec):
+            v = (synth.uniform_values_device(synth.seed_for(41, i), n, b) if p is None
+                 else synth.clustered_values_device(synth.seed_for(41, i), n, b, p))
+            c = gbscan.Column.from_device(v, n, b, stream=s)
+            c.zonemap_build(s)
+            cols.append(c)
+            raws.append(v.cpu().numpy().view(np.uint32) if i % 8 == 0 else None)
+            preds.append(synth.pick_range(synth.seed_for(41, i, 1), b, sigma))
+    torch.cuda.synchronize()
+    feats = plmod.features(cols, preds)
+    beta, tdec = 7000.0, [4.3, 2.9, 4.3, 2.9]
+    probe = gbscan.Batch(cols)
+    law = plmod.choose_law(probe, feats, beta, tdec)
+    probe.close()
+    L = plmod.law_log_times(cols, feats, beta, tdec)
+    guarded = plmod.choose_guarded(pl, feats, law, L, margin, box=plmod.feature_box(X))
+    pl.close()
+    moved = sum(a != g for a, g in zip(law, guarded))
+    b_law, b_g = gbscan.Batch(cols, law), gbscan.Batch(cols, guarded)
+    r_law, r_g = [r.pair() for r in b_law.run(preds)], [r.pair() for r in b_g.run(preds)]
+    assert r_law == r_g                                            # a plan never changes a result
+    for i in range(0, len(cols), 8):                               # and those results are the oracle's
+        assert r_g[i] == oracle.scan_values(raws[i], *preds[i]), i
+    out = torch.zeros((len(cols), 4), dtype=torch.int64, device="cuda")
+    parr = gbscan.Batch.pred_array(preds)
+    ts = {"law": [], "guarded": []}
+    for _ in range(9):                                             # interleaved replays
+        for name, bt in (("law", b_law), ("guarded", b_g)):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            bt.run(parr, stream=s, dev_out=out, host=False)
+            e1.record(s)
+            e1.synchronize()
+            ts[name].append(e0.elapsed_time(e1))
+    t_law, t_g = sorted(ts["law"])[4], sorted(ts["guarded"])[4]
+    print(f"guarded planner vs law: {t_law / t_g:.4f}x ({moved} of {len(cols)} columns moved, "
+          f"margin {margin:.3f}; law {t_law:.4f} ms, guarded {t_g:.4f} ms)")
+    assert t_g <= 1.03 * t_law, (t_g, t_law, moved)
+    b_law.close()
+    b_g.close()
+    for c in cols:
+        c.close()
