@@ -1010,7 +1010,11 @@ def run_probes(args, dev, stream, gbscan, beta_read, law):
     per_b = {}
     for b in WIDTHS:
         shape = gbscan.scan_launch_shape(b)
-        n2 = 6 * shape["ctas"] * shape["warps_per_cta"] * shape["blocks_per_tile"] * 1024
+        round_values = shape["ctas"] * shape["warps_per_cta"] * shape["blocks_per_tile"] * 1024
+        # an even number of whole tile rounds (at least 6), as many as fit 64 MiB packed:
+        # L2-resident, and long enough that t(N) - t(N/2) is well above the timing noise
+        rounds = max(6, 2 * int((64 << 20) // (2 * round_values * b / 8)))
+        n2 = rounds * round_values
         n1 = n2 // 2
         with torch.cuda.stream(stream):
             v = synth.uniform_values_device(synth.seed_for(20, b), n2, b, device=dev)
@@ -1019,8 +1023,8 @@ def run_probes(args, dev, stream, gbscan, beta_read, law):
         torch.cuda.synchronize()
         part = gbscan.Column.from_packed(col.dev_packed, n1, b, stream=stream)
         lo, hi = synth.pick_range(synth.seed_for(20, b, 1), b, 0.1)
-        t2 = _graph_time(lambda: col.run_async(lo, hi, res, "branchfree", stream), stream)
-        t1 = _graph_time(lambda: part.run_async(lo, hi, res, "branchfree", stream), stream)
+        t2 = _graph_time(lambda: col.run_async(lo, hi, res, "branchfree", stream), stream, reps=40, trials=7)
+        t1 = _graph_time(lambda: part.run_async(lo, hi, res, "branchfree", stream), stream, reps=40, trials=7)
         col.status(stream)
         part.close()
         col.close()
@@ -1043,9 +1047,9 @@ def run_probes(args, dev, stream, gbscan, beta_read, law):
                "beta_read_gbs": round(beta_read, 1), "above_beta_read": bool(min(wide) > beta_read)}
     return {"triad": {"workload": "STREAM triad a = b + 3c over 2^28 float32 (3 GiB), best of 10",
                       "gbs": round(best, 1), "beta_read_gbs": round(beta_read, 1), "exact": triad_ok},
-            "decode_resident": {"workload": "branch-free scan of an L2-resident column per b (N = six rounds of "
-                                            "tiles over all warps, <= 60 MB packed), sigma = 0.1, slope between N "
-                                            "and N/2 values, CUDA graphs of 20 launches",
+            "decode_resident": {"workload": "branch-free scan of an L2-resident column per b (N = whole rounds of "
+                                            "tiles over all warps, <= 64 MiB packed), sigma = 0.1, slope between N "
+                                            "and N/2 values, CUDA graphs of 40 launches, median of 7",
                                 "per_b": per_b, "t_dec_median_below_ridge_gvals": med,
                                 "t_dec_fitted_gvals": fitted, "b_star_fitted": ridge,
                                 "resident_over_fitted": round(med / fitted, 3) if med and fitted else None,

@@ -571,14 +571,17 @@ scan_status scan_launch_shape(uint32_t b, uint32_t *sms, uint32_t *ctas, uint32_
  * SM of `warps` warps; each warp streams tiles of `tile_blocks` 1024-value
  * blocks through `stages` shared-memory slots (the zone-skip kernels pop
  * `tile_blocks` candidate blocks at a time); vote_rows = 1 makes the branchy
- * kernel vote once per row of a thread's lanes instead of once per value.
- * Legal shapes: full scans 1..16 warps, zone-skip scans 1..8; 1..6 stages;
- * tile_blocks a positive multiple of the warp step (4 for b <= 16, else 2),
- * at most 64 (full) or 32 (zone skip); vote_rows only for SCAN_BRANCHY at
- * b <= 21; warps * stages * (tile_blocks * 128 * b + 12) <= 226 KB (the
- * kernels keep up to 1 KB of static shared memory). */
+ * kernel vote once per row of a thread's lanes instead of once per value;
+ * vec_lanes is how many lanes a thread reads as one vector per row: 0 (the
+ * width's default: 4 for b <= 16, else 2) or 2 for full scans at b = 9..16,
+ * whose smaller warp step lets 16 warps fit.  Legal shapes: full scans 1..16
+ * warps, zone-skip scans 1..8; 1..6 stages; tile_blocks a positive multiple of
+ * the warp step (vec_lanes blocks), at most 64 (full) or 32 (zone skip);
+ * vote_rows only for SCAN_BRANCHY at b <= 21; warps * stages * (tile_blocks
+ * * 128 * b + 12) <= 226 KB (the kernels keep up to 1 KB of static shared
+ * memory). */
 typedef struct {
-    uint32_t warps, stages, tile_blocks, vote_rows;
+    uint32_t warps, stages, tile_blocks, vote_rows, vec_lanes;
 } scan_shape;
 
 /* Tuning outcome for one (strategy, b): the installed shape and the rule's,
@@ -615,9 +618,10 @@ scan_status scan_shape_candidates(uint32_t b, scan_strategy strategy, scan_shape
  * scans; on failure the previous shape stays installed. */
 scan_status scan_autotune_column(scan_column *col, scan_pred pred, scan_strategy strategy, uint32_t reps,
                                  void *stream, scan_tune_result *out);
-/* Write the tuned shapes to `path`, a versioned text file: a "gbscan-shapes 1"
+/* Write the tuned shapes to `path`, a versioned text file: a "gbscan-shapes 2"
  * line, a "device <name> <SMs>" line, then one "kind b warps stages
- * tile_blocks vote_rows tuned_us rule_us" line per tuned (kernel, b). */
+ * tile_blocks vote_rows vec_lanes tuned_us rule_us" line per tuned (kernel,
+ * b). */
 scan_status scan_autotune_save(const char *path);
 /* Replace the installed shapes with those of a file written by
  * scan_autotune_save.  All or nothing: a wrong magic or version, a file tuned
@@ -632,7 +636,7 @@ scan_status scan_autotune_reset(void);
  * group of a batch launches one kernel with its width's shape (tile_blocks =
  * blocks per batch tile; vote_rows must be 0).  Legal: 1..16 warps, 1..6
  * stages, tile_blocks a multiple of the warp step and at most 64, warps *
- * stages * (tile_blocks * 128 * b + 24) <= 226 KB.  branchy = 0 for the
+ * stages * (tile_blocks * 128 * b + 24) <= 226 KB, vec_lanes = 0.  branchy = 0 for the
  * branch-free kernel, 1 for the branchy one.  They are saved and loaded with
  * the others ("batch_bf" / "batch_br" lines).  A batch picks up shape
  * changes when it is created, when its strategies are set, or when it is

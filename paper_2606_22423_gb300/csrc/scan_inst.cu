@@ -47,6 +47,15 @@ cudaError_t launch_one(const ScanParams& p, const LaunchShape& sh, int grid, cud
 template <int B, bool BRANCHY>
 cudaError_t launch_full(const ScanParams& p, const LaunchShape& sh, int grid, cudaStream_t st)
 {
+    if constexpr (B >= 9 && B <= 16) {  // the 2-lane geometry: 16-warp bound only
+        if (sh.vec_lanes == 2) {
+            if constexpr (BRANCHY) {
+                if (sh.vote_rows) return launch_one<B, k_scan_full<B, true, kLayLanes, 16, true, 2>>(p, sh, grid, st);
+            }
+            return launch_one<B, k_scan_full<B, BRANCHY, kLayLanes, 16, false, 2>>(p, sh, grid, st);
+        }
+    }
+    if (sh.vec_lanes != 0 && sh.vec_lanes != default_lpt(B)) return cudaErrorInvalidValue;
     const bool w16 = sh.warps > 8;
     if constexpr (BRANCHY && B <= 21) {
         if (sh.vote_rows)

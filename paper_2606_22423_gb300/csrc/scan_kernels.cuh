@@ -54,12 +54,17 @@ template <int B>
 struct Shape;
 
 // ------------------------------------------------------------- geometry
-// Threads per block: a thread owns kLpt consecutive lanes and reads them as one
-// vector per row (16 bytes for b <= 16, 8 bytes above, where four blocks per
-// warp step would not fit an 8 KB slot); a warp step covers kLpt blocks.
-template <int B>
+// Threads per block: a thread owns LPT consecutive lanes and reads them as one
+// vector per row; a warp step covers LPT blocks.  By default 4 lanes (16 bytes
+// per row) for b <= 16 and 2 (8 bytes) above, where four blocks per warp step
+// would not fit an 8 KB slot.  The 2-lane geometry at b = 9..16 is a tuned
+// variant: its smaller warp step lets 16 warps fit in shared memory there.
+__host__ __device__ constexpr int default_lpt(int b) { return b <= 16 ? 4 : 2; }
+
+template <int B, int LPT = default_lpt(B)>
 struct Geo {
-    static constexpr int kLpt = B <= 16 ? 4 : 2;
+    static_assert(LPT == 2 || LPT == 4, "2 or 4 lanes per thread");
+    static constexpr int kLpt = LPT;
     static constexpr int kTpb = 32 / kLpt;
     using Vec = typename std::conditional<kLpt == 4, uint4, uint2>::type;
 };
@@ -131,8 +136,8 @@ __device__ __forceinline__ uint32_t lane_word(const uint4& v, int k)
 __device__ __forceinline__ uint32_t lane_word(const uint2& v, int k) { return k == 0 ? v.x : v.y; }
 
 // Code of row r for the thread's lane k (r, k compile-time after unrolling).
-template <int B>
-__device__ __forceinline__ uint32_t code_of(const typename Geo<B>::Vec (&W)[B], int r, int k)
+template <int B, int LPT = default_lpt(B)>
+__device__ __forceinline__ uint32_t code_of(const typename Geo<B, LPT>::Vec (&W)[B], int r, int k)
 {
     const int bit = r * B;
     const int w0 = bit >> 5;
@@ -148,11 +153,11 @@ __device__ __forceinline__ uint32_t code_of(const typename Geo<B>::Vec (&W)[B], 
     }
 }
 
-template <int B>
-__device__ __forceinline__ void load_rows(typename Geo<B>::Vec (&W)[B], const typename Geo<B>::Vec* rows)
+template <int B, int LPT = default_lpt(B)>
+__device__ __forceinline__ void load_rows(typename Geo<B, LPT>::Vec (&W)[B], const typename Geo<B, LPT>::Vec* rows)
 {
 #pragma unroll
-    for (int w = 0; w < B; ++w) W[w] = rows[w * Geo<B>::kTpb];
+    for (int w = 0; w < B; ++w) W[w] = rows[w * Geo<B, LPT>::kTpb];
 }
 
 // -------------------------------------------------------------- aggregate
@@ -213,8 +218,8 @@ __device__ __forceinline__ bool top_field(int r)
 }
 
 // Code of row r, lane k, plus L.add (r, k compile-time after unrolling).
-template <int B>
-__device__ __forceinline__ uint32_t field_add(const typename Geo<B>::Vec (&W)[B], int r, int k,
+template <int B, int LPT = default_lpt(B)>
+__device__ __forceinline__ uint32_t field_add(const typename Geo<B, LPT>::Vec (&W)[B], int r, int k,
                                               const Lanes& L)
 {
     const int bit = r * B;
@@ -357,14 +362,14 @@ __device__ __forceinline__ void acc2(uint32_t& c, uint64_t& s, uint32_t ui, cons
 // values over kLpt blocks): one vote per kLpt values, but all kLpt tests must
 // be held across the vote.  Which form is faster depends on the width and on
 // how many warps share an SM (the autotuner picks per width).
-template <int B, bool BRANCHY, bool ROWVOTE = false>
-__device__ __forceinline__ void agg_block(const typename Geo<B>::Vec* rows, const Lanes& L,
+template <int B, bool BRANCHY, bool ROWVOTE = false, int LPT = default_lpt(B)>
+__device__ __forceinline__ void agg_block(const typename Geo<B, LPT>::Vec* rows, const Lanes& L,
                                           uint64_t& cnt, uint64_t& sum)
 {
     constexpr int kMode = B <= 21 ? 0 : (B <= 27 ? 1 : 2);
-    constexpr int kLpt = Geo<B>::kLpt;
-    typename Geo<B>::Vec W[B];
-    load_rows<B>(W, rows);
+    constexpr int kLpt = LPT;
+    typename Geo<B, LPT>::Vec W[B];
+    load_rows<B, LPT>(W, rows);
     uint32_t a[kLpt] = {};
     uint32_t c = 0u;
     uint64_t s64 = 0u;
@@ -378,7 +383,7 @@ __device__ __forceinline__ void agg_block(const typename Geo<B>::Vec* rows, cons
             bool any = false;
 #pragma unroll
             for (int k = 0; k < kLpt; ++k) {
-                ui[k] = field_add<B>(W, r, k, L);
+                ui[k] = field_add<B, LPT>(W, r, k, L);
                 const uint32_t t = top ? ui[k] - L.loi : imad(ui[k], L.one, L.negloi);
                 m[k] = t <= L.wm1;
                 any = any || m[k];
@@ -396,7 +401,7 @@ __device__ __forceinline__ void agg_block(const typename Geo<B>::Vec* rows, cons
         } else {
 #pragma unroll
             for (int k = 0; k < kLpt; ++k) {
-                const uint32_t ui = field_add<B>(W, r, k, L);
+                const uint32_t ui = field_add<B, LPT>(W, r, k, L);
                 if constexpr (BRANCHY) {
                     // subtract and add on the FMA pipe unless the extraction already used it
                     const bool top = top_field<B>(r);
@@ -458,21 +463,21 @@ __device__ __forceinline__ void agg_block(const typename Geo<B>::Vec* rows, cons
 // Same with a validity mask: value (r, lane kLpt*q + k) counts iff `ok` and
 // its index in the block, 32r + kLpt*q + k, is below `limit`.  Used for the
 // last partial warp step of a tile and for the zero-padded tail block.
-template <int B>
-__device__ __forceinline__ void agg_block_masked(const typename Geo<B>::Vec* rows, uint32_t lo,
+template <int B, int LPT = default_lpt(B)>
+__device__ __forceinline__ void agg_block_masked(const typename Geo<B, LPT>::Vec* rows, uint32_t lo,
                                                  uint32_t wm1, uint64_t& cnt, uint64_t& sum, bool ok,
                                                  uint32_t limit, int q)
 {
-    constexpr int kLpt = Geo<B>::kLpt;
-    typename Geo<B>::Vec W[B];
-    load_rows<B>(W, rows);
+    constexpr int kLpt = LPT;
+    typename Geo<B, LPT>::Vec W[B];
+    load_rows<B, LPT>(W, rows);
     uint32_t c = 0u;
     uint64_t s = 0u;
 #pragma unroll
     for (int r = 0; r < 32; ++r) {
 #pragma unroll
         for (int k = 0; k < kLpt; ++k) {
-            const uint32_t u = code_of<B>(W, r, k);
+            const uint32_t u = code_of<B, LPT>(W, r, k);
             const uint32_t j = 32u * r + static_cast<uint32_t>(kLpt * q + k);
             if (ok && j < limit && (u - lo) <= wm1) {
                 c += 1u;
@@ -507,10 +512,10 @@ __device__ __forceinline__ void minmax_block(const typename Geo<B>::Vec* rows, u
     }
 }
 
-template <int B>
-__device__ __forceinline__ const typename Geo<B>::Vec* block_rows(const unsigned char* blk, int q)
+template <int B, int LPT = default_lpt(B)>
+__device__ __forceinline__ const typename Geo<B, LPT>::Vec* block_rows(const unsigned char* blk, int q)
 {
-    return reinterpret_cast<const typename Geo<B>::Vec*>(blk) + q;
+    return reinterpret_cast<const typename Geo<B, LPT>::Vec*>(blk) + q;
 }
 
 // ------------------------------------------- the other layouts (§3 i, iii)
@@ -680,22 +685,22 @@ __device__ __forceinline__ void scan_tail_layout(const ScanParams& p, int lane, 
 }
 
 // All `nb` blocks of a staged tile (blocks are contiguous in the slot).
-template <int B, bool BRANCHY, bool ROWVOTE = false>
+template <int B, bool BRANCHY, bool ROWVOTE = false, int LPT = default_lpt(B)>
 __device__ __forceinline__ void scan_tile(const unsigned char* tile, uint32_t nb, int lane,
                                           const Lanes& L, uint32_t lo, uint32_t wm1, uint64_t& cnt,
                                           uint64_t& sum)
 {
     constexpr uint32_t kBB = 128u * B;
-    constexpr uint32_t kStep = Geo<B>::kLpt;          // blocks per warp step
-    const int q = lane % Geo<B>::kTpb;
-    const uint32_t sub = static_cast<uint32_t>(lane / Geo<B>::kTpb);
+    constexpr uint32_t kStep = Geo<B, LPT>::kLpt;          // blocks per warp step
+    const int q = lane % Geo<B, LPT>::kTpb;
+    const uint32_t sub = static_cast<uint32_t>(lane / Geo<B, LPT>::kTpb);
     uint32_t g = 0;
 #pragma unroll 1
     for (; g + kStep <= nb; g += kStep)
-        agg_block<B, BRANCHY, ROWVOTE>(block_rows<B>(tile + (g + sub) * kBB, q), L, cnt, sum);
+        agg_block<B, BRANCHY, ROWVOTE, LPT>(block_rows<B, LPT>(tile + (g + sub) * kBB, q), L, cnt, sum);
     if (g < nb) {
         const bool ok = g + sub < nb;
-        agg_block_masked<B>(block_rows<B>(tile + (ok ? g + sub : g) * kBB, q), lo, wm1, cnt, sum, ok,
+        agg_block_masked<B, LPT>(block_rows<B, LPT>(tile + (ok ? g + sub : g) * kBB, q), lo, wm1, cnt, sum, ok,
                             1024u, q);
     }
 }
@@ -781,16 +786,16 @@ __device__ __forceinline__ void grid_finish(const ScanParams& p, uint64_t cnt, u
 }
 
 // Tail block (n mod 1024 values, zero padded) read straight from global memory.
-template <int B>
+template <int B, int LPT = default_lpt(B)>
 __device__ __forceinline__ void scan_tail(const ScanParams& p, int lane, uint64_t& cnt,
                                           uint64_t& sum)
 {
     const uint64_t tb = p.n >> 10;
     const uint32_t rem = static_cast<uint32_t>(p.n & 1023u);
-    const int q = lane % Geo<B>::kTpb;
-    const bool ok = lane < Geo<B>::kTpb;
-    const auto* rows = block_rows<B>(reinterpret_cast<const unsigned char*>(p.packed + tb * 32u * B), q);
-    agg_block_masked<B>(rows, p.lo, p.wm1, cnt, sum, ok, rem, q);
+    const int q = lane % Geo<B, LPT>::kTpb;
+    const bool ok = lane < Geo<B, LPT>::kTpb;
+    const auto* rows = block_rows<B, LPT>(reinterpret_cast<const unsigned char*>(p.packed + tb * 32u * B), q);
+    agg_block_masked<B, LPT>(rows, p.lo, p.wm1, cnt, sum, ok, rem, q);
 }
 
 // ------------------------------------------------------------- full scan
@@ -798,7 +803,7 @@ __device__ __forceinline__ void scan_tail(const ScanParams& p, int lane, uint64_
 // to warp t mod (all warps), numbered warp-major, through the warp's ring of
 // slots.  Returns false when a bounded wait gave up (the warp's copies in
 // flight have landed by then and the status bit is set).
-template <int B, bool BRANCHY, int LAY, bool ROWVOTE>
+template <int B, bool BRANCHY, int LAY, bool ROWVOTE, int LPT = default_lpt(B)>
 __device__ __forceinline__ bool walk_static(const ScanParams& p, const Pipe& P, int warp, int lane, int nwarps,
                                             uint64_t& cnt, uint64_t& sum)
 {
@@ -839,7 +844,7 @@ __device__ __forceinline__ bool walk_static(const ScanParams& p, const Pipe& P, 
         const uint64_t left = full_blocks - t * P.tb;
         const uint32_t nb = left < P.tb ? static_cast<uint32_t>(left) : P.tb;
         if constexpr (LAY == kLayLanes)
-            scan_tile<B, BRANCHY, ROWVOTE>(P.slots + s * P.tile_bytes, nb, lane, L, p.lo, p.wm1, cnt, sum);
+            scan_tile<B, BRANCHY, ROWVOTE, LPT>(P.slots + s * P.tile_bytes, nb, lane, L, p.lo, p.wm1, cnt, sum);
         else
             scan_tile_layout<B, BRANCHY, LAY>(P.slots + s * P.tile_bytes, nb, lane, L, cnt, sum);
         __syncwarp();
@@ -868,8 +873,8 @@ __device__ __forceinline__ bool walk_static(const ScanParams& p, const Pipe& P, 
 
 // WMAX: the largest CTA the instantiation is compiled for (launch bound; 8
 // warps leave up to 255 registers per thread, 16 warps 128).  ROWVOTE: the
-// branchy vote group (see agg_block).
-template <int B, bool BRANCHY, int LAY = kLayLanes, int WMAX = 8, bool ROWVOTE = false>
+// branchy vote group (see agg_block).  LPT: lanes per thread (see Geo).
+template <int B, bool BRANCHY, int LAY = kLayLanes, int WMAX = 8, bool ROWVOTE = false, int LPT = default_lpt(B)>
 __global__ void __launch_bounds__(WMAX * 32, 1) k_scan_full(const ScanParams p)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -882,11 +887,11 @@ __global__ void __launch_bounds__(WMAX * 32, 1) k_scan_full(const ScanParams p)
     }
     __syncwarp();
     uint64_t cnt = 0, sum = 0;
-    walk_static<B, BRANCHY, LAY, ROWVOTE>(p, P, warp, lane, nwarps, cnt, sum);
+    walk_static<B, BRANCHY, LAY, ROWVOTE, LPT>(p, P, warp, lane, nwarps, cnt, sum);
     const uint64_t gw = static_cast<uint64_t>(warp) * gridDim.x + blockIdx.x;
     if ((p.n & 1023u) && gw == static_cast<uint64_t>(gridDim.x) * nwarps - 1) {
         if constexpr (LAY == kLayLanes)
-            scan_tail<B>(p, lane, cnt, sum);
+            scan_tail<B, LPT>(p, lane, cnt, sum);
         else
             scan_tail_layout<B, LAY>(p, lane, cnt, sum);
     }
@@ -1141,12 +1146,14 @@ struct ShapeInfo {
 };
 
 // A runtime launch shape: one CTA per SM of `warps` warps, each with `stages`
-// slots of `tile_blocks` blocks (the queue kernels pop that many candidates
-// at a time); vote_rows picks the branchy vote group (full branchy scans at
-// b <= 21 only).  Full scans take 8..16 warps (above 8 the 16-warp-bound
+// slots of `tile_blocks` blocks (the zone-skip kernels take that many
+// candidates per tile); vote_rows picks the branchy vote group (full branchy
+// scans at b <= 21 only); vec_lanes = 2 the 2-lane geometry (full scans at
+// b = 9..16, compiled with the 16-warp bound).  Full scans take 8..16 warps (above 8 the 16-warp-bound
 // instantiation, <= 128 registers per thread); every other kernel 1..8.
 struct LaunchShape {
     int warps, stages, tile_blocks, vote_rows;
+    int vec_lanes;  // lanes per thread and row (4 or 2; 0 = the width's default); full scans only
 };
 
 template <int LO, int HI>

@@ -75,9 +75,9 @@ gb::LaunchShape default_shape(int kind, int b)
 {
     if (is_batch(kind))
         return gb::LaunchShape{gb::kBatchWarps, gb::kBatchStages,
-                               static_cast<int>(gb::batch_tile_blocks(static_cast<uint32_t>(b))), 0};
+                               static_cast<int>(gb::batch_tile_blocks(static_cast<uint32_t>(b))), 0, 0};
     const gb::ShapeInfo si = gb::shape_of(b);
-    return gb::LaunchShape{si.warps, si.stages, si.tile_blocks, 0};
+    return gb::LaunchShape{si.warps, si.stages, si.tile_blocks, 0, 0};
 }
 
 uint32_t smem_of(int kind, int b, const gb::LaunchShape& s)
@@ -88,20 +88,24 @@ uint32_t smem_of(int kind, int b, const gb::LaunchShape& s)
                           : gb::pipe_smem_bytes(static_cast<uint32_t>(b), w, st, static_cast<uint32_t>(s.tile_blocks));
 }
 
-int step_of(int b) { return b <= 16 ? 4 : 2; }
+int step_of(int b, int vec_lanes = 0) { return vec_lanes ? vec_lanes : gb::default_lpt(b); }
 
 // Legality of a shape for (kind, b); `why` names the first violated rule.
 bool shape_ok(int kind, int b, const gb::LaunchShape& s, const char** why)
 {
     const bool wide = kind == kKFullBF || kind == kKFullBR || is_batch(kind);  // up to 16 warps, 64-block tiles
-    const int step = step_of(b);
     if (b < 1 || b > 32) return *why = "b must be in 1..32", false;
+    if (s.vec_lanes != 0 && s.vec_lanes != gb::default_lpt(b) &&
+        !(s.vec_lanes == 2 && b >= 9 && b <= 16 && (kind == kKFullBF || kind == kKFullBR)))
+        return *why = "vec_lanes is 0, the width's default, or 2 for full scans at b = 9..16", false;
+    const int step = step_of(b, s.vec_lanes);
     if (s.warps < 1 || s.warps > (wide ? 16 : 8))
         return *why = wide ? "full and batched scans take 1..16 warps per CTA" : "zone-skip scans take 1..8 warps per CTA",
                false;
     if (s.stages < 1 || s.stages > 6) return *why = "stages must be in 1..6", false;
     if (s.tile_blocks < step || s.tile_blocks % step != 0)
-        return *why = "tile_blocks must be a positive multiple of the warp step (4 blocks for b <= 16, else 2)",
+        return *why = "tile_blocks must be a positive multiple of the warp step (vec_lanes blocks; by default 4 for "
+                      "b <= 16, else 2)",
                false;
     if (s.tile_blocks > (wide ? 64 : 32))
         return *why = wide ? "full and batched scans take at most 64 blocks per tile" : "zone-skip tiles hold at most 32 blocks",
@@ -122,28 +126,32 @@ bool shape_ok(int kind, int b, const gb::LaunchShape& s, const char** why)
 std::vector<gb::LaunchShape> candidates(int kind, int b)
 {
     const bool full = kind == kKFullBF || kind == kKFullBR || is_batch(kind);
-    const int step = step_of(b);
+    std::vector<int> geos{0};
+    if ((kind == kKFullBF || kind == kKFullBR) && b >= 9 && b <= 16) geos.push_back(2);
     std::vector<int> warps = full ? std::vector<int>{8, 12, 16} : std::vector<int>{8};
-    std::vector<int> tiles;
     const std::vector<int> kbs = is_batch(kind) ? std::vector<int>{8, 12, 16, 24, 32}
                                                 : std::vector<int>{2, 4, 6, 8, 12, 16, 24};
-    for (int kb : kbs) {
-        int tb = (kb * 1024 / (128 * b)) / step * step;
-        tb = std::max(tb, step);
-        tb = std::min(tb, is_batch(kind) ? 64 : 32);
-        if (std::find(tiles.begin(), tiles.end(), tb) == tiles.end()) tiles.push_back(tb);
-    }
     const int votes = (kind == kKFullBR && b <= 21) ? 2 : 1;
     const std::vector<int> stages = is_batch(kind) ? std::vector<int>{2, 3} : std::vector<int>{2, 3, 4};
     std::vector<gb::LaunchShape> out;
-    for (int v = 0; v < votes; ++v)
-        for (int w : warps)
-            for (int st : stages)
-                for (int tb : tiles) {
-                    const gb::LaunchShape s{w, st, tb, v};
-                    const char* why = nullptr;
-                    if (shape_ok(kind, b, s, &why)) out.push_back(s);
-                }
+    for (int geo : geos) {
+        const int step = step_of(b, geo);
+        std::vector<int> tiles;
+        for (int kb : kbs) {
+            int tb = (kb * 1024 / (128 * b)) / step * step;
+            tb = std::max(tb, step);
+            tb = std::min(tb, is_batch(kind) ? 64 : 32);
+            if (std::find(tiles.begin(), tiles.end(), tb) == tiles.end()) tiles.push_back(tb);
+        }
+        for (int v = 0; v < votes; ++v)
+            for (int w : (geo == 2 ? std::vector<int>{12, 16} : warps))
+                for (int st : stages)
+                    for (int tb : tiles) {
+                        const gb::LaunchShape s{w, st, tb, v, geo};
+                        const char* why = nullptr;
+                        if (shape_ok(kind, b, s, &why)) out.push_back(s);
+                    }
+    }
     return out;
 }
 
@@ -156,13 +164,14 @@ scan_status shapes_fail(scan_status s, const std::string& msg)
 gb::LaunchShape from_abi(const scan_shape& s)
 {
     return gb::LaunchShape{static_cast<int>(s.warps), static_cast<int>(s.stages), static_cast<int>(s.tile_blocks),
-                           static_cast<int>(s.vote_rows)};
+                           static_cast<int>(s.vote_rows), static_cast<int>(s.vec_lanes)};
 }
 
 scan_shape to_abi(const gb::LaunchShape& s)
 {
     return scan_shape{static_cast<uint32_t>(s.warps), static_cast<uint32_t>(s.stages),
-                      static_cast<uint32_t>(s.tile_blocks), static_cast<uint32_t>(s.vote_rows)};
+                      static_cast<uint32_t>(s.tile_blocks), static_cast<uint32_t>(s.vote_rows),
+                      static_cast<uint32_t>(s.vec_lanes)};
 }
 
 // The device a cache file belongs to: its name (blanks replaced) and SM
@@ -182,7 +191,7 @@ std::string device_identity()
 }
 
 constexpr const char* kMagic = "gbscan-shapes";
-constexpr int kVersion = 1;
+constexpr int kVersion = 2;  // 2: vec_lanes column
 
 }  // namespace
 
@@ -432,7 +441,7 @@ scan_status scan_autotune_save(const char* path)
     if (!path) return shapes_fail(SCAN_EINVAL, "path is NULL");
     std::string text = std::string(kMagic) + " " + std::to_string(kVersion) + "\n";
     text += "device " + device_identity() + "\n";
-    text += "# kind b warps stages tile_blocks vote_rows tuned_us rule_us\n";
+    text += "# kind b warps stages tile_blocks vote_rows vec_lanes tuned_us rule_us\n";
     {
         std::lock_guard<std::mutex> lock(g_mu);
         for (int k = 0; k < kKinds; ++k)
@@ -440,8 +449,9 @@ scan_status scan_autotune_save(const char* path)
                 const Entry& e = g_table[k][b];
                 if (!e.tuned) continue;
                 char line[160];
-                std::snprintf(line, sizeof line, "%s %d %d %d %d %d %.3f %.3f\n", kKindName[k], b, e.shape.warps,
-                              e.shape.stages, e.shape.tile_blocks, e.shape.vote_rows, e.best_us, e.default_us);
+                std::snprintf(line, sizeof line, "%s %d %d %d %d %d %d %.3f %.3f\n", kKindName[k], b, e.shape.warps,
+                              e.shape.stages, e.shape.tile_blocks, e.shape.vote_rows, e.shape.vec_lanes, e.best_us,
+                              e.default_us);
                 text += line;
             }
     }
@@ -478,7 +488,8 @@ scan_status scan_autotune_load(const char* path)
     if (lines.empty() || std::sscanf(lines[0].c_str(), "%31s %d", magic, &version) != 2 ||
         std::strcmp(magic, kMagic) != 0)
         return bad(0, "not a gbscan shape cache");
-    if (version != kVersion) return bad(0, "version " + std::to_string(version) + " (this library reads 1)");
+    if (version != kVersion)
+        return bad(0, "version " + std::to_string(version) + " (this library reads " + std::to_string(kVersion) + ")");
     if (lines.size() < 2 || lines[1].rfind("device ", 0) != 0) return bad(1, "missing the device line");
     const std::string want = device_identity();
     if (lines[1].substr(7) != want)
@@ -488,16 +499,17 @@ scan_status scan_autotune_load(const char* path)
         const std::string& s = lines[i];
         if (s.empty() || s[0] == '#') continue;
         char kname[32];
-        int b, w, st, tb, v, used = 0;
+        int b, w, st, tb, v, vl, used = 0;
         float tu, ru;
-        if (std::sscanf(s.c_str(), "%31s %d %d %d %d %d %f %f%n", kname, &b, &w, &st, &tb, &v, &tu, &ru, &used) != 8 ||
+        if (std::sscanf(s.c_str(), "%31s %d %d %d %d %d %d %f %f%n", kname, &b, &w, &st, &tb, &v, &vl, &tu, &ru,
+                        &used) != 9 ||
             s.find_first_not_of(" \t", static_cast<size_t>(used)) != std::string::npos)
-            return bad(i, "expected: kind b warps stages tile_blocks vote_rows tuned_us rule_us");
+            return bad(i, "expected: kind b warps stages tile_blocks vote_rows vec_lanes tuned_us rule_us");
         int kind = -1;
         for (int k = 0; k < kKinds; ++k)
             if (std::strcmp(kname, kKindName[k]) == 0) kind = k;
         if (kind < 0) return bad(i, std::string("unknown kernel kind '") + kname + "'");
-        const gb::LaunchShape shape{w, st, tb, v};
+        const gb::LaunchShape shape{w, st, tb, v, vl};
         const char* why = nullptr;
         if (!shape_ok(kind, b, shape, &why)) return bad(i, why);
         if (fresh[kind][b].tuned) return bad(i, "duplicate entry");

@@ -41,11 +41,18 @@ class scan_pred(ctypes.Structure):
 
 class scan_shape(ctypes.Structure):
     _fields_ = [("warps", ctypes.c_uint32), ("stages", ctypes.c_uint32), ("tile_blocks", ctypes.c_uint32),
-                ("vote_rows", ctypes.c_uint32)]
+                ("vote_rows", ctypes.c_uint32), ("vec_lanes", ctypes.c_uint32)]
 
     def as_dict(self):
         return {"warps": int(self.warps), "stages": int(self.stages), "tile_blocks": int(self.tile_blocks),
-                "vote_rows": int(self.vote_rows)}
+                "vote_rows": int(self.vote_rows), "vec_lanes": int(self.vec_lanes)}
+
+
+def _shape(shape) -> "scan_shape":
+    if isinstance(shape, scan_shape):
+        return shape
+    return scan_shape(shape["warps"], shape["stages"], shape["tile_blocks"], shape.get("vote_rows", 0),
+                      shape.get("vec_lanes", 0))
 
 
 class scan_tune_result(ctypes.Structure):
@@ -257,9 +264,7 @@ def shape_set(b: int, strategy="branchfree", shape=None):
     if shape is None:
         _check(load().scan_shape_set(b, _strategy(strategy), None))
         return
-    sh = shape if isinstance(shape, scan_shape) else scan_shape(shape["warps"], shape["stages"],
-                                                                 shape["tile_blocks"], shape.get("vote_rows", 0))
-    _check(load().scan_shape_set(b, _strategy(strategy), ctypes.byref(sh)))
+    _check(load().scan_shape_set(b, _strategy(strategy), ctypes.byref(_shape(shape))))
 
 
 def shape_candidates(b: int, strategy="branchfree") -> list:
@@ -282,9 +287,7 @@ def batch_shape_set(b: int, branchy: bool = False, shape=None):
     if shape is None:
         _check(load().scan_batch_shape_set(b, int(bool(branchy)), None))
         return
-    sh = shape if isinstance(shape, scan_shape) else scan_shape(shape["warps"], shape["stages"],
-                                                                 shape["tile_blocks"], shape.get("vote_rows", 0))
-    _check(load().scan_batch_shape_set(b, int(bool(branchy)), ctypes.byref(sh)))
+    _check(load().scan_batch_shape_set(b, int(bool(branchy)), ctypes.byref(_shape(shape))))
 
 
 def batch_shape_candidates(b: int, branchy: bool = False) -> list:

@@ -196,7 +196,8 @@ def test_batch_autotune_installs_group_shapes_and_stays_exact():
     assert 0 <= res["groups"] <= 64 and 0 < res["tuned_us"] <= res["rule_us"]
     for b in (1, 16, 32):
         assert gbscan.batch_shape_get(b, False) in gbscan.batch_shape_candidates(b, False) + \
-            [dict(warps=8, stages=2, tile_blocks=gbscan.batch_shape_get(b, False)["tile_blocks"], vote_rows=0)]
+            [dict(warps=8, stages=2, tile_blocks=gbscan.batch_shape_get(b, False)["tile_blocks"], vote_rows=0,
+                  vec_lanes=0)]
     for rep in range(2):
         got = bt.run(preds)
         assert [r.pair() for r in got] == [oracle.scan_values(v, lo, hi) for v, (lo, hi) in zip(vals, preds)]

@@ -97,7 +97,7 @@ def test_autotune_rejects_an_empty_predicate_and_keeps_the_old_shape():
     gbscan.autotune_reset()
     v = synth.uniform_values(5, 1 << 16, 10)
     col = gbscan.Column.from_host(v, 10)
-    keep = dict(warps=12, stages=2, tile_blocks=4, vote_rows=0)
+    keep = dict(warps=12, stages=2, tile_blocks=4, vote_rows=0, vec_lanes=0)
     gbscan.shape_set(10, "branchfree", keep)
     with pytest.raises(gbscan.ScanError) as e:
         col.autotune(500, 500, "branchfree")

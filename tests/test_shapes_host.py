@@ -25,7 +25,11 @@ def lib():
 def legal(kind, b, s):
     """The header's rules, restated."""
     full = kind in ("branchfree", "branchy")
-    step = 4 if b <= 16 else 2
+    default = 4 if b <= 16 else 2
+    lanes = s.get("vec_lanes", 0)
+    if lanes not in (0, default) and not (lanes == 2 and full and 9 <= b <= 16):
+        return False
+    step = lanes or default
     smem = s["warps"] * s["stages"] * (s["tile_blocks"] * 128 * b + 12)
     return (1 <= s["warps"] <= (16 if full else 8) and 1 <= s["stages"] <= 6
             and s["tile_blocks"] >= step and s["tile_blocks"] % step == 0
@@ -48,6 +52,10 @@ def test_candidates_are_legal_and_include_more_warps_and_vote_forms(kind):
             assert max(c["warps"] for c in cands) > 8
         if kind == "branchy" and b <= 21:
             assert {c["vote_rows"] for c in cands} == {0, 1}
+        if kind in ("branchfree", "branchy") and 9 <= b <= 16:       # the 2-lane geometry with 16 warps
+            assert any(c["vec_lanes"] == 2 and c["warps"] == 16 for c in cands)
+        else:
+            assert all(c["vec_lanes"] == 0 for c in cands)
 
 
 def test_illegal_shapes_are_refused_with_the_rule():
@@ -59,7 +67,10 @@ def test_illegal_shapes_are_refused_with_the_rule():
              (1, "zone_bf", dict(warps=8, stages=3, tile_blocks=36), "at most 32"),
              (8, "branchfree", dict(warps=8, stages=3, tile_blocks=8, vote_rows=1), "row vote"),
              (24, "branchy", dict(warps=8, stages=3, tile_blocks=2, vote_rows=1), "row vote"),
-             (32, "branchfree", dict(warps=16, stages=4, tile_blocks=2), "226 KB")]
+             (32, "branchfree", dict(warps=16, stages=4, tile_blocks=2), "226 KB"),
+             (8, "branchfree", dict(warps=16, stages=2, tile_blocks=4, vec_lanes=2), "vec_lanes"),
+             (12, "zone_bf", dict(warps=8, stages=2, tile_blocks=4, vec_lanes=2), "vec_lanes"),
+             (12, "branchfree", dict(warps=16, stages=2, tile_blocks=3, vec_lanes=2), "multiple of the warp step")]
     for b, kind, shape, why in cases:
         with pytest.raises(gbscan.ScanError) as e:
             gbscan.shape_set(b, kind, shape)
@@ -72,7 +83,7 @@ def test_illegal_shapes_are_refused_with_the_rule():
 
 def test_set_get_and_back_to_the_rule():
     rule = gbscan.shape_get(12, "branchy")
-    s = dict(warps=16, stages=2, tile_blocks=4, vote_rows=1)
+    s = dict(warps=16, stages=2, tile_blocks=4, vote_rows=1, vec_lanes=0)
     gbscan.shape_set(12, "branchy", s)
     assert gbscan.shape_get(12, "branchy") == s
     assert gbscan.shape_get(12, "branchfree") != s                 # per kernel
@@ -81,17 +92,18 @@ def test_set_get_and_back_to_the_rule():
 
 
 def test_cache_round_trip(tmp_path):
-    installed = {(3, "branchfree"): dict(warps=16, stages=3, tile_blocks=8, vote_rows=0),
-                 (9, "branchy"): dict(warps=12, stages=2, tile_blocks=4, vote_rows=1),
-                 (16, "zone_bf"): dict(warps=8, stages=2, tile_blocks=4, vote_rows=0),
-                 (30, "zone_br"): dict(warps=8, stages=2, tile_blocks=2, vote_rows=0)}
+    installed = {(3, "branchfree"): dict(warps=16, stages=3, tile_blocks=8, vote_rows=0, vec_lanes=0),
+                 (9, "branchy"): dict(warps=12, stages=2, tile_blocks=4, vote_rows=1, vec_lanes=0),
+                 (15, "branchy"): dict(warps=16, stages=2, tile_blocks=2, vote_rows=1, vec_lanes=2),
+                 (16, "zone_bf"): dict(warps=8, stages=2, tile_blocks=4, vote_rows=0, vec_lanes=0),
+                 (30, "zone_br"): dict(warps=8, stages=2, tile_blocks=2, vote_rows=0, vec_lanes=0)}
     gbscan.autotune_reset()
     for (b, kind), s in installed.items():
         gbscan.shape_set(b, kind, s)
     path = str(tmp_path / "shapes.txt")
     gbscan.autotune_save(path)
     lines = open(path).read().splitlines()
-    assert lines[0] == "gbscan-shapes 1" and lines[1].startswith("device ")
+    assert lines[0] == "gbscan-shapes 2" and lines[1].startswith("device ")
     assert len([ln for ln in lines[2:] if ln and not ln.startswith("#")]) == len(installed)
     gbscan.autotune_reset()
     assert gbscan.shape_get(3, "branchfree")["warps"] == 8
@@ -111,19 +123,20 @@ def _write(tmp_path, name, text):
 
 def test_cache_validation_is_all_or_nothing(tmp_path):
     gbscan.autotune_reset()
-    keep = dict(warps=12, stages=2, tile_blocks=4, vote_rows=0)
+    keep = dict(warps=12, stages=2, tile_blocks=4, vote_rows=0, vec_lanes=0)
     gbscan.shape_set(5, "branchfree", keep)
     good = str(tmp_path / "good.txt")
     gbscan.autotune_save(good)
     head, device = open(good).read().splitlines()[:2]
-    row = "full_bf 7 16 2 8 0 10.0 12.0"
-    cases = [("gbscan-shapes 1\n", "device line"),
-             ("gbscan-shape 1\n" + device + "\n", "not a gbscan shape cache"),
-             ("gbscan-shapes 2\n" + device + "\n", "version 2"),
+    row = "full_bf 7 16 2 8 0 0 10.0 12.0"
+    cases = [("gbscan-shapes 2\n", "device line"),
+             ("gbscan-shape 2\n" + device + "\n", "not a gbscan shape cache"),
+             ("gbscan-shapes 1\n" + device + "\n", "version 1"),
              (head + "\ndevice Other_GPU 7\n" + row + "\n", "tuned on 'Other_GPU 7'"),
-             (head + "\n" + device + "\nfull_xx 7 16 3 8 0 1 1\n", "unknown kernel kind"),
-             (head + "\n" + device + "\nfull_bf 7 16 3 6 0 1 1\n", "multiple of the warp step"),
-             (head + "\n" + device + "\nqueue_bf 7 12 3 8 0 1 1\n", "warps"),
+             (head + "\n" + device + "\nfull_xx 7 16 3 8 0 0 1 1\n", "unknown kernel kind"),
+             (head + "\n" + device + "\nfull_bf 7 16 3 6 0 0 1 1\n", "multiple of the warp step"),
+             (head + "\n" + device + "\nqueue_bf 7 12 3 8 0 0 1 1\n", "warps"),
+             (head + "\n" + device + "\nfull_bf 7 16 2 8 0 2 1 1\n", "vec_lanes"),
              (head + "\n" + device + "\n" + row + "\n" + row + "\n", "duplicate"),
              (head + "\n" + device + "\nfull_bf 7 16 3\n", "expected"),
              (head + "\n" + device + "\n" + row + " extra\n", "expected")]
@@ -136,7 +149,7 @@ def test_cache_validation_is_all_or_nothing(tmp_path):
         gbscan.autotune_load(str(tmp_path / "missing.txt"))
     # comments and blank lines are allowed; a valid file replaces the table
     gbscan.autotune_load(_write(tmp_path, "ok.txt", head + "\n" + device + "\n# note\n\n" + row + "\n"))
-    assert gbscan.shape_get(7, "branchfree") == dict(warps=16, stages=2, tile_blocks=8, vote_rows=0)
+    assert gbscan.shape_get(7, "branchfree") == dict(warps=16, stages=2, tile_blocks=8, vote_rows=0, vec_lanes=0)
     assert gbscan.shape_get(5, "branchfree")["warps"] == 8                # replaced, not merged
     gbscan.autotune_reset()
     assert os.path.exists(good)
@@ -148,7 +161,7 @@ def test_batch_shapes_candidates_rules_and_cache(tmp_path):
         for b in range(1, 33):
             rule = gbscan.batch_shape_get(b, br)
             step = 4 if b <= 16 else 2
-            assert rule["warps"] == 8 and rule["stages"] == 2 and rule["vote_rows"] == 0
+            assert rule["warps"] == 8 and rule["stages"] == 2 and rule["vote_rows"] == 0 and rule["vec_lanes"] == 0
             assert rule["tile_blocks"] % step == 0 and rule["tile_blocks"] * 128 * b <= 12 * 1024
             cands = gbscan.batch_shape_candidates(b, br)
             assert cands and max(c["warps"] for c in cands) > 8
@@ -161,12 +174,12 @@ def test_batch_shapes_candidates_rules_and_cache(tmp_path):
     with pytest.raises(gbscan.ScanError) as e:
         gbscan.batch_shape_set(32, True, dict(warps=16, stages=3, tile_blocks=4))
     assert "226 KB" in str(e.value)
-    s = dict(warps=16, stages=2, tile_blocks=4, vote_rows=0)
+    s = dict(warps=16, stages=2, tile_blocks=4, vote_rows=0, vec_lanes=0)
     gbscan.batch_shape_set(9, True, s)
     assert gbscan.batch_shape_get(9, True) == s and gbscan.batch_shape_get(9, False)["warps"] == 8
     path = str(tmp_path / "b.txt")
     gbscan.autotune_save(path)
-    assert "batch_br 9 16 2 4 0" in open(path).read()
+    assert "batch_br 9 16 2 4 0 0" in open(path).read()
     gbscan.autotune_reset()
     assert gbscan.batch_shape_get(9, True)["warps"] == 8
     gbscan.autotune_load(path)
