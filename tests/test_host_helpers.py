@@ -73,7 +73,7 @@ def test_headline_line_stays_small_with_every_section_present():
         "plain": {"ms_l2_flushed": 0.0105, "gbs_l2_flushed": 1600.0, "ms_l2_warm": 0.0082},
         "probes": {"triad": {"gbs": 6700.0}, "decode_resident": {
             "t_dec_median_below_ridge_gvals": 5.0,
-            "l2_control": {"case": "c" * 100, "l2_gbs_median": 8500.0, "l2_gbs_min": 8100.0,
+            "l2_control": {"case": "c" * 100, "l2_gbs": 9500.0, "l2_gbs_median_b20_32": 8100.0,
                            "beta_read_gbs": 7100.0, "above_beta_read": True}}},
         "zone": {"rows": [{"p": p, "sigma": s, "speedup": 12.5, "speedup_zone_agg": 13.1, "speedup_auto": 12.4, "exact": True}
                           for p in (0.0, 0.01, 0.1, 1.0) for s in (1e-4, 1e-3, 1e-2, 0.1, 0.5)]},
