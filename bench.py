@@ -680,6 +680,8 @@ def summarise(plain, probes, zone, select, layouts, conj, batched, serving, beta
         ld = {x["load"]: x for x in serving["loads"]}
         if 0.9 in ld:
             out["serve_0.9"] = [ld[0.9]["achieved_qps"], ld[0.9]["p50_us"], ld[0.9]["p99_us"]]
+        if 2.0 in ld:
+            out["serve_2.0"] = [ld[2.0]["achieved_qps"], ld[2.0]["queries_per_batch"]]
         out["serve_exact"] = all(x["exact_vs_alone"] for x in serving["loads"])
     return out
 
@@ -1291,7 +1293,7 @@ SERVE_WORKLOAD = ("serving: device-resident table of 64 columns x 2^27 values, b
                   "range predicates, sigma log-uniform in [1e-4, 1]; COUNT + SUM per column")
 
 
-def run_serving(args, dev, stream, gbscan):
+def run_serving(args, dev, stream, gbscan, slots=4, loads=(0.25, 0.5, 0.9, 1.5, 2.0)):
     """Continuous-batching server vs serial per-query launches (config 5)."""
     import threading
 
@@ -1341,12 +1343,12 @@ def run_serving(args, dev, stream, gbscan):
                                                   "p99_us": round(float(np.percentile(lat, 99)), 1)},
            "loads": []}
     checked = 0
-    for factor in [0.25, 0.5, 0.9, 1.5]:
+    for factor in loads:
         rate = factor * serial_qps
         count = max(200, int(rate * args.serve_seconds))
         qs = [make_query() for _ in range(count)]
         gaps = rng.exponential(1.0 / rate, size=count)
-        srv = gbscan.Server(cols, slots=4, device_bytes_per_slot=112 * 512, max_queue=1 << 20)
+        srv = gbscan.Server(cols, slots=slots, device_bytes_per_slot=112 * 512, max_queue=1 << 20)
         ids = [None] * count
         lats = [None] * count
         results = [None] * count
