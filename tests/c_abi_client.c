@@ -7,7 +7,12 @@
  * success; on a library error it prints the status name and message and exits
  * 1.  The test that runs it compares the lines with the oracle.
  *
- * usage: c_abi_client <values.bin> <n> <b> <base> <lo> <hi>
+ * With a seventh argument it also tunes the branch-free kernel's launch
+ * shape on this column, saves the shape cache to that path, resets and
+ * reloads it, and scans once more, printing "shape <warps> <stages>
+ * <tile_blocks> <vote_rows> <vec_lanes>" and "tuned <count> <sum> <blocks>".
+ *
+ * usage: c_abi_client <values.bin> <n> <b> <base> <lo> <hi> [shape-cache]
  */
 #include <stdint.h>
 #include <stdio.h>
@@ -23,8 +28,8 @@ static int fail(const char *what, scan_status s)
 
 int main(int argc, char **argv)
 {
-    if (argc != 7) {
-        fprintf(stderr, "usage: %s <values.bin> <n> <b> <base> <lo> <hi>\n", argv[0]);
+    if (argc != 7 && argc != 8) {
+        fprintf(stderr, "usage: %s <values.bin> <n> <b> <base> <lo> <hi> [shape-cache]\n", argv[0]);
         return 2;
     }
     const uint64_t n = strtoull(argv[2], NULL, 10);
@@ -56,6 +61,25 @@ int main(int argc, char **argv)
         if (s != SCAN_OK) return fail("scan_run", s);
         printf("%d %lld %lld %llu\n", (int)strategies[i], (long long)r.count, (long long)r.sum,
                (unsigned long long)r.blocks_scanned);
+    }
+    if (argc == 8) {
+        scan_tune_result t;
+        s = scan_autotune_column(col, pred, SCAN_BRANCHFREE, 1, NULL, &t);
+        if (s != SCAN_OK) return fail("scan_autotune_column", s);
+        s = scan_autotune_save(argv[7]);
+        if (s != SCAN_OK) return fail("scan_autotune_save", s);
+        s = scan_autotune_reset();
+        if (s != SCAN_OK) return fail("scan_autotune_reset", s);
+        s = scan_autotune_load(argv[7]);
+        if (s != SCAN_OK) return fail("scan_autotune_load", s);
+        scan_shape sh;
+        s = scan_shape_get(b, SCAN_BRANCHFREE, &sh);
+        if (s != SCAN_OK) return fail("scan_shape_get", s);
+        printf("shape %u %u %u %u %u\n", sh.warps, sh.stages, sh.tile_blocks, sh.vote_rows, sh.vec_lanes);
+        scan_result r;
+        s = scan_run(col, pred, SCAN_BRANCHFREE, NULL, &r);
+        if (s != SCAN_OK) return fail("scan_run", s);
+        printf("tuned %lld %lld %llu\n", (long long)r.count, (long long)r.sum, (unsigned long long)r.blocks_scanned);
     }
     s = scan_column_destroy(col);
     if (s != SCAN_OK) return fail("scan_column_destroy", s);

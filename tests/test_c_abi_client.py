@@ -1,7 +1,8 @@
 """The boundary from plain C.  tests/c_abi_client.c includes only
 include/gbscan.h and links only libgbscan.so: on CPU it must compile and link
 cleanly (every call it makes is declared and exported); on the GPU every
-strategy's COUNT, SUM and blocks read must equal the oracle's."""
+strategy's COUNT, SUM and blocks read must equal the oracle's, and so must a
+scan after the client tunes its launch shape and round-trips the cache."""
 import os
 import shutil
 import subprocess
@@ -55,11 +56,18 @@ def test_c_client_matches_the_oracle_for_every_strategy(tmp_path, n, b, base, si
     lo, hi = synth.pick_range(seed + 1, b, sigma, base)
     path = tmp_path / "values.bin"
     np.ascontiguousarray(v, dtype=np.uint32).tofile(path)
-    r = subprocess.run([exe, str(path), str(n), str(b), str(base), str(lo), str(hi)],
+    cache = tmp_path / "shapes.txt"
+    r = subprocess.run([exe, str(path), str(n), str(b), str(base), str(lo), str(hi), str(cache)],
                        capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stderr[-3000:]
     lines = [ln.split() for ln in r.stdout.splitlines() if ln.strip()]
-    assert len(lines) == 7
+    assert len(lines) == 9
+    shape, tuned = lines[7], lines[8]
+    assert shape[0] == "shape" and tuned[0] == "tuned"
+    assert open(cache).read().startswith("gbscan-shapes 2\ndevice ")
+    assert (int(tuned[1]), int(tuned[2])) == oracle.scan_values(v, lo, hi)
+    assert int(tuned[3]) == (n + 1023) // 1024
+    lines = lines[:7]
     want = oracle.scan_values(v, lo, hi)
     words = oracle.pack(v, b, base)
     zmin, zmax = oracle.zonemap(words, n, b, base)
