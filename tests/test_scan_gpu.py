@@ -257,3 +257,45 @@ def test_zone_size_n2pow30_b16_from_raw_values():
             if strat in ("zone_bf", "zone_br"):
                 assert r.blocks_scanned == touched
     col.close()
+
+
+def test_auto_edges_layouts_stale_and_rebuilt_zone_maps():
+    """SCAN_AUTO without a zone map (or on a non-lane layout) runs the full scan;
+    after scan_column_upload_packed the zone map is stale, AUTO falls back to the
+    full scan on the new data, and once the map is rebuilt its survivor count
+    (sorted bounds taken again) follows the new data."""
+    b, n = 12, 200 * 1024 + 99
+    sorted_v = synth.clustered_values(synth.seed_for(76, 1), n, b, 0.0)
+    shuffled_v = synth.clustered_values(synth.seed_for(76, 2), n, b, 1.0)
+    nblocks = (n + 1023) // 1024
+    lo, hi = synth.pick_range(synth.seed_for(76, 3), b, 0.02)
+    col = gbscan.Column.from_host(sorted_v, b)
+    r = col.run(lo, hi, "auto")                          # no zone map yet: full scan
+    assert r.pair() == oracle.scan_values(sorted_v, lo, hi) and r.blocks_scanned == nblocks
+    col.zonemap_build()
+    r = col.run(lo, hi, "auto")                          # sorted and selective: zone skipping
+    assert r.pair() == oracle.scan_values(sorted_v, lo, hi) and r.blocks_scanned < nblocks // 10
+    for plo, phi in [(5, 5), (0, 1 << b), (-(1 << 40), 0), (1 << b, 1 << 40)]:   # empty, full, outside
+        assert col.run(plo, phi, "auto").pair() == oracle.scan_values(sorted_v, plo, phi)
+    # new data through the packed upload: the zone map is stale and AUTO scans everything
+    col.upload_packed(oracle.pack(shuffled_v, b))
+    torch.cuda.synchronize()
+    r = col.run(lo, hi, "auto")
+    assert r.pair() == oracle.scan_values(shuffled_v, lo, hi) and r.blocks_scanned == nblocks
+    col.zonemap_build()                                  # shuffled: every block survives -> full scan
+    r = col.run(lo, hi, "auto")
+    assert r.pair() == oracle.scan_values(shuffled_v, lo, hi) and r.blocks_scanned == nblocks
+    col.upload_packed(oracle.pack(sorted_v, b))          # and back: selective again once rebuilt
+    torch.cuda.synchronize()
+    col.zonemap_build()
+    r = col.run(lo, hi, "auto")
+    assert r.pair() == oracle.scan_values(sorted_v, lo, hi) and r.blocks_scanned < nblocks // 10
+    col.close()
+    for layout in ("rowmajor", "bytes"):
+        lb = 16 if layout == "bytes" else 13
+        v = synth.clustered_values(synth.seed_for(76, 4), n, lb, 0.0)
+        c = gbscan.Column.from_host(v, lb, layout=layout)
+        plo, phi = synth.pick_range(synth.seed_for(76, 5), lb, 0.01)
+        r = c.run(plo, phi, "auto")
+        assert r.pair() == oracle.scan_values(v, plo, phi) and r.blocks_scanned == nblocks
+        c.close()

@@ -56,6 +56,28 @@ def test_noalloc_matches_the_oracle_on_consecutive_calls(b, n, strategy):
     col.close()
 
 
+def test_noalloc_with_a_tuned_sixteen_warp_shape():
+    """The allocation-free scan launches with the installed (tuned) shape: 16
+    warps and 2-block tiles of the 2-lane geometry at b = 15 still give the
+    oracle's result from the static scratch."""
+    b, n = 15, 120 * 1024 + 5
+    v = synth.uniform_values(synth.seed_for(97, b), n, b, 3)
+    col = gbscan.Column.from_host(v, b, 3)
+    out = torch.zeros(4, dtype=torch.int64, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    lo, hi = synth.pick_range(synth.seed_for(97, b, 1), b, 0.3, 3)
+    try:
+        gbscan.shape_set(b, "branchfree", dict(warps=16, stages=2, tile_blocks=2, vote_rows=0, vec_lanes=2))
+        for _ in range(2):
+            gbscan.scan_run_packed_noalloc(col.dev_packed, n, b, 3, lo, hi, out, status)
+            torch.cuda.synchronize()
+            assert int(status.cpu()[0]) == 0
+            assert tuple(int(x) for x in out.cpu()[:2]) == oracle.scan_values(v, lo, hi)
+    finally:
+        gbscan.shape_set(b, "branchfree", None)
+    col.close()
+
+
 def test_noalloc_empty_range_and_limits():
     v = synth.uniform_values(5, 4096, 9)
     col = gbscan.Column.from_host(v, 9)
