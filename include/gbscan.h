@@ -304,10 +304,14 @@ typedef struct scan_batch scan_batch; /* opaque: a planned batch of column scans
 
 /* Plan a batch over `ncols` columns (the paper has no batched form; this
  * runs thousands of column scans as one CUDA-graph launch).  Every column's
- * blocks are cut into tiles of at most 12 KB; columns are grouped by
+ * blocks are cut into tiles (by default about 6 KB); columns are grouped by
  * (predicate flavour, width) and each group is served by one width-specialised
- * persistent kernel, the groups recorded as parallel branches of one graph with
- * grids sized to their work.  Warps pop `tiles_per_pop` consecutive tiles per
+ * persistent kernel.  Groups of 16 us or more by the bandwidth law are recorded
+ * as two concurrent chains of one graph: the narrow half of their widths
+ * ascending, the wide half descending, so that a decode-bound and a
+ * bandwidth-bound kernel share every SM (two CTAs per SM); shorter groups run
+ * on six more chains, with grids in proportion to their law time.  Warps pop
+ * `tiles_per_pop` consecutive tiles per
  * atomic (0 = chosen per group: at least 4, about four pops per warp).
  * strategies[i] picks column i's flavour and whether it skips blocks by zone
  * map (NULL = SCAN_BRANCHFREE for all; SCAN_AUTO counts as branch-free).
@@ -618,7 +622,7 @@ scan_status scan_shape_candidates(uint32_t b, scan_strategy strategy, scan_shape
  * scans; on failure the previous shape stays installed. */
 scan_status scan_autotune_column(scan_column *col, scan_pred pred, scan_strategy strategy, uint32_t reps,
                                  void *stream, scan_tune_result *out);
-/* Write the tuned shapes to `path`, a versioned text file: a "gbscan-shapes 2"
+/* Write the tuned shapes to `path`, a versioned text file: a "gbscan-shapes 3"
  * line, a "device <name> <SMs>" line, then one "kind b warps stages
  * tile_blocks vote_rows vec_lanes tuned_us rule_us" line per tuned (kernel,
  * b). */
@@ -636,7 +640,9 @@ scan_status scan_autotune_reset(void);
  * group of a batch launches one kernel with its width's shape (tile_blocks =
  * blocks per batch tile; vote_rows must be 0).  Legal: 1..16 warps, 1..6
  * stages, tile_blocks a multiple of the warp step and at most 64, warps *
- * stages * (tile_blocks * 128 * b + 24) <= 226 KB, vec_lanes = 0.  branchy = 0 for the
+ * stages * (tile_blocks * 128 * b + 24) <= 226 KB, vec_lanes = 0.  Shapes
+ * above 112 KB of slots leave no room for a second CTA on the SM and lose the
+ * overlap of the two chains; the candidates stay below it.  branchy = 0 for the
  * branch-free kernel, 1 for the branchy one.  They are saved and loaded with
  * the others ("batch_bf" / "batch_br" lines).  A batch picks up shape
  * changes when it is created, when its strategies are set, or when it is

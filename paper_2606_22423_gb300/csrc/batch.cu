@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -47,7 +48,18 @@ int batch_grid() { return gb_device_sms(); }
 // then the status word at u32 index kMaxGroups.
 constexpr size_t kMaxGroups = 64;
 constexpr size_t kCtlWords = 40;  // u64 words: 64 + 1 u32 fit in 33
-constexpr int kBranches = 8;      // parallel chains of width-group kernels in the graph
+constexpr int kBranches = 8;      // concurrent chains of width-group kernels in the graph
+constexpr int kPairChains = 2;    // chains 0 and 1: the large groups, narrow and wide widths
+// A group's time on the whole GPU by the bandwidth law, with GB300 figures
+// (copy bandwidth 6.7 TB/s, branch-free decode 4.3 Tvalues/s), in
+// microseconds; its packed bytes and values count whole columns (zone skipping
+// only shortens it).
+double law_us(double bytes, int b) { return std::max(bytes / 6.7e6, bytes * 8.0 / b / 4.3e6); }
+// Groups shorter than this run on the small-group chains (2..7).
+constexpr double kSmallGroupUs = 16.0;
+// A group of this law time or more gets two CTAs per SM; a shorter one a
+// proportional share (fewer warps to start, to pop and to drain).
+constexpr double kFullGridUs = 10.0;
 
 }  // namespace
 
@@ -77,8 +89,8 @@ struct scan_batch {
     unsigned long long* d_results = nullptr;  // 4 words per column, then 2 pop counters + status
     scan_result* h_results = nullptr;  // pinned copy of the results
     cudaStream_t capture_stream = nullptr;
-    cudaStream_t branch[8] = {};       // capture-time branches (one graph node chain each)
-    cudaEvent_t fork = nullptr, join[8] = {};
+    cudaStream_t branch[kBranches] = {};  // capture-time branches (one graph node chain each)
+    cudaEvent_t fork = nullptr, join[kBranches] = {};
     cudaGraphExec_t graph = nullptr;
 };
 
@@ -93,10 +105,10 @@ static cudaError_t launch_batch_kernel(bool branchy, int b, const BatchParams& p
 namespace {
 
 // Lay out the tiles for the current strategies: branch-free columns first,
-// and within each kernel by width, so that at any moment the persistent warps
-// of the whole GPU run the same width's decode code (one kernel holds 32
-// fully unrolled width variants; mixing them on an SM thrashes its
-// instruction cache).
+// and within each kernel by width, one width-specialised launch per group,
+// so that an SM runs at most two widths' decode code at a time (one CTA of
+// each graph chain; a kernel holding all 32 fully unrolled width variants
+// thrashed the instruction cache).
 scan_status layout(scan_batch* bt)
 {
     std::vector<uint32_t> order;
@@ -156,15 +168,22 @@ scan_status layout(scan_batch* bt)
     }
     for (int k = 0; k < 2; ++k) bt->ntiles_k[k] = tiles[k];
     if (bt->groups.size() > kMaxGroups) return bfail(SCAN_EINVAL, "too many width groups");
-    // per group: a grid sized to its work (about 16 tiles per warp, at most one
-    // CTA per SM), pops of about a quarter of a warp's share (at least 4
-    // tiles), and a host-built table of each pop's first column
+    // per group: two CTAs per SM for a group of kFullGridUs or more, a share
+    // in proportion to its law time below that (and a tile per warp at
+    // least), pops of about a quarter of a warp's share (at least 4 tiles),
+    // and a host-built table of each pop's first column.  Two CTAs per SM let
+    // the block scheduler give every SM one CTA of each concurrent chain; with
+    // one per SM the chains split the SMs between them and the replay took
+    // 22% longer.  Full grids for small groups cost 5-40% on batches of 64 and
+    // 512 columns (thousands of warps popping a few tiles from one counter).
     std::vector<uint32_t> chunk_col;
-    const int sms = batch_grid();
+    const uint64_t cap = 2ull * static_cast<uint64_t>(batch_grid());
     for (auto& g : bt->groups) {
         const uint64_t gw = static_cast<uint64_t>(g.shape.warps);
-        const uint64_t want = (static_cast<uint64_t>(g.ntiles) + 16 * gw - 1) / (16 * gw);
-        g.grid = static_cast<int>(std::max<uint64_t>(1, std::min<uint64_t>(want, sms)));
+        const uint64_t by_tiles = (static_cast<uint64_t>(g.ntiles) + gw - 1) / gw;
+        const uint64_t by_time =
+            static_cast<uint64_t>(std::ceil(static_cast<double>(cap) * law_us(g.bytes, g.b) / kFullGridUs));
+        g.grid = static_cast<int>(std::max<uint64_t>(1, std::min({by_tiles, by_time, cap})));
         const uint32_t warps = static_cast<uint32_t>(g.grid * gw);
         const uint32_t c = bt->tiles_per_pop ? bt->tiles_per_pop : std::max<uint32_t>(4, g.ntiles / (4 * warps));
         g.chunk = std::min<uint32_t>(c, 1024);
@@ -555,16 +574,37 @@ scan_status scan_batch_exec(scan_batch* bt, const scan_pred* preds, void* stream
         cudaMemcpyAsync(bt->d_table, bt->h_table, table_bytes, cudaMemcpyHostToDevice, cs);
         cudaMemsetAsync(bt->d_results, 0, res_words * sizeof(unsigned long long), cs);
         cudaEventRecord(bt->fork, cs);
-        // groups in width order, round-robin over the branches: neighbouring
-        // widths run side by side.  (Longest-first onto the least-loaded branch
-        // was 3.8% slower: the largest groups then start together and share the
-        // GPU, so their times alone do not add up along a branch.)
-        bool used[kBranches] = {};
-        int next_branch = 0;
+        // Large groups (law time kSmallGroupUs or more) on two chains: the
+        // narrow half in ascending width, the wide half in descending width,
+        // captured alternately.  At any moment a decode-bound kernel (small b)
+        // runs beside a bandwidth-bound one (large b), one CTA of each per SM,
+        // and both chains end on the middle widths.  (Eight chains in width
+        // order, one CTA per SM: 0.97 ms on the 4096-column workload; these two
+        // chains: 0.86-0.87 ms.  Halves cut by equal law time instead of equal
+        // group counts: 0.93 ms.)  Small groups, whose time is mostly launch
+        // and ramp, go round-robin on six more chains so that few of them queue
+        // behind one another: 512 columns of 2^28 values in all took 0.38 ms
+        // on the two chains and 0.23 ms this way.
+        std::vector<size_t> live, small;
         for (size_t gi = 0; gi < bt->groups.size(); ++gi) {
             const auto& g = bt->groups[gi];
             if (!g.ntiles) continue;
-            const int k = next_branch++ % kBranches;
+            (law_us(g.bytes, g.b) < kSmallGroupUs ? small : live).push_back(gi);
+        }
+        const auto by_width = [&](size_t x, size_t y) { return bt->groups[x].b < bt->groups[y].b; };
+        std::stable_sort(live.begin(), live.end(), by_width);
+        std::stable_sort(small.begin(), small.end(), by_width);
+        const size_t half = (live.size() + 1) / 2;
+        std::vector<std::pair<size_t, int>> seq;  // (group, chain) in capture order
+        for (size_t i = 0; i < small.size(); ++i)
+            seq.push_back({small[i], kPairChains + static_cast<int>(i % (kBranches - kPairChains))});
+        for (size_t i = 0; i < half; ++i) {
+            seq.push_back({live[i], 0});
+            if (half + i < live.size()) seq.push_back({live[live.size() - 1 - i], 1});
+        }
+        bool used[kBranches] = {};
+        for (const auto& [gi, k] : seq) {
+            const auto& g = bt->groups[gi];
             cudaStream_t bs = bt->branch[k];
             if (!used[k]) cudaStreamWaitEvent(bs, bt->fork, 0);  // joins the capture
             used[k] = true;

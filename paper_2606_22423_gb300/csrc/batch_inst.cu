@@ -21,30 +21,29 @@ namespace {
 
 constexpr bool kBr = GB_BATCH_BRANCHY != 0;
 
-template <int BFIX, int WMAX>
-cudaError_t launch_one(const gb::BatchParams& p, int warps, int grid, cudaStream_t st)
+template <int BFIX>
+cudaError_t launch_fixed(const gb::BatchParams& p, int warps, int grid, cudaStream_t st)
 {
+    if (warps < 1 || warps > 16) return cudaErrorInvalidValue;
     static std::atomic<unsigned long long> configured{0ull};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     const unsigned long long bit = 1ull << (dev & 63);
-    const void* fn = reinterpret_cast<const void*>(gb::k_scan_batch<kBr, BFIX, WMAX>);
+    const void* fn = reinterpret_cast<const void*>(gb::k_scan_batch<kBr, BFIX>);
     if (!(configured.load() & bit)) {
         e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, gb::kSmemMax);
+        if (e != cudaSuccess) return e;
+        // all of the SM's unified memory as shared memory: two CTAs of up to
+        // 112 KB of slots each must fit side by side
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 static_cast<int>(cudaSharedmemCarveoutMaxShared));
         if (e != cudaSuccess) return e;
         configured.fetch_or(bit);
     }
     const uint32_t smem = gb::batch_smem_bytes(static_cast<uint32_t>(warps), p.stages, p.slot_bytes);
-    gb::k_scan_batch<kBr, BFIX, WMAX><<<grid, warps * 32, smem, st>>>(p);
+    gb::k_scan_batch<kBr, BFIX><<<grid, warps * 32, smem, st>>>(p);
     return cudaGetLastError();
-}
-
-template <int BFIX>
-cudaError_t launch_fixed(const gb::BatchParams& p, int warps, int grid, cudaStream_t st)
-{
-    if (warps < 1 || warps > 16) return cudaErrorInvalidValue;
-    return warps > 8 ? launch_one<BFIX, 16>(p, warps, grid, st) : launch_one<BFIX, 8>(p, warps, grid, st);
 }
 
 template <int LO, int HI>

@@ -1,7 +1,7 @@
 // Batched scan: thousands of columns in one CUDA-graph launch.
 //
 // The host cuts every column's 1024-value blocks into tiles (per width, the
-// most blocks that fill a 12 KB slot in whole warp steps), groups the
+// most blocks that fill a 6 KB slot in whole warp steps), groups the
 // columns by width and numbers each group's tiles consecutively.  One
 // persistent kernel serves a group: warps pop chunks of consecutive tile
 // numbers from the group's atomic counter (a host-built table gives each
@@ -47,22 +47,29 @@ struct BatchParams {
     uint32_t slot_bytes;           // bytes per slot: the group's largest tile
 };
 
-// Default batch shape: 8 warps, each with 2 slots of 12 KB (per tile the batch
-// kernel spends about a third of its issue on bookkeeping -- column lookup,
-// keep mask, copy issue -- so tiles larger than the scans' 8 KB paid: 3 x 8 KB
-// slots took 12% longer).  The shape is a run-time choice per width group;
+// Default batch shape: 8 warps, each with 2 slots of 6 KB, and at most
+// kBatchPairSmem of slots per CTA so that two CTAs share an SM (the kernel
+// is compiled for 128 registers a thread).  The graph runs the narrow widths
+// (decode-bound) and the wide ones (bandwidth-bound) as two concurrent chains,
+// so an SM holds one CTA of each kind and its ALUs and the HBM are busy at
+// once.  On the 4096-column workload this took the replay from 0.97 to
+// 0.86 ms; 3 or 4 stages of smaller slots, 4- or 6-warp CTAs and three CTAs
+// per SM were all slower.  The shape is a run-time choice per width group;
 // the autotuner may replace it.
 constexpr int kBatchWarps = 8;
 constexpr int kBatchStages = 2;
-constexpr int kBatchSlot = 12 * 1024;
+constexpr int kBatchSlot = 6 * 1024;
 constexpr uint32_t kBatchSlotExtra = 8 + 16;   // a slot's barrier and metadata
+// Slot bytes of a CTA that leave room for a second one on the SM (228 KB of
+// shared memory per SM, 1 KB of it reserved per CTA).
+constexpr uint32_t kBatchPairSmem = 112 * 1024;
 
 __host__ __device__ constexpr uint32_t batch_smem_bytes(uint32_t warps, uint32_t stages, uint32_t slot_bytes)
 {
     return warps * stages * (slot_bytes + kBatchSlotExtra);
 }
 
-// Default blocks per batch tile at width b: as many as fill a 12 KB slot, a
+// Default blocks per batch tile at width b: as many as fill a 6 KB slot, a
 // multiple of the warp step (4 blocks for b <= 16, else 2), at most 64 (the
 // keep mask).
 __host__ __device__ constexpr uint32_t batch_tile_blocks(uint32_t b)
@@ -71,7 +78,16 @@ __host__ __device__ constexpr uint32_t batch_tile_blocks(uint32_t b)
     const uint32_t tb = (static_cast<uint32_t>(kBatchSlot) / (128u * b)) / step * step;
     return tb < step ? step : (tb > 64u ? 64u : tb);
 }
-static_assert(batch_tile_blocks(32) * 128u * 32u <= static_cast<uint32_t>(kBatchSlot), "a tile fits its slot");
+
+// Default warps per CTA at width b: 8, fewer where the one-step tiles of the
+// widest columns (b = 14..16, 28..32: 7-8 KB) would overflow kBatchPairSmem.
+__host__ __device__ constexpr int batch_default_warps(uint32_t b)
+{
+    const uint32_t per_warp = static_cast<uint32_t>(kBatchStages) * (batch_tile_blocks(b) * 128u * b + kBatchSlotExtra);
+    const uint32_t w = kBatchPairSmem / per_warp;
+    return w >= static_cast<uint32_t>(kBatchWarps) ? kBatchWarps : static_cast<int>(w);
+}
+static_assert(batch_default_warps(32) == 6 && batch_default_warps(1) == 8, "default batch CTAs fit two per SM");
 
 struct SlotMeta {
     uint32_t col;   // column index
@@ -110,10 +126,10 @@ __device__ __forceinline__ CountSum batch_consume_body(const unsigned char* slot
 // Every column of the launch has width BFIX and its decode is inlined: one
 // width's code per kernel keeps the instruction cache warm (a kernel holding
 // all 32 unrolled decoders stalled on instruction fetch), so a batch runs one
-// such kernel per width group.  WMAX: the largest CTA the instantiation is
-// compiled for (8 or 16 warps).
-template <bool BRANCHY, int BFIX, int WMAX = 8>
-__global__ void __launch_bounds__(WMAX * 32, 1) k_scan_batch(const BatchParams P)
+// such kernel per width group.  Compiled for CTAs of up to 16 warps, which
+// caps it at 128 registers a thread: two 8-warp CTAs then fit one SM.
+template <bool BRANCHY, int BFIX>
+__global__ void __launch_bounds__(512, 1) k_scan_batch(const BatchParams P)
 {
     static_assert(BFIX >= 1 && BFIX <= 32, "batch kernels are width-specialised");
     extern __shared__ __align__(128) unsigned char smem[];

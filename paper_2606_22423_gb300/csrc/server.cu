@@ -157,7 +157,7 @@ cudaError_t launch_slot(scan_server* sv, Slot& s, const char** step)
         // the default batch shape: the tiles were cut by batch_tile_blocks
         p.stages = gb::kBatchStages;
         p.slot_bytes = gb::batch_tile_blocks(g.b) * 128u * g.b;
-        e = gb_launch_batch(false, static_cast<int>(g.b), p, gb::kBatchWarps, sv->sms, s.stream);
+        e = gb_launch_batch(false, static_cast<int>(g.b), p, gb::batch_default_warps(g.b), sv->sms, s.stream);
     }
     if (e == cudaSuccess) {
         // results of the n entries, then the control words (pop counters, status)

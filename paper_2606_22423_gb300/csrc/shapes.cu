@@ -74,7 +74,7 @@ bool is_batch(int kind) { return kind == kKBatchBF || kind == kKBatchBR; }
 gb::LaunchShape default_shape(int kind, int b)
 {
     if (is_batch(kind))
-        return gb::LaunchShape{gb::kBatchWarps, gb::kBatchStages,
+        return gb::LaunchShape{gb::batch_default_warps(static_cast<uint32_t>(b)), gb::kBatchStages,
                                static_cast<int>(gb::batch_tile_blocks(static_cast<uint32_t>(b))), 0, 0};
     const gb::ShapeInfo si = gb::shape_of(b);
     return gb::LaunchShape{si.warps, si.stages, si.tile_blocks, 0, 0};
@@ -121,15 +121,18 @@ bool shape_ok(int kind, int b, const gb::LaunchShape& s, const char** why)
 // The tuner's search space for (kind, b): 8/12/16 warps (full scans; queue
 // scans 8), 2..4 stages, tiles of about 2..24 KB in whole warp steps, and for
 // full branchy scans at b <= 21 both vote groups; illegal shapes dropped.
-// Batched scans: 8/12/16 warps, 2 or 3 stages, tiles of about 8..32 KB (their
-// per-tile bookkeeping favours larger tiles).
+// Batched scans: 4/6/8 warps, 2 or 3 stages, tiles of about 4..12 KB, only
+// shapes whose slots leave room for a second CTA on the SM (the graph runs
+// two chains of width groups side by side).
 std::vector<gb::LaunchShape> candidates(int kind, int b)
 {
     const bool full = kind == kKFullBF || kind == kKFullBR || is_batch(kind);
     std::vector<int> geos{0};
     if ((kind == kKFullBF || kind == kKFullBR) && b >= 9 && b <= 16) geos.push_back(2);
-    std::vector<int> warps = full ? std::vector<int>{8, 12, 16} : std::vector<int>{8};
-    const std::vector<int> kbs = is_batch(kind) ? std::vector<int>{8, 12, 16, 24, 32}
+    std::vector<int> warps = is_batch(kind) ? std::vector<int>{4, 6, 8}
+                             : full           ? std::vector<int>{8, 12, 16}
+                                              : std::vector<int>{8};
+    const std::vector<int> kbs = is_batch(kind) ? std::vector<int>{4, 6, 8, 12}
                                                 : std::vector<int>{2, 4, 6, 8, 12, 16, 24};
     const int votes = (kind == kKFullBR && b <= 21) ? 2 : 1;
     const std::vector<int> stages = is_batch(kind) ? std::vector<int>{2, 3} : std::vector<int>{2, 3, 4};
@@ -149,6 +152,7 @@ std::vector<gb::LaunchShape> candidates(int kind, int b)
                     for (int tb : tiles) {
                         const gb::LaunchShape s{w, st, tb, v, geo};
                         const char* why = nullptr;
+                        if (is_batch(kind) && smem_of(kind, b, s) > gb::kBatchPairSmem) continue;
                         if (shape_ok(kind, b, s, &why)) out.push_back(s);
                     }
     }
@@ -191,7 +195,7 @@ std::string device_identity()
 }
 
 constexpr const char* kMagic = "gbscan-shapes";
-constexpr int kVersion = 2;  // 2: vec_lanes column
+constexpr int kVersion = 3;  // 2: vec_lanes column; 3: batch shapes for two CTAs per SM
 
 }  // namespace
 

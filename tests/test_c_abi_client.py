@@ -64,7 +64,7 @@ def test_c_client_matches_the_oracle_for_every_strategy(tmp_path, n, b, base, si
     assert len(lines) == 9
     shape, tuned = lines[7], lines[8]
     assert shape[0] == "shape" and tuned[0] == "tuned"
-    assert open(cache).read().startswith("gbscan-shapes 2\ndevice ")
+    assert open(cache).read().startswith("gbscan-shapes 3\ndevice ")
     assert (int(tuned[1]), int(tuned[2])) == oracle.scan_values(v, lo, hi)
     assert int(tuned[3]) == (n + 1023) // 1024
     lines = lines[:7]

@@ -287,7 +287,7 @@ def test_guarded_planner_against_the_law_on_a_held_out_batch():
     out = torch.zeros((len(cols), 4), dtype=torch.int64, device="cuda")
     parr = gbscan.Batch.pred_array(preds)
     ts = {"law": [], "guarded": []}
-    for _ in range(9):                                             # interleaved replays
+    for _ in range(21):                                            # interleaved replays (0.2 ms each)
         for name, bt in (("law", b_law), ("guarded", b_g)):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(s)
@@ -295,7 +295,7 @@ def test_guarded_planner_against_the_law_on_a_held_out_batch():
             e1.record(s)
             e1.synchronize()
             ts[name].append(e0.elapsed_time(e1))
-    t_law, t_g = sorted(ts["law"])[4], sorted(ts["guarded"])[4]
+    t_law, t_g = sorted(ts["law"])[10], sorted(ts["guarded"])[10]
     print(f"guarded planner vs law: {t_law / t_g:.4f}x ({moved} of {len(cols)} columns moved, "
           f"margin {margin:.3f}; law {t_law:.4f} ms, guarded {t_g:.4f} ms)")
     assert t_g <= 1.03 * t_law, (t_g, t_law, moved)

@@ -103,7 +103,7 @@ def test_cache_round_trip(tmp_path):
     path = str(tmp_path / "shapes.txt")
     gbscan.autotune_save(path)
     lines = open(path).read().splitlines()
-    assert lines[0] == "gbscan-shapes 2" and lines[1].startswith("device ")
+    assert lines[0] == "gbscan-shapes 3" and lines[1].startswith("device ")
     assert len([ln for ln in lines[2:] if ln and not ln.startswith("#")]) == len(installed)
     gbscan.autotune_reset()
     assert gbscan.shape_get(3, "branchfree")["warps"] == 8
@@ -129,9 +129,10 @@ def test_cache_validation_is_all_or_nothing(tmp_path):
     gbscan.autotune_save(good)
     head, device = open(good).read().splitlines()[:2]
     row = "full_bf 7 16 2 8 0 0 10.0 12.0"
-    cases = [("gbscan-shapes 2\n", "device line"),
-             ("gbscan-shape 2\n" + device + "\n", "not a gbscan shape cache"),
+    cases = [("gbscan-shapes 3\n", "device line"),
+             ("gbscan-shape 3\n" + device + "\n", "not a gbscan shape cache"),
              ("gbscan-shapes 1\n" + device + "\n", "version 1"),
+             ("gbscan-shapes 2\n" + device + "\n", "version 2"),
              (head + "\ndevice Other_GPU 7\n" + row + "\n", "tuned on 'Other_GPU 7'"),
              (head + "\n" + device + "\nfull_xx 7 16 3 8 0 0 1 1\n", "unknown kernel kind"),
              (head + "\n" + device + "\nfull_bf 7 16 3 6 0 0 1 1\n", "multiple of the warp step"),
@@ -161,13 +162,20 @@ def test_batch_shapes_candidates_rules_and_cache(tmp_path):
         for b in range(1, 33):
             rule = gbscan.batch_shape_get(b, br)
             step = 4 if b <= 16 else 2
-            assert rule["warps"] == 8 and rule["stages"] == 2 and rule["vote_rows"] == 0 and rule["vec_lanes"] == 0
-            assert rule["tile_blocks"] % step == 0 and rule["tile_blocks"] * 128 * b <= 12 * 1024
+            # the rule: 2 stages of about 6 KB (one warp step where a step is larger), 8 warps
+            # unless two such CTAs would not share an SM (112 KB of slots each at most)
+            assert rule["stages"] == 2 and rule["vote_rows"] == 0 and rule["vec_lanes"] == 0
+            assert rule["tile_blocks"] % step == 0
+            assert rule["tile_blocks"] * 128 * b <= 6 * 1024 or rule["tile_blocks"] == step
+            slots = rule["warps"] * rule["stages"] * (rule["tile_blocks"] * 128 * b + 24)
+            assert slots <= 112 * 1024
+            assert rule["warps"] == 8 or (rule["warps"] + 1) * 2 * (rule["tile_blocks"] * 128 * b + 24) > 112 * 1024
             cands = gbscan.batch_shape_candidates(b, br)
-            assert cands and max(c["warps"] for c in cands) > 8
+            assert cands and max(c["warps"] for c in cands) <= 8 and min(c["warps"] for c in cands) == 4
             for c in cands:
                 assert c["vote_rows"] == 0 and c["tile_blocks"] % step == 0 and c["tile_blocks"] <= 64
-                assert c["warps"] * c["stages"] * (c["tile_blocks"] * 128 * b + 24) <= 226 * 1024
+                assert c["warps"] * c["stages"] * (c["tile_blocks"] * 128 * b + 24) <= 112 * 1024
+    assert [gbscan.batch_shape_get(b)["warps"] for b in (1, 13, 14, 16, 27, 28, 32)] == [8, 8, 7, 6, 8, 7, 6]
     with pytest.raises(gbscan.ScanError) as e:
         gbscan.batch_shape_set(9, False, dict(warps=8, stages=2, tile_blocks=4, vote_rows=1))
     assert "row vote" in str(e.value)
