@@ -671,6 +671,8 @@ def summarise(plain, probes, zone, select, layouts, conj, batched, serving, beta
         pl = batched["plans"]
         out["batch_ms"] = [batched["ms_per_column_graph"], pl["law"]["ms"], pl["planned_mlp"]["ms"],
                            all(v["exact"] for v in pl.values())]
+        if "frac_of_law" in pl["law"]:
+            out["batch_frac_law"] = [pl["law"]["frac_of_law"], pl["branchfree"]["frac_of_law"]]
         if batched.get("autotune"):
             out["batch_tune_gain"] = batched["autotune"]["gain"]
         if batched.get("planner_vs_law"):
@@ -1121,6 +1123,29 @@ BATCH_WORKLOAD = ("batched: 4096 columns, lengths log-uniform in [2^10, 2^26] sc
 TRAIN_COLS = 120
 
 
+def batch_law_bounds(spec, strategies, blocks, beta_gbs, t_dec_gvals):
+    """The bandwidth law's two bounds on a batch plan, in ms, from the blocks each column
+    actually read: per column bytes = blocks * 128 * b and values = min(n, 1024 * blocks), its
+    flavour's T_dec (t_dec_gvals[0] branch-free, [1] branchy).
+
+      summed: per (flavour, width) group max(bytes / beta, values / T_dec), summed over the
+              groups -- the law applied to each kernel of the replay on its own;
+      mixed:  max(all bytes / beta, sum over flavours of values / T_dec) -- the groups
+              overlapping perfectly, decode of some under the copies of others."""
+    beta = beta_gbs * 1e9
+    groups = {}
+    for (n, b, _, _), st, k in zip(spec, strategies, blocks):
+        fl = 1 if st in ("branchy", "zone_br") else 0
+        g = groups.setdefault((fl, b), [0.0, 0.0])
+        g[0] += float(k) * 128.0 * b
+        g[1] += float(min(n, 1024 * int(k)))
+    t = [x * 1e9 for x in t_dec_gvals]
+    summed = sum(max(B / beta, V / t[fl]) for (fl, _), (B, V) in groups.items())
+    by_bytes = sum(B for B, _ in groups.values()) / beta
+    by_decode = sum(V / t[fl] for (fl, _), (_, V) in groups.items())
+    return summed * 1e3, max(by_bytes, by_decode) * 1e3
+
+
 def run_batched(args, dev, stream, gbscan, beta_gbs, t_dec_gvals):
     """4096-column batch: one planned graph launch vs one plain launch per column.
 
@@ -1261,7 +1286,10 @@ def run_batched(args, dev, stream, gbscan, beta_gbs, t_dec_gvals):
         exact = bool((got[:, :2] == want[:, :2]).all())
         ms = time_calls(lambda: bt.run(parr, stream=stream, dev_out=res_b, host=False), 7)
         mix = {k: strategies.count(k) for k in plmod.STRATEGIES if strategies.count(k)}
+        law_ms, mix_ms = batch_law_bounds(spec, strategies, got[:, 2], beta_gbs, t_dec_gvals)
         out[name] = {"ms": round(ms, 4), "exact": exact, "strategy_mix": mix,
+                     "law_bound_ms": round(law_ms, 4), "mixed_bound_ms": round(mix_ms, 4),
+                     "frac_of_law": round(law_ms / ms, 3), "frac_of_mixed": round(mix_ms / ms, 3),
                      "speedup_vs_per_column_graph": round(ms_graph / ms, 2),
                      "speedup_vs_per_column_loop": round(ms_loop / ms, 2),
                      "gbs": round(total_bytes / (ms * 1e-3) / 1e9, 1),

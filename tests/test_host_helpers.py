@@ -83,7 +83,7 @@ def test_headline_line_stays_small_with_every_section_present():
         "conj": {"rows": [{"frac_conj": 0.77} for _ in range(4)]},
         "tune": {"sweep_gain": 1.097},
         "batched": {"ms_per_column_graph": 23.7, "plans": {
-            k: {"ms": 0.97, "speedup_vs_per_column_graph": 24.4, "exact": True}
+            k: {"ms": 0.97, "speedup_vs_per_column_graph": 24.4, "exact": True, "frac_of_law": 0.712}
             for k in ("branchfree", "law", "planned_mlp", "law_calibrated", "planned_mlp_law_prior")},
             "planner_vs_law": {"min": 0.99, "median": 1.01, "max": 1.03}},
         "serving": {"serial": {"qps": 3200.0}, "loads": [
@@ -103,3 +103,20 @@ def test_headline_line_stays_small_with_every_section_present():
     assert line["roofline"]["frac"] == 0.94 and line["cpu_baseline"]["kind"] == "oracle"
     assert line["summary"]["neg_ctrl_iii"] is True and line["summary"]["tune_gain"] > 1
     assert line["gpu_launches"] == 384 * 20
+
+
+def test_batch_law_bounds_on_a_hand_computed_plan():
+    """The batch plan's two law bounds from the blocks each column read, against values worked
+    out by hand (beta 2 GB/s; T_dec 2 G values/s branch-free, 1 G branchy)."""
+    import bench
+
+    spec = [(4096, 4, None, 0.1), (2048, 4, None, 0.1), (3000, 32, None, 0.1), (1024, 8, None, 0.1)]
+    strategies = ["branchfree", "zone_bf", "branchfree", "branchy"]
+    blocks = [4, 1, 3, 1]                  # the zone skip read 1 of its 2 blocks
+    summed, mixed = bench.batch_law_bounds(spec, strategies, blocks, 2.0, [2.0, 1.0])
+    # (bf, 4): 2560 B, 5120 values -> max(1.28, 2.56) us; (bf, 32): 12288 B, 3000 values (the
+    # tail block holds 952) -> max(6.144, 1.5) us; (branchy, 8): 1024 B, 1024 values -> 1.024 us
+    assert summed == pytest.approx((2.56 + 6.144 + 1.024) * 1e-3, rel=1e-12)
+    # all bytes 15872 / 2e9 = 7.936 us against decode 8120 / 2e9 + 1024 / 1e9 = 5.084 us
+    assert mixed == pytest.approx(7.936e-3, rel=1e-12)
+    assert mixed <= summed
