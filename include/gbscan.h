@@ -575,7 +575,10 @@ scan_status scan_launch_shape(uint32_t b, uint32_t *sms, uint32_t *ctas, uint32_
  * SM of `warps` warps; each warp streams tiles of `tile_blocks` 1024-value
  * blocks through `stages` shared-memory slots (the zone-skip kernels pop
  * `tile_blocks` candidate blocks at a time); vote_rows = 1 makes the branchy
- * kernel vote once per row of a thread's lanes instead of once per value;
+ * kernel vote once per row of a thread's lanes instead of once per value, and
+ * vote_rows = 2 does the same with each row written as one PTX block (tests
+ * OR-ed into one predicate, one vote, one uniform branch), vote_rows = 3 with
+ * two rows per block (both rows' tests and votes before either branch);
  * vec_lanes is how many lanes a thread reads as one vector per row: 0 (the
  * width's default: 4 for b <= 16, else 2) or 2 for full scans at b = 9..16,
  * whose smaller warp step lets 16 warps fit.  Legal shapes: full scans 1..16

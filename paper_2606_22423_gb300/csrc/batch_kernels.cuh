@@ -155,6 +155,11 @@ __global__ void __launch_bounds__(512, 1) k_scan_batch(const BatchParams P)
     bool exhausted = false;
     uint32_t phase = 0;  // bit s: parity of slot s's next completion
     uint32_t pc_id = ~0u, next_begin = 0;
+    // zone skipping: blocks [zs_begin, zs_end) of column zs_col are known to hold no
+    // survivor (found by a look-ahead read of zone entries), so tiles inside
+    // that run are skipped without loading their entries again
+    uint32_t zs_col = ~0u;
+    uint64_t zs_begin = 0, zs_end = 0;
     const uint32_t* pc_packed = nullptr;
     const uint2* pc_zm = nullptr;
     uint64_t pc_n = 0, pc_zlo = 0, pc_zhi = 0;
@@ -219,17 +224,36 @@ __global__ void __launch_bounds__(512, 1) k_scan_batch(const BatchParams P)
         if (pc_flags & kColEmpty) {
             keep = 0;
         } else if (pc_flags & kColZone) {
-            uint64_t km = 0;
-            for (uint32_t base_i = 0; base_i < nb; base_i += 32u) {
-                const uint32_t i = base_i + lane;
+            if (zs_col == pc_id && k0 >= zs_begin && k0 + nb <= zs_end) {
+                keep = 0;  // inside a run already known to hold no survivor
+            } else if (nb < 32u) {
+                // one load covers this tile and the blocks after it, up to 32
+                const uint64_t span = nblocks - k0 < 32u ? nblocks - k0 : 32u;
                 bool k = false;
-                if (i < nb) {
-                    const uint2 z = __ldg(&pc_zm[k0 + i]);
+                if (lane < span) {
+                    const uint2 z = __ldg(&pc_zm[k0 + lane]);
                     k = static_cast<uint64_t>(z.y) >= pc_zlo && static_cast<uint64_t>(z.x) < pc_zhi;
                 }
-                km |= static_cast<uint64_t>(__ballot_sync(kFull, k)) << base_i;
+                const uint32_t m32 = __ballot_sync(kFull, k);
+                keep = m32 & ((1u << nb) - 1u);
+                if (!keep) {  // no survivor up to the first one found (or the whole span)
+                    zs_col = pc_id;
+                    zs_begin = k0;
+                    zs_end = k0 + (m32 ? static_cast<uint64_t>(__ffs(static_cast<int>(m32)) - 1) : span);
+                }
+            } else {
+                uint64_t km = 0;
+                for (uint32_t base_i = 0; base_i < nb; base_i += 32u) {
+                    const uint32_t i = base_i + lane;
+                    bool k = false;
+                    if (i < nb) {
+                        const uint2 z = __ldg(&pc_zm[k0 + i]);
+                        k = static_cast<uint64_t>(z.y) >= pc_zlo && static_cast<uint64_t>(z.x) < pc_zhi;
+                    }
+                    km |= static_cast<uint64_t>(__ballot_sync(kFull, k)) << base_i;
+                }
+                keep = km;
             }
-            keep = km;
         }
         const uint32_t nk = static_cast<uint32_t>(__popcll(keep));
         if (lane == 0) {

@@ -50,20 +50,25 @@ cudaError_t launch_full(const ScanParams& p, const LaunchShape& sh, int grid, cu
     if constexpr (B >= 9 && B <= 16) {  // the 2-lane geometry: 16-warp bound only
         if (sh.vec_lanes == 2) {
             if constexpr (BRANCHY) {
-                if (sh.vote_rows) return launch_one<B, k_scan_full<B, true, kLayLanes, 16, true, 2>>(p, sh, grid, st);
+                if (sh.vote_rows == 3) return launch_one<B, k_scan_full<B, true, kLayLanes, 16, 3, 2>>(p, sh, grid, st);
+                if (sh.vote_rows == 2) return launch_one<B, k_scan_full<B, true, kLayLanes, 16, 2, 2>>(p, sh, grid, st);
+                if (sh.vote_rows) return launch_one<B, k_scan_full<B, true, kLayLanes, 16, 1, 2>>(p, sh, grid, st);
             }
-            return launch_one<B, k_scan_full<B, BRANCHY, kLayLanes, 16, false, 2>>(p, sh, grid, st);
+            return launch_one<B, k_scan_full<B, BRANCHY, kLayLanes, 16, 0, 2>>(p, sh, grid, st);
         }
     }
     if (sh.vec_lanes != 0 && sh.vec_lanes != default_lpt(B)) return cudaErrorInvalidValue;
     const bool w16 = sh.warps > 8;
     if constexpr (BRANCHY && B <= 21) {
+        // the PTX row vote: the 16-warp bound only (any CTA up to 16 warps)
+        if (sh.vote_rows == 3) return launch_one<B, k_scan_full<B, true, kLayLanes, 16, 3>>(p, sh, grid, st);
+        if (sh.vote_rows == 2) return launch_one<B, k_scan_full<B, true, kLayLanes, 16, 2>>(p, sh, grid, st);
         if (sh.vote_rows)
-            return w16 ? launch_one<B, k_scan_full<B, true, kLayLanes, 16, true>>(p, sh, grid, st)
-                       : launch_one<B, k_scan_full<B, true, kLayLanes, 8, true>>(p, sh, grid, st);
+            return w16 ? launch_one<B, k_scan_full<B, true, kLayLanes, 16, 1>>(p, sh, grid, st)
+                       : launch_one<B, k_scan_full<B, true, kLayLanes, 8, 1>>(p, sh, grid, st);
     }
-    return w16 ? launch_one<B, k_scan_full<B, BRANCHY, kLayLanes, 16, false>>(p, sh, grid, st)
-               : launch_one<B, k_scan_full<B, BRANCHY, kLayLanes, 8, false>>(p, sh, grid, st);
+    return w16 ? launch_one<B, k_scan_full<B, BRANCHY, kLayLanes, 16, 0>>(p, sh, grid, st)
+               : launch_one<B, k_scan_full<B, BRANCHY, kLayLanes, 8, 0>>(p, sh, grid, st);
 }
 
 template <int B>

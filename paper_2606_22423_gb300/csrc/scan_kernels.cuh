@@ -351,6 +351,150 @@ __device__ __forceinline__ void acc2(uint32_t& c, uint64_t& s, uint32_t ui, cons
             : "+r"(c), "+l"(s) : "r"(ui), "r"(L.negloi), "r"(L.wm1), "r"(L.one));
 }
 
+// One branchy row of mode 0 (packed accumulators) as a single PTX block: the
+// thread's kLpt tests t = u - lo' <= w - 1 (subtract on the FMA pipe unless
+// the field was extracted there, TOP), OR-ed into one predicate, one warp vote,
+// and a uniform branch that skips the kLpt predicated adds when no lane of the
+// warp matches anywhere in the row.
+template <bool TOP, int LPT>
+__device__ __forceinline__ void branchy_row(uint32_t (&a)[LPT], const uint32_t (&u)[LPT], const Lanes& L);
+
+template <>
+__device__ __forceinline__ void branchy_row<true, 4>(uint32_t (&a)[4], const uint32_t (&u)[4], const Lanes& L)
+{
+    asm volatile(
+        "{\n\t.reg .pred p0, p1, p2, p3, q;\n\t.reg .b32 t0, t1, t2, t3;\n\t"
+        "sub.u32 t0, %4, %8;\n\tsub.u32 t1, %5, %8;\n\tsub.u32 t2, %6, %8;\n\tsub.u32 t3, %7, %8;\n\t"
+        "setp.le.u32 p0, t0, %9;\n\tsetp.le.u32 p1, t1, %9;\n\t"
+        "setp.le.u32 p2, t2, %9;\n\tsetp.le.u32 p3, t3, %9;\n\t"
+        "or.pred q, p0, p1;\n\tor.pred q, q, p2;\n\tor.pred q, q, p3;\n\t"
+        "vote.sync.any.pred q, q, 0xffffffff;\n\t"
+        "@!q bra.uni BR_SKIP;\n\t"
+        "@p0 add.u32 %0, %0, %4;\n\t@p1 add.u32 %1, %1, %5;\n\t"
+        "@p2 add.u32 %2, %2, %6;\n\t@p3 add.u32 %3, %3, %7;\n\t"
+        "BR_SKIP:\n\t}"
+        : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3])
+        : "r"(u[0]), "r"(u[1]), "r"(u[2]), "r"(u[3]), "r"(L.loi), "r"(L.wm1));
+}
+template <>
+__device__ __forceinline__ void branchy_row<false, 4>(uint32_t (&a)[4], const uint32_t (&u)[4], const Lanes& L)
+{
+    asm volatile(
+        "{\n\t.reg .pred p0, p1, p2, p3, q;\n\t.reg .b32 t0, t1, t2, t3;\n\t"
+        "mad.lo.u32 t0, %4, %10, %8;\n\tmad.lo.u32 t1, %5, %10, %8;\n\t"
+        "mad.lo.u32 t2, %6, %10, %8;\n\tmad.lo.u32 t3, %7, %10, %8;\n\t"
+        "setp.le.u32 p0, t0, %9;\n\tsetp.le.u32 p1, t1, %9;\n\t"
+        "setp.le.u32 p2, t2, %9;\n\tsetp.le.u32 p3, t3, %9;\n\t"
+        "or.pred q, p0, p1;\n\tor.pred q, q, p2;\n\tor.pred q, q, p3;\n\t"
+        "vote.sync.any.pred q, q, 0xffffffff;\n\t"
+        "@!q bra.uni BR_SKIP;\n\t"
+        "@p0 mad.lo.u32 %0, %4, %10, %0;\n\t@p1 mad.lo.u32 %1, %5, %10, %1;\n\t"
+        "@p2 mad.lo.u32 %2, %6, %10, %2;\n\t@p3 mad.lo.u32 %3, %7, %10, %3;\n\t"
+        "BR_SKIP:\n\t}"
+        : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3])
+        : "r"(u[0]), "r"(u[1]), "r"(u[2]), "r"(u[3]), "r"(L.negloi), "r"(L.wm1), "r"(L.one));
+}
+template <>
+__device__ __forceinline__ void branchy_row<true, 2>(uint32_t (&a)[2], const uint32_t (&u)[2], const Lanes& L)
+{
+    asm volatile(
+        "{\n\t.reg .pred p0, p1, q;\n\t.reg .b32 t0, t1;\n\t"
+        "sub.u32 t0, %2, %4;\n\tsub.u32 t1, %3, %4;\n\t"
+        "setp.le.u32 p0, t0, %5;\n\tsetp.le.u32 p1, t1, %5;\n\t"
+        "or.pred q, p0, p1;\n\t"
+        "vote.sync.any.pred q, q, 0xffffffff;\n\t"
+        "@!q bra.uni BR_SKIP;\n\t"
+        "@p0 add.u32 %0, %0, %2;\n\t@p1 add.u32 %1, %1, %3;\n\t"
+        "BR_SKIP:\n\t}"
+        : "+r"(a[0]), "+r"(a[1])
+        : "r"(u[0]), "r"(u[1]), "r"(L.loi), "r"(L.wm1));
+}
+template <>
+__device__ __forceinline__ void branchy_row<false, 2>(uint32_t (&a)[2], const uint32_t (&u)[2], const Lanes& L)
+{
+    asm volatile(
+        "{\n\t.reg .pred p0, p1, q;\n\t.reg .b32 t0, t1;\n\t"
+        "mad.lo.u32 t0, %2, %6, %4;\n\tmad.lo.u32 t1, %3, %6, %4;\n\t"
+        "setp.le.u32 p0, t0, %5;\n\tsetp.le.u32 p1, t1, %5;\n\t"
+        "or.pred q, p0, p1;\n\t"
+        "vote.sync.any.pred q, q, 0xffffffff;\n\t"
+        "@!q bra.uni BR_SKIP;\n\t"
+        "@p0 mad.lo.u32 %0, %2, %6, %0;\n\t@p1 mad.lo.u32 %1, %3, %6, %1;\n\t"
+        "BR_SKIP:\n\t}"
+        : "+r"(a[0]), "+r"(a[1])
+        : "r"(u[0]), "r"(u[1]), "r"(L.negloi), "r"(L.wm1), "r"(L.one));
+}
+
+// Two branchy rows of mode 0 as one PTX block (ROWVOTE = 3): both rows' tests
+// and both votes come before the first branch, so the scheduler has 2 * kLpt
+// independent tests and two votes in one basic block; then, per row, a uniform
+// branch around its predicated adds.  Operands: %0.. the kLpt accumulators,
+// then the row-A codes, the row-B codes, lo', -lo', w - 1, an opaque 1.
+#define GB_BR_SUB_ALU(t, u, LOI, NLOI, ONE) "sub.u32 " t ", " u ", " LOI ";\n\t"
+#define GB_BR_SUB_FMA(t, u, LOI, NLOI, ONE) "mad.lo.u32 " t ", " u ", " ONE ", " NLOI ";\n\t"
+#define GB_BR_ADD_ALU(p, a, u, ONE) "@" p " add.u32 " a ", " a ", " u ";\n\t"
+#define GB_BR_ADD_FMA(p, a, u, ONE) "@" p " mad.lo.u32 " a ", " u ", " ONE ", " a ";\n\t"
+#define GB_BR_TWO_ROWS4(SUBA, ADDA, SUBB, ADDB)                                                           \
+    asm volatile("{\n\t.reg .pred pa0, pa1, pa2, pa3, pb0, pb1, pb2, pb3, qa, qb;\n\t"                     \
+                 ".reg .b32 ta0, ta1, ta2, ta3, tb0, tb1, tb2, tb3;\n\t"                                  \
+                 SUBA("ta0", "%4", "%12", "%13", "%15") SUBA("ta1", "%5", "%12", "%13", "%15")            \
+                 SUBA("ta2", "%6", "%12", "%13", "%15") SUBA("ta3", "%7", "%12", "%13", "%15")            \
+                 SUBB("tb0", "%8", "%12", "%13", "%15") SUBB("tb1", "%9", "%12", "%13", "%15")            \
+                 SUBB("tb2", "%10", "%12", "%13", "%15") SUBB("tb3", "%11", "%12", "%13", "%15")          \
+                 "setp.le.u32 pa0, ta0, %14;\n\tsetp.le.u32 pa1, ta1, %14;\n\t"                           \
+                 "setp.le.u32 pa2, ta2, %14;\n\tsetp.le.u32 pa3, ta3, %14;\n\t"                           \
+                 "setp.le.u32 pb0, tb0, %14;\n\tsetp.le.u32 pb1, tb1, %14;\n\t"                           \
+                 "setp.le.u32 pb2, tb2, %14;\n\tsetp.le.u32 pb3, tb3, %14;\n\t"                           \
+                 "or.pred qa, pa0, pa1;\n\tor.pred qa, qa, pa2;\n\tor.pred qa, qa, pa3;\n\t"              \
+                 "or.pred qb, pb0, pb1;\n\tor.pred qb, qb, pb2;\n\tor.pred qb, qb, pb3;\n\t"              \
+                 "vote.sync.any.pred qa, qa, 0xffffffff;\n\tvote.sync.any.pred qb, qb, 0xffffffff;\n\t"  \
+                 "@!qa bra.uni BR_SKIP_A;\n\t"                                                            \
+                 ADDA("pa0", "%0", "%4", "%15") ADDA("pa1", "%1", "%5", "%15")                            \
+                 ADDA("pa2", "%2", "%6", "%15") ADDA("pa3", "%3", "%7", "%15")                            \
+                 "BR_SKIP_A:\n\t@!qb bra.uni BR_SKIP_B;\n\t"                                              \
+                 ADDB("pb0", "%0", "%8", "%15") ADDB("pb1", "%1", "%9", "%15")                            \
+                 ADDB("pb2", "%2", "%10", "%15") ADDB("pb3", "%3", "%11", "%15")                          \
+                 "BR_SKIP_B:\n\t}"                                                                        \
+                 : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3])                                         \
+                 : "r"(ua[0]), "r"(ua[1]), "r"(ua[2]), "r"(ua[3]), "r"(ub[0]), "r"(ub[1]), "r"(ub[2]),   \
+                   "r"(ub[3]), "r"(L.loi), "r"(L.negloi), "r"(L.wm1), "r"(L.one))
+#define GB_BR_TWO_ROWS2(SUBA, ADDA, SUBB, ADDB)                                                           \
+    asm volatile("{\n\t.reg .pred pa0, pa1, pb0, pb1, qa, qb;\n\t.reg .b32 ta0, ta1, tb0, tb1;\n\t"       \
+                 SUBA("ta0", "%2", "%6", "%7", "%9") SUBA("ta1", "%3", "%6", "%7", "%9")                  \
+                 SUBB("tb0", "%4", "%6", "%7", "%9") SUBB("tb1", "%5", "%6", "%7", "%9")                  \
+                 "setp.le.u32 pa0, ta0, %8;\n\tsetp.le.u32 pa1, ta1, %8;\n\t"                             \
+                 "setp.le.u32 pb0, tb0, %8;\n\tsetp.le.u32 pb1, tb1, %8;\n\t"                             \
+                 "or.pred qa, pa0, pa1;\n\tor.pred qb, pb0, pb1;\n\t"                                     \
+                 "vote.sync.any.pred qa, qa, 0xffffffff;\n\tvote.sync.any.pred qb, qb, 0xffffffff;\n\t"  \
+                 "@!qa bra.uni BR_SKIP_A;\n\t"                                                            \
+                 ADDA("pa0", "%0", "%2", "%9") ADDA("pa1", "%1", "%3", "%9")                              \
+                 "BR_SKIP_A:\n\t@!qb bra.uni BR_SKIP_B;\n\t"                                              \
+                 ADDB("pb0", "%0", "%4", "%9") ADDB("pb1", "%1", "%5", "%9")                              \
+                 "BR_SKIP_B:\n\t}"                                                                        \
+                 : "+r"(a[0]), "+r"(a[1])                                                                 \
+                 : "r"(ua[0]), "r"(ua[1]), "r"(ub[0]), "r"(ub[1]), "r"(L.loi), "r"(L.negloi), "r"(L.wm1), \
+                   "r"(L.one))
+
+// TOPA / TOPB: the row's fields sit at the top of their words (extracted on
+// the FMA pipe), so its subtract and add go to the ALU.
+template <bool TOPA, bool TOPB, int LPT>
+__device__ __forceinline__ void branchy_two_rows(uint32_t (&a)[LPT], const uint32_t (&ua)[LPT],
+                                                 const uint32_t (&ub)[LPT], const Lanes& L)
+{
+    if constexpr (LPT == 4) {
+        if constexpr (TOPA && TOPB) GB_BR_TWO_ROWS4(GB_BR_SUB_ALU, GB_BR_ADD_ALU, GB_BR_SUB_ALU, GB_BR_ADD_ALU);
+        else if constexpr (TOPA) GB_BR_TWO_ROWS4(GB_BR_SUB_ALU, GB_BR_ADD_ALU, GB_BR_SUB_FMA, GB_BR_ADD_FMA);
+        else if constexpr (TOPB) GB_BR_TWO_ROWS4(GB_BR_SUB_FMA, GB_BR_ADD_FMA, GB_BR_SUB_ALU, GB_BR_ADD_ALU);
+        else GB_BR_TWO_ROWS4(GB_BR_SUB_FMA, GB_BR_ADD_FMA, GB_BR_SUB_FMA, GB_BR_ADD_FMA);
+    } else {
+        static_assert(LPT == 2, "two-row blocks are written for 2 or 4 lanes per thread");
+        if constexpr (TOPA && TOPB) GB_BR_TWO_ROWS2(GB_BR_SUB_ALU, GB_BR_ADD_ALU, GB_BR_SUB_ALU, GB_BR_ADD_ALU);
+        else if constexpr (TOPA) GB_BR_TWO_ROWS2(GB_BR_SUB_ALU, GB_BR_ADD_ALU, GB_BR_SUB_FMA, GB_BR_ADD_FMA);
+        else if constexpr (TOPB) GB_BR_TWO_ROWS2(GB_BR_SUB_FMA, GB_BR_ADD_FMA, GB_BR_SUB_ALU, GB_BR_ADD_ALU);
+        else GB_BR_TWO_ROWS2(GB_BR_SUB_FMA, GB_BR_ADD_FMA, GB_BR_SUB_FMA, GB_BR_ADD_FMA);
+    }
+}
+
 // One block, this thread's 4 lanes x 32 rows, every value valid.
 // Accumulators stay 32-bit inside the block:
 //   B <= 21: one word per lane packs (count << (B+5)) + sum  (mode 0);
@@ -358,11 +502,14 @@ __device__ __forceinline__ void acc2(uint32_t& c, uint64_t& s, uint32_t ui, cons
 //   else   : a 64-bit sum plus a count                       (mode 2).
 // BRANCHY adds a warp vote and skips the aggregation when no value of the
 // voting group matches.  The group is one value per thread (32 values) by
-// default; with ROWVOTE it is a whole row of the thread's kLpt lanes (32 * kLpt
-// values over kLpt blocks): one vote per kLpt values, but all kLpt tests must
-// be held across the vote.  Which form is faster depends on the width and on
-// how many warps share an SM (the autotuner picks per width).
-template <int B, bool BRANCHY, bool ROWVOTE = false, int LPT = default_lpt(B)>
+// default (ROWVOTE = 0); with ROWVOTE = 1 or 2 it is a whole row of the
+// thread's kLpt lanes (32 * kLpt values over kLpt blocks): one vote per kLpt
+// values, but all kLpt tests must be held across the vote.  ROWVOTE = 2 writes
+// the row as one PTX block (branchy_row): tests combined by or.pred, one
+// vote.sync.any, one uniform branch around the predicated adds.  Which form is
+// faster depends on the width and on how many warps share an SM (the
+// autotuner picks per width).
+template <int B, bool BRANCHY, int ROWVOTE = 0, int LPT = default_lpt(B)>
 __device__ __forceinline__ void agg_block(const typename Geo<B, LPT>::Vec* rows, const Lanes& L,
                                           uint64_t& cnt, uint64_t& sum)
 {
@@ -375,7 +522,29 @@ __device__ __forceinline__ void agg_block(const typename Geo<B, LPT>::Vec* rows,
     uint64_t s64 = 0u;
 #pragma unroll
     for (int r = 0; r < 32; ++r) {
-        if constexpr (BRANCHY && ROWVOTE) {
+        if constexpr (BRANCHY && ROWVOTE == 3) {
+            static_assert(kMode == 0 && (kLpt == 2 || kLpt == 4), "the PTX row vote is written for mode 0");
+            if ((r & 1) == 0) {  // rows r and r + 1 (32 rows: always a pair)
+                uint32_t ua[kLpt], ub[kLpt];
+#pragma unroll
+                for (int k = 0; k < kLpt; ++k) {
+                    ua[k] = field_add<B, LPT>(W, r, k, L);
+                    ub[k] = field_add<B, LPT>(W, r + 1, k, L);
+                }
+                const bool ta = top_field<B>(r), tb = top_field<B>(r + 1);  // folded after unrolling
+                if (ta && tb) branchy_two_rows<true, true, kLpt>(a, ua, ub, L);
+                else if (ta) branchy_two_rows<true, false, kLpt>(a, ua, ub, L);
+                else if (tb) branchy_two_rows<false, true, kLpt>(a, ua, ub, L);
+                else branchy_two_rows<false, false, kLpt>(a, ua, ub, L);
+            }
+        } else if constexpr (BRANCHY && ROWVOTE == 2) {
+            static_assert(kMode == 0 && (kLpt == 2 || kLpt == 4), "the PTX row vote is written for mode 0");
+            uint32_t ui[kLpt];
+#pragma unroll
+            for (int k = 0; k < kLpt; ++k) ui[k] = field_add<B, LPT>(W, r, k, L);
+            if (top_field<B>(r)) branchy_row<true, kLpt>(a, ui, L);  // folded after unrolling
+            else branchy_row<false, kLpt>(a, ui, L);
+        } else if constexpr (BRANCHY && ROWVOTE == 1) {
             // subtract on the FMA pipe unless the extraction already used it
             const bool top = top_field<B>(r);
             uint32_t ui[kLpt];
@@ -685,7 +854,7 @@ __device__ __forceinline__ void scan_tail_layout(const ScanParams& p, int lane, 
 }
 
 // All `nb` blocks of a staged tile (blocks are contiguous in the slot).
-template <int B, bool BRANCHY, bool ROWVOTE = false, int LPT = default_lpt(B)>
+template <int B, bool BRANCHY, int ROWVOTE = 0, int LPT = default_lpt(B)>
 __device__ __forceinline__ void scan_tile(const unsigned char* tile, uint32_t nb, int lane,
                                           const Lanes& L, uint32_t lo, uint32_t wm1, uint64_t& cnt,
                                           uint64_t& sum)
@@ -803,7 +972,7 @@ __device__ __forceinline__ void scan_tail(const ScanParams& p, int lane, uint64_
 // to warp t mod (all warps), numbered warp-major, through the warp's ring of
 // slots.  Returns false when a bounded wait gave up (the warp's copies in
 // flight have landed by then and the status bit is set).
-template <int B, bool BRANCHY, int LAY, bool ROWVOTE, int LPT = default_lpt(B)>
+template <int B, bool BRANCHY, int LAY, int ROWVOTE, int LPT = default_lpt(B)>
 __device__ __forceinline__ bool walk_static(const ScanParams& p, const Pipe& P, int warp, int lane, int nwarps,
                                             uint64_t& cnt, uint64_t& sum)
 {
@@ -874,7 +1043,7 @@ __device__ __forceinline__ bool walk_static(const ScanParams& p, const Pipe& P, 
 // WMAX: the largest CTA the instantiation is compiled for (launch bound; 8
 // warps leave up to 255 registers per thread, 16 warps 128).  ROWVOTE: the
 // branchy vote group (see agg_block).  LPT: lanes per thread (see Geo).
-template <int B, bool BRANCHY, int LAY = kLayLanes, int WMAX = 8, bool ROWVOTE = false, int LPT = default_lpt(B)>
+template <int B, bool BRANCHY, int LAY = kLayLanes, int WMAX = 8, int ROWVOTE = 0, int LPT = default_lpt(B)>
 __global__ void __launch_bounds__(WMAX * 32, 1) k_scan_full(const ScanParams p)
 {
     extern __shared__ __align__(128) unsigned char smem[];

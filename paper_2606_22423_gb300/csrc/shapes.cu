@@ -110,7 +110,7 @@ bool shape_ok(int kind, int b, const gb::LaunchShape& s, const char** why)
     if (s.tile_blocks > (wide ? 64 : 32))
         return *why = wide ? "full and batched scans take at most 64 blocks per tile" : "zone-skip tiles hold at most 32 blocks",
                false;
-    if (s.vote_rows != 0 && s.vote_rows != 1) return *why = "vote_rows must be 0 or 1", false;
+    if (s.vote_rows < 0 || s.vote_rows > 3) return *why = "vote_rows must be 0, 1, 2 or 3", false;
     if (s.vote_rows && (kind != kKFullBR || b > 21))
         return *why = "the row vote applies to full branchy scans at b <= 21", false;
     if (smem_of(kind, b, s) > static_cast<uint32_t>(gb::kSmemMax))
@@ -134,7 +134,7 @@ std::vector<gb::LaunchShape> candidates(int kind, int b)
                                               : std::vector<int>{8};
     const std::vector<int> kbs = is_batch(kind) ? std::vector<int>{4, 6, 8, 12}
                                                 : std::vector<int>{2, 4, 6, 8, 12, 16, 24};
-    const int votes = (kind == kKFullBR && b <= 21) ? 2 : 1;
+    const int votes = (kind == kKFullBR && b <= 21) ? 4 : 1;
     const std::vector<int> stages = is_batch(kind) ? std::vector<int>{2, 3} : std::vector<int>{2, 3, 4};
     std::vector<gb::LaunchShape> out;
     for (int geo : geos) {

@@ -195,15 +195,18 @@ def test_trained_planner_beats_the_fixed_full_scan_on_clustered_low_selectivity_
     from paper_2606_22423_gb300 import planner as plmod
 
     s = torch.cuda.Stream()
-    tcols, tpreds = plmod.training_columns(seed=1, count=80, n_lo=1 << 22, n_hi=1 << 26, stream=s)
-    X, T = plmod.collect(tcols, tpreds, s, reps=2)
+    tcols, tpreds = plmod.training_columns(seed=1, count=160, n_lo=1 << 22, n_hi=1 << 26, stream=s)
+    X, T = plmod.collect(tcols, tpreds, s, reps=5)
     pl = gbscan.Planner(4, seed=3)
-    plmod.train(pl, X, T, steps=800, lr=3e-3)
-    # held-out batch: sorted columns, selective predicates -> zone skipping should win
+    plmod.train(pl, X, T, steps=1500, lr=3e-3)
+    # held-out batch: sorted columns, selective predicates -> zone skipping should win.  2^24
+    # values each, mid-range of the training lengths: at 2^22 a batched full scan costs only a
+    # few µs more than zone skipping, inside the labels' noise, and the network's picks there
+    # varied from run to run
     cols, preds = [], []
     with torch.cuda.stream(s):
         for i in range(64):
-            b, n = 8 + (i % 20), 1 << 22
+            b, n = 8 + (i % 20), 1 << 24
             c = gbscan.Column.from_device(synth.clustered_values_device(500 + i, n, b, 0.0), n, b, stream=s)
             c.zonemap_build(s)
             cols.append(c)

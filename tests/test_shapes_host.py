@@ -34,7 +34,7 @@ def legal(kind, b, s):
     return (1 <= s["warps"] <= (16 if full else 8) and 1 <= s["stages"] <= 6
             and s["tile_blocks"] >= step and s["tile_blocks"] % step == 0
             and s["tile_blocks"] <= (64 if full else 32)
-            and (s["vote_rows"] == 0 or (kind == "branchy" and b <= 21 and s["vote_rows"] == 1))
+            and (s["vote_rows"] == 0 or (kind == "branchy" and b <= 21 and s["vote_rows"] in (1, 2, 3)))
             and smem <= 226 * 1024)
 
 
@@ -51,7 +51,7 @@ def test_candidates_are_legal_and_include_more_warps_and_vote_forms(kind):
         if kind in ("branchfree", "branchy"):
             assert max(c["warps"] for c in cands) > 8
         if kind == "branchy" and b <= 21:
-            assert {c["vote_rows"] for c in cands} == {0, 1}
+            assert {c["vote_rows"] for c in cands} == {0, 1, 2, 3}
         if kind in ("branchfree", "branchy") and 9 <= b <= 16:       # the 2-lane geometry with 16 warps
             assert any(c["vec_lanes"] == 2 and c["warps"] == 16 for c in cands)
         else:
@@ -67,6 +67,9 @@ def test_illegal_shapes_are_refused_with_the_rule():
              (1, "zone_bf", dict(warps=8, stages=3, tile_blocks=36), "at most 32"),
              (8, "branchfree", dict(warps=8, stages=3, tile_blocks=8, vote_rows=1), "row vote"),
              (24, "branchy", dict(warps=8, stages=3, tile_blocks=2, vote_rows=1), "row vote"),
+             (22, "branchy", dict(warps=16, stages=2, tile_blocks=2, vote_rows=2), "row vote"),
+             (8, "branchfree", dict(warps=16, stages=2, tile_blocks=4, vote_rows=2), "row vote"),
+             (8, "branchy", dict(warps=16, stages=2, tile_blocks=4, vote_rows=4), "0, 1, 2 or 3"),
              (32, "branchfree", dict(warps=16, stages=4, tile_blocks=2), "226 KB"),
              (8, "branchfree", dict(warps=16, stages=2, tile_blocks=4, vec_lanes=2), "vec_lanes"),
              (12, "zone_bf", dict(warps=8, stages=2, tile_blocks=4, vec_lanes=2), "vec_lanes"),
