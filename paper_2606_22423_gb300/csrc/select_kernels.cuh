@@ -523,7 +523,8 @@ __global__ void __launch_bounds__(kSelWarps * 32, 1) k_select(const SelectParams
             uint32_t off = base + before;
             for (int w = 0; w < warp; ++w) off += cc[w];
             const uint64_t blk0 = tile_of(wi * S::kM) * S::kTB;  // the iteration's blocks are consecutive
-            if (blk0 < nblocks && off < p.capacity) {
+            // a warp with no match in the iteration skips the transposes and scans
+            if (cc[warp] != 0u && blk0 < nblocks && off < p.capacity) {
                 const uint32_t* mk = masks + (wi % (kSelLag + 1)) * S::kIB * 32;
                 const uint64_t left = nblocks - blk0;
                 const uint32_t nb = left < S::kIB ? static_cast<uint32_t>(left) : static_cast<uint32_t>(S::kIB);
