@@ -317,7 +317,7 @@ typedef struct scan_batch scan_batch; /* opaque: a planned batch of column scans
  * map (NULL = SCAN_BRANCHFREE for all; SCAN_AUTO counts as branch-free).
  * Zone-skip columns need a built zone map.  The columns must outlive the plan.
  * The first scan_batch_exec records the CUDA graph (copy descriptors, reset
- * results, kernels, copy results back) that later calls replay. */
+ * results, kernels) that later calls replay. */
 scan_status scan_batch_create(scan_column *const *cols, uint32_t ncols,
                               const scan_strategy *strategies, uint32_t tiles_per_pop,
                               void *stream, scan_batch **out);
@@ -325,7 +325,9 @@ scan_status scan_batch_create(scan_column *const *cols, uint32_t ncols,
 /* Run the plan with one predicate per column.  host_out (ncols results, may
  * be NULL) is filled after the stream is synchronised; dev_out (ncols results
  * in device memory, may be NULL) is written asynchronously.  Results equal
- * scan_run's bit for bit.  SCAN_ETIMEOUT if a bounded device wait gave up. */
+ * scan_run's bit for bit.  SCAN_ETIMEOUT if a bounded device wait gave up
+ * (reported here when host_out is given; a caller that asks for dev_out only
+ * checks scan_batch_status). */
 scan_status scan_batch_exec(scan_batch *batch, const scan_pred *preds, void *stream,
                             scan_result *host_out, scan_result *dev_out);
 
@@ -345,6 +347,13 @@ scan_status scan_batch_exec(scan_batch *batch, const scan_pred *preds, void *str
  * shapes.  Results are unaffected. */
 scan_status scan_batch_autotune(scan_batch *batch, const scan_pred *preds, uint32_t reps, void *stream,
                                 uint32_t *groups_tuned, float *rule_us, float *tuned_us);
+
+/* Status of the plan's last replay on `stream` (no paper counterpart: the
+ * error path of a bounded device wait): synchronises the stream and returns
+ * SCAN_ETIMEOUT if a device-side wait of that replay gave up, else SCAN_OK.
+ * For callers that run scan_batch_exec with dev_out only; the next replay
+ * clears the status. */
+scan_status scan_batch_status(scan_batch *batch, void *stream);
 
 /* Free the plan (synchronises the device first). */
 scan_status scan_batch_destroy(scan_batch *batch);

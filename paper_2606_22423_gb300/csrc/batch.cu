@@ -1,7 +1,8 @@
 // Host side of the batched scan: a plan lays out the tiles of many columns,
 // keeps a device descriptor table, and records one CUDA graph per plan:
-//   descriptors H2D -> reset results/counters -> branch-free batch kernel
-//   -> branchy batch kernel -> results D2H.
+//   descriptors H2D -> reset results/counters -> the width groups' kernels
+// (results are copied back to the host after the replay only when a caller
+// asks for host results).
 // Running the plan again with new predicates only rewrites the pinned
 // descriptor table and replays the graph.
 #include <cuda_runtime.h>
@@ -626,8 +627,6 @@ scan_status scan_batch_exec(scan_batch* bt, const scan_pred* preds, void* stream
             cudaEventRecord(bt->join[k], bt->branch[k]);
             cudaStreamWaitEvent(cs, bt->join[k], 0);
         }
-        cudaMemcpyAsync(bt->h_results, bt->d_results, res_words * sizeof(unsigned long long),
-                        cudaMemcpyDeviceToHost, cs);
         cudaGraph_t g = nullptr;
         const cudaError_t ec = cudaStreamEndCapture(cs, &g);
         if (ec != cudaSuccess || !g) return bcuda(ec != cudaSuccess ? ec : cudaErrorUnknown, "graph capture");
@@ -639,13 +638,29 @@ scan_status scan_batch_exec(scan_batch* bt, const scan_pred* preds, void* stream
     if (dev_out)
         BT_CUDA(cudaMemcpyAsync(dev_out, bt->d_results, 4ull * bt->ncols * sizeof(unsigned long long),
                                 cudaMemcpyDeviceToDevice, st));
-    if (host_out) {
+    if (host_out) {  // results and control words back to the host only when asked for
+        BT_CUDA(cudaMemcpyAsync(bt->h_results, bt->d_results, res_words * sizeof(unsigned long long),
+                                cudaMemcpyDeviceToHost, st));
         BT_CUDA(cudaStreamSynchronize(st));
         const unsigned int status = reinterpret_cast<const unsigned int*>(
             reinterpret_cast<const unsigned long long*>(bt->h_results) + 4ull * std::max<uint32_t>(1, bt->ncols))[kMaxGroups];
         if (status) return bfail(SCAN_ETIMEOUT, "a device-side wait timed out in the batch kernel");
         std::memcpy(host_out, bt->h_results, sizeof(scan_result) * bt->ncols);
     }
+    return SCAN_OK;
+}
+
+scan_status scan_batch_status(scan_batch* bt, void* stream)
+{
+    gb_set_last_error("");
+    if (!bt) return bfail(SCAN_EINVAL, "batch is NULL");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const unsigned long long* ctl = bt->d_results + 4ull * std::max<uint32_t>(1, bt->ncols);
+    unsigned long long* h_ctl = reinterpret_cast<unsigned long long*>(bt->h_results) + 4ull * std::max<uint32_t>(1, bt->ncols);
+    BT_CUDA(cudaMemcpyAsync(h_ctl, ctl, kCtlWords * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    BT_CUDA(cudaStreamSynchronize(st));
+    if (reinterpret_cast<const unsigned int*>(h_ctl)[kMaxGroups])
+        return bfail(SCAN_ETIMEOUT, "a device-side wait timed out in the batch kernel");
     return SCAN_OK;
 }
 

@@ -124,6 +124,7 @@ SIGNATURES = {
     "scan_batch_create": (_st, [_vp, _u32, _vp, _u32, _vp, ctypes.POINTER(_vp)]),
     "scan_batch_exec": (_st, [_vp, _vp, _vp, _vp, _vp]),
     "scan_batch_destroy": (_st, [_vp]),
+    "scan_batch_status": (_st, [_vp, _vp]),
     "scan_batch_run": (_st, [_vp, _vp, _u32, _vp, _vp, _vp]),
     "scan_batch_set_strategies": (_st, [_vp, _vp]),
     "scan_batch_features": (_st, [_vp, _vp, _vp, _vp]),
@@ -486,6 +487,10 @@ class Batch:
         out = (scan_result * max(n, 1))() if host else None
         _check(load().scan_batch_exec(self._h, pr, _stream(stream), out if host else None, _ptr(dev_out)))
         return [out[i] for i in range(n)] if host else None
+
+    def status(self, stream=None):
+        """Raise ScanError (SCAN_ETIMEOUT) if the last replay's device waits gave up."""
+        _check(load().scan_batch_status(self._h, _stream(stream)))
 
     def autotune(self, preds, reps: int = 3, stream=None) -> dict:
         """Tune the width groups' kernels on these predicates (scan_batch_autotune): groups

@@ -90,11 +90,16 @@ def test_batch_device_results_and_zone_requirement():
     preds = _preds(meta, 6)
     bt = gbscan.Batch(cols, ["zone_bf"] * 10)
     out = torch.zeros((10, 4), dtype=torch.int64, device="cuda")
-    bt.run(preds, dev_out=out, host=False)
-    torch.cuda.synchronize()
-    got = out.cpu().numpy()
-    for i, (v, (lo, hi)) in enumerate(zip(vals, preds)):
-        assert (int(got[i, 0]), int(got[i, 1])) == oracle.scan_values(v, lo, hi)
+    for _ in range(2):                      # device results only: nothing is copied to the host
+        bt.run(preds, dev_out=out, host=False)
+        bt.status()                         # syncs; no device wait gave up
+        got = out.cpu().numpy()
+        for i, (v, (lo, hi)) in enumerate(zip(vals, preds)):
+            assert (int(got[i, 0]), int(got[i, 1])) == oracle.scan_values(v, lo, hi)
+    # host results after device-only replays come from this replay
+    host = bt.run(_preds(meta, 7))
+    for i, (v, (lo, hi)) in enumerate(zip(vals, _preds(meta, 7))):
+        assert host[i].pair() == oracle.scan_values(v, lo, hi)
     bt.close()
     plain = gbscan.Column.from_host(vals[0], meta[0][0], meta[0][1])
     with pytest.raises(gbscan.ScanError):
