@@ -724,7 +724,7 @@ def run_zone_sweep(args, dev, stream, gbscan):
             for k, strat in enumerate(["branchfree", "zone_bf", "zone_agg_bf", "auto"]):
                 col.run_async(lo, hi, res[k], strat, stream)
                 vals = []
-                for _ in range(3):
+                for _ in range(7):                  # 25-330 us each: medians of 3 moved by 3-5%
                     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                     e0.record(stream)
                     col.run_async(lo, hi, res[k], strat, stream)
