@@ -1314,12 +1314,15 @@ struct ShapeInfo {
     int warps, stages, tile_blocks, smem_bytes;
 };
 
-// A runtime launch shape: one CTA per SM of `warps` warps, each with `stages`
-// slots of `tile_blocks` blocks (the zone-skip kernels take that many
-// candidates per tile); vote_rows picks the branchy vote group (full branchy
-// scans at b <= 21 only); vec_lanes = 2 the 2-lane geometry (full scans at
-// b = 9..16, compiled with the 16-warp bound).  Full scans take 8..16 warps (above 8 the 16-warp-bound
-// instantiation, <= 128 registers per thread); every other kernel 1..8.
+// A runtime launch shape: CTAs of `warps` warps (one per SM for single-column
+// scans, two for batched ones), each warp with `stages` slots of `tile_blocks`
+// blocks (the zone-skip kernels take that many candidates per tile); vote_rows
+// picks the branchy vote form (0 per value, 1 per row, 2 and 3 the PTX row
+// blocks; full branchy scans at b <= 21 only); vec_lanes = 2 the 2-lane
+// geometry (full scans at b = 9..16, compiled with the 16-warp bound).  Full
+// scans take 8..16 warps (above 8, and for vote forms 2 and 3, the
+// 16-warp-bound instantiation, <= 128 registers per thread); every other
+// single-column kernel 1..8.
 struct LaunchShape {
     int warps, stages, tile_blocks, vote_rows;
     int vec_lanes;  // lanes per thread and row (4 or 2; 0 = the width's default); full scans only

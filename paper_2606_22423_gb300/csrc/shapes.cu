@@ -8,7 +8,10 @@
 // trade differs with the width b: below the ridge the decode is issue-bound
 // and more warps hide its dependent chains; above it the copies bind and
 // deeper rings or larger tiles pay.  The branchy kernel adds a choice of vote
-// group (one value or one row of a thread's lanes per vote).
+// form (one value or one row of a thread's lanes per vote, the row as C++ or
+// as one PTX block of one or two rows).  Batched scans run two CTAs per SM
+// (one of each graph chain), so their shapes stay within half the SM's shared
+// memory.
 //
 // This unit keeps one shape per (kernel kind, b): the built-in rule until a
 // tuned shape is installed.  The tuner times every legal candidate on a
