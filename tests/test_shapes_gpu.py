@@ -107,3 +107,28 @@ def test_autotune_rejects_an_empty_predicate_and_keeps_the_old_shape():
     gbscan.autotune_reset()
     col.close()
     assert np.all(v < 1024)
+
+
+@pytest.mark.parametrize("b", [1, 4, 8, 13, 16, 24, 32])
+def test_single_slot_shapes_match_the_oracle(b):
+    """Single-slot rings (stages = 1, legal for any full scan) at several tile sizes and
+    warp counts, on a column of several tile rounds with a ragged tail: the oracle's
+    COUNT/SUM, every block read, both flavours."""
+    gbscan.autotune_reset()
+    step = 4 if b <= 16 else 2
+    base = min(77, (1 << 32) - (1 << b))
+    n = 200 * 1024 + 71
+    v = synth.uniform_values(synth.seed_for(92, b), n, b, base)
+    col = gbscan.Column.from_host(v, b, base)
+    preds = [synth.pick_range(synth.seed_for(92, b, i), b, s, base) for i, s in enumerate([0.001, 0.1, 1.0])]
+    for warps, tiles in ((8, step), (12, 2 * step), (16, 4 * step)):
+        if warps * (tiles * 128 * b + 12) > 226 * 1024:
+            continue
+        for st in ("branchfree", "branchy"):
+            gbscan.shape_set(b, st, dict(warps=warps, stages=1, tile_blocks=tiles, vote_rows=0, vec_lanes=0))
+            for lo, hi in preds:
+                r = col.run(lo, hi, st)
+                assert r.pair() == oracle.scan_values(v, lo, hi), (b, st, warps, tiles, lo, hi)
+                assert r.blocks_scanned == (n + 1023) // 1024
+            gbscan.shape_set(b, st, None)
+    col.close()
