@@ -175,7 +175,7 @@ scan_status layout(scan_batch* bt)
     // and a host-built table of each pop's first column.  Two CTAs per SM let
     // the block scheduler give every SM one CTA of each concurrent chain; with
     // one per SM the chains split the SMs between them and the replay took
-    // 22% longer.  Full grids for small groups cost 5-40% on batches of 64 and
+    // 22% longer.  Full grids for small groups cost 5-21% on batches of 64 and
     // 512 columns (thousands of warps popping a few tiles from one counter).
     std::vector<uint32_t> chunk_col;
     const uint64_t cap = 2ull * static_cast<uint64_t>(batch_grid());
